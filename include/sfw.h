@@ -1,0 +1,200 @@
+/*
+ * sfw.h -- C ABI of the GB300 (sm_103a) hot path of the sliding Frank-Wolfe
+ * solver for 3D deconvolution (Courbot & Colicchio, "Boosting the Sliding
+ * Frank-Wolfe solver for 3D deconvolution", arXiv 2009.05473).
+ *
+ * Model (Section 1.1).  A measure mu = sum_n w_n delta_{theta_n} with w_n >= 0
+ * and theta_n = (m_n, sigma_n, d_n) is observed through
+ *     y = H * sum_n G(theta_n, w_n) + noise                       (Eqs. 1, 3)
+ *     G(theta, w; s) = w exp(-|m - s|^d / (2 sigma^d))            (Eq. 2)
+ * The criterion is C = 1/2 |y - Phi mu|^2 + lambda sum_n w_n     (Eq. 4)
+ * and the certificate eta = Phi^T (y - Phi mu) / lambda           (Eq. 5).
+ *
+ * Discretisation (the paper is silent; this library fixes it):
+ *   - a volume of shape n = (n0, n1, n2) is C-contiguous, axis 2 fastest,
+ *     voxel centres at integer coordinates 0..n_a-1;
+ *   - the PSF H has shape (2R0+1, 2R1+1, 2R2+1), centred at index R;
+ *   - atoms are sampled at voxel centres of the extended grid E = n + 2R
+ *     (E index t <-> grid coordinate t - R), blurred by the discrete linear
+ *     convolution with H, and observed on the grid.  Phi is therefore an exact
+ *     finite linear operator and Phi^T its transpose.
+ *
+ * Conventions of every call:
+ *   - returns sfw_status; on failure sfw_last_error() (thread-local) holds a
+ *     one-line message.  No C++ exception crosses the ABI.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary host memory, read during the call only.
+ *   - calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream) unless stated otherwise.
+ *   - a plan owns its device workspace: calls that share a plan must be
+ *     ordered on one stream (or otherwise serialised by the caller).
+ *   - all floating-point data is IEEE binary32 unless the type says double.
+ */
+#ifndef SFW_H_
+#define SFW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFW_OK = 0,
+    SFW_ERR_ARG = 1,         /* NULL pointer, bad count, bad option */
+    SFW_ERR_SHAPE = 2,       /* sizes outside the supported range */
+    SFW_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    SFW_ERR_NAN = 4,         /* a NaN reached a reduction that needs a total order */
+    SFW_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+    SFW_ERR_ALLOC = 6,       /* device allocation failed */
+    SFW_ERR_UNSUPPORTED = 7  /* option not built into this library */
+} sfw_status;
+
+enum { SFW_PREC_FP32 = 0, SFW_PREC_BF16 = 1 };
+
+/* Problem geometry, certificate grid and options of a plan (all HOST memory).
+ *   n[3]      grid shape, each in [4, 1024]
+ *   R[3]      PSF half-widths, each in [0, 64]
+ *   psf       (2R0+1)(2R1+1)(2R2+1) values, C order, centred at index R
+ *   n_sigma, n_d, sigmas, ds
+ *             certificate grid (step 1 of Algorithms 1 and 2): kernels
+ *             k = i_sigma * n_d + i_d, sigma in [0.25, 16], d in [0.5, 4]
+ *   precision SFW_PREC_FP32 (complex64 kernel-family table) or SFW_PREC_BF16
+ *             (bfloat16 table, FP32 arithmetic; see sfw_certificate_grid)
+ *   eps       atom truncation level for rendering and the adjoint: an atom is
+ *             evaluated only where exp(-(rho/sigma)^d/2) >= eps; 0 selects
+ *             1e-9 */
+typedef struct {
+    int n[3];
+    int R[3];
+    const float* psf;
+    int n_sigma;
+    int n_d;
+    const float* sigmas;
+    const float* ds;
+    int precision;
+    float eps;
+} sfw_plan_desc;
+
+typedef struct sfw_plan sfw_plan;
+
+/* Sizes a plan chose (filled by sfw_plan_query). */
+typedef struct {
+    int E[3];               /* extended grid n + 2R */
+    int P_conv[3];          /* FFT grid of the blur, >= E, 2-3-5 smooth */
+    int P_cert[3];          /* FFT grid of the certificate, >= 2n - 1, 2-3-5 smooth */
+    int K;                  /* number of certificate kernels */
+    int real_table;         /* 1 if the kernel-family spectra are real (even H) */
+    size_t table_bytes;     /* device bytes of the kernel-family table */
+    size_t workspace_bytes; /* device bytes of the plan workspace */
+} sfw_plan_info;
+
+/* Atom set (DEVICE memory, FP32, structure of arrays).
+ *   N      number of atoms, 0 <= N <= 4096
+ *   m      N x 3 positions in grid coordinates, row-major
+ *   sigma  N widths (> 0), d  N shape exponents (> 0), w  N weights */
+typedef struct {
+    int N;
+    const float* m;
+    const float* sigma;
+    const float* d;
+    const float* w;
+} sfw_atoms;
+
+/* Create a plan: uploads H, computes its spectrum on P_conv and the table of
+ * kernel-family spectra used by the certificate -- the "lookup table for
+ * convolution in D computed once" of Section 2: for every grid kernel k,
+ * K_k = H * g_{sigma_k, d_k} sampled at every grid displacement, transformed
+ * on P_cert.  Synchronous (returns after the table is built).  *out receives
+ * the plan.  Errors: SFW_ERR_ARG / SFW_ERR_SHAPE on bad sizes,
+ * SFW_ERR_ALLOC, SFW_ERR_CUDA. */
+sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out);
+
+/* Free a plan and its device memory (synchronises the device). NULL is a no-op. */
+sfw_status sfw_plan_destroy(sfw_plan* plan);
+
+/* Copy the plan's sizes into *info (host). */
+sfw_status sfw_plan_query(const sfw_plan* plan, sfw_plan_info* info);
+
+/* Forward operator Phi mu (Eq. 3 without noise), Section 1.1.
+ *   atoms  device atom set (m, sigma, d, w)
+ *   y_out  device, n0*n1*n2 floats, receives (H * sum_n G(theta_n, w_n)) on the grid */
+sfw_status sfw_forward(sfw_plan* plan, const sfw_atoms* atoms, float* y_out, void* stream);
+
+/* Certificate of Eq. 5 on the grid (step 1 of Algorithms 1 and 2):
+ *   eta_k(m) = (1/lambda) sum_{s in grid} r(s) (H * g_k)(s - m)
+ *            = (1/lambda) <Phi G((m, sigma_k, d_k), 1), r>
+ * for every voxel m and kernel k, by FFT correlation with the plan's table.
+ *   residual  device, n0*n1*n2 floats (r = y - Phi mu; r = y for mu = 0)
+ *   lambda    > 0
+ *   eta_out   device K*n0*n1*n2 floats or NULL: eta in flat order k*V + lin(m)
+ *   max_out   device n0*n1*n2 floats or NULL: max over k
+ *   argk_out  device n0*n1*n2 int32 or NULL: the k of max_out (ties -> lowest k)
+ *   best_val, best_idx
+ *             device 1 float / 1 int64 or NULL: the grid maximum and its flat
+ *             index k*V + lin(m), ties -> lowest flat index (the seed of the
+ *             local ascent).  If any eta is NaN, best_idx = -1 and best_val =
+ *             NaN (the call itself cannot see it: it does not synchronise).
+ * With precision SFW_PREC_BF16 the table is read as bfloat16 (values carry
+ * ~3 significant digits); sfw_eta_points re-evaluates candidates in FP32. */
+sfw_status sfw_certificate_grid(sfw_plan* plan, const float* residual, double lambda,
+                                float* eta_out, float* max_out, int32_t* argk_out,
+                                float* best_val, int64_t* best_idx, void* stream);
+
+/* Certificate of Eq. 5 at arbitrary (off-grid) parameters, with its
+ * gradient: the objective of the local ascent of step 1 ("local ascent using
+ * e.g. BFGS, starting from a maximum attained on a grid") and the FP32
+ * re-scoring of grid candidates.
+ *   eta(theta) = (1/lambda) sum_{t in E} g_theta(t) b(t),  b = Phi^T r on E
+ *   residual  device n0*n1*n2 floats
+ *   lambda    > 0
+ *   P         number of rows, 1..4096
+ *   theta     device P x 5 floats, rows (m0, m1, m2, sigma, d)
+ *   eta_out   device P doubles
+ *   grad_out  device P x 5 doubles or NULL: d eta / d (m0, m1, m2, sigma, d)
+ * The atom profile is evaluated where g >= eps (plan option). */
+sfw_status sfw_eta_points(sfw_plan* plan, const float* residual, double lambda, int P,
+                          const float* theta, double* eta_out, double* grad_out, void* stream);
+
+/* Arg-maximum / top-k of a device float array (the grid maximum that seeds
+ * step 1).
+ *   values   device, count floats, count in [1, 2^40]
+ *   topk     1..64: the topk largest values, in decreasing order, ties ->
+ *            lower index first
+ *   val_out  device topk floats; idx_out device topk int64
+ * A NaN anywhere makes idx_out[0] = -1 (checked on the device; the call does
+ * not synchronise). */
+sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_out,
+                      int64_t* idx_out, void* stream);
+
+/* Loss and analytic gradient of the sliding step (step 4 of Algorithm 1,
+ * step 2b of Algorithm 2; Section 2: "grad C computed analytically").
+ *   y         device n0*n1*n2 floats (observation)
+ *   atoms     device atom set, N >= 1
+ *   lambda    >= 0
+ *   loss_out  device 1 double: C = 1/2 sum (y - Phi mu)^2 + lambda sum w
+ *   grad_out  device 6N doubles: [dC/dm (N x 3, row-major) | dC/dsigma (N) |
+ *             dC/dd (N) | dC/dw (N)], with b = Phi^T r on E,
+ *               dC/dw_n = lambda - sum_t g_n(t) b(t),
+ *               dC/dtheta_n = -w_n sum_t (d g_n / d theta)(t) b(t)
+ *   residual_out  device n0*n1*n2 floats or NULL: r = y - Phi mu
+ * The atom field is recomputed inside the call (never stored per atom). */
+sfw_status sfw_slide_loss_grad(sfw_plan* plan, const float* y, const sfw_atoms* atoms,
+                               double lambda, double* loss_out, double* grad_out,
+                               float* residual_out, void* stream);
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char* sfw_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t sfw_launch_count(void);
+
+/* Library version string. */
+const char* sfw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFW_H_ */

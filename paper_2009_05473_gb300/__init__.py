@@ -1,0 +1,209 @@
+"""GB300 hot path of the sliding Frank-Wolfe solver for 3D deconvolution (arXiv 2009.05473).
+
+The compute lives in ``libsfw.so`` (hand-written CUDA for sm_103a, C ABI in
+``include/sfw.h``).  This package marshals torch device tensors into those
+calls; PyTorch only provides device memory and streams.  There is no CPU
+path: without the built library every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _abi
+from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_eta_points, sfw_forward,  # noqa: F401
+                   sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
+                   sfw_slide_loss_grad, sfw_version)
+
+__all__ = ["Plan", "AtomSet", "argmax", "launch_count", "SfwError", "build_library"]
+
+
+def build_library(force: bool = False) -> str:
+    from .build import build
+    return build(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _f32(x, device) -> "torch.Tensor":
+    torch = _torch()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32, device=device).contiguous()
+
+
+@dataclass
+class AtomSet:
+    """Device atom set (FP32 structure of arrays): m (N, 3), sigma, d, w (N)."""
+
+    m: "torch.Tensor"
+    sigma: "torch.Tensor"
+    d: "torch.Tensor"
+    w: "torch.Tensor"
+
+    @property
+    def N(self) -> int:
+        return int(self.w.shape[0])
+
+    @staticmethod
+    def from_numpy(m, sigma, d, w, device="cuda") -> "AtomSet":
+        return AtomSet(_f32(np.reshape(m, (-1, 3)), device), _f32(sigma, device), _f32(d, device),
+                       _f32(w, device))
+
+    @staticmethod
+    def from_params(x, device="cuda") -> "AtomSet":
+        """From a 6N vector in gradient order [m (N x 3) | sigma | d | w]."""
+        torch = _torch()
+        x = torch.as_tensor(x, device=device).to(torch.float32)
+        N = x.numel() // 6
+        return AtomSet(x[:3 * N].reshape(N, 3).contiguous(), x[3 * N:4 * N].contiguous(),
+                       x[4 * N:5 * N].contiguous(), x[5 * N:].contiguous())
+
+    def abi(self) -> _abi.Atoms:
+        for t in (self.m, self.sigma, self.d, self.w):
+            if not (t.is_cuda and t.dtype == _torch().float32 and t.is_contiguous()):
+                raise ValueError("atom arrays must be contiguous float32 CUDA tensors")
+        return _abi.Atoms(self.N, _ptr(self.m), _ptr(self.sigma), _ptr(self.d), _ptr(self.w))
+
+
+class Plan:
+    """A geometry (grid n, PSF half-widths R, PSF H) plus a certificate grid of
+    (sigma, d) kernels; owns the PSF spectrum, the kernel-family table and the
+    device workspace (libsfw ``sfw_plan``)."""
+
+    def __init__(self, n: Sequence[int], R: Sequence[int], psf, sigmas: Sequence[float] = (),
+                 ds: Sequence[float] = (), precision: str = "fp32", eps: float = 0.0,
+                 device: Optional[int] = None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2009_05473_gb300 needs a CUDA GPU (no CPU path)")
+        if device is not None:
+            torch.cuda.set_device(device)
+        self.n = tuple(int(v) for v in n)
+        self.R = tuple(int(v) for v in R)
+        psf = np.ascontiguousarray(psf, dtype=np.float32)
+        sig = np.ascontiguousarray(sigmas, dtype=np.float32)
+        dd = np.ascontiguousarray(ds, dtype=np.float32)
+        self.kernels = [(float(s), float(x)) for s in sig for x in dd]
+        desc = _abi.PlanDesc()
+        desc.n[:] = list(self.n)
+        desc.R[:] = list(self.R)
+        fp = ctypes.POINTER(ctypes.c_float)
+        desc.psf = psf.ctypes.data_as(fp)
+        desc.n_sigma = int(sig.size)
+        desc.n_d = int(dd.size)
+        desc.sigmas = sig.ctypes.data_as(fp) if sig.size else ctypes.cast(None, fp)
+        desc.ds = dd.ctypes.data_as(fp) if dd.size else ctypes.cast(None, fp)
+        desc.precision = {"fp32": _abi.SFW_PREC_FP32, "bf16": _abi.SFW_PREC_BF16}[precision]
+        desc.eps = float(eps)
+        self._keep = (psf, sig, dd)
+        self.handle = sfw_plan_create(desc)
+        info = sfw_plan_query(self.handle)
+        self.info = {"E": tuple(info.E), "P_conv": tuple(info.P_conv), "P_cert": tuple(info.P_cert),
+                     "K": info.K, "real_table": bool(info.real_table),
+                     "table_bytes": int(info.table_bytes), "workspace_bytes": int(info.workspace_bytes)}
+        self.K = info.K
+        self.V = int(np.prod(self.n))
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sfw_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the hot path ------------------------------------------------------------------
+    def forward(self, atoms: AtomSet, out=None, stream=None):
+        """Phi mu on the grid (Eq. 3 without noise)."""
+        torch = _torch()
+        y = out if out is not None else torch.empty(self.n, dtype=torch.float32, device="cuda")
+        sfw_forward(self.handle, atoms.abi(), _ptr(y), _stream_ptr(stream))
+        return y
+
+    def certificate(self, residual, lam: float, want_eta: bool = False, want_max: bool = True,
+                    stream=None, out=None):
+        """Grid certificate (Eq. 5): dict with max (n), argk (n), best_val, best_idx, eta (K, n)."""
+        torch = _torch()
+        out = out or {}
+        eta = out.get("eta")
+        if want_eta and eta is None:
+            eta = torch.empty((self.K,) + self.n, dtype=torch.float32, device="cuda")
+        mx = out.get("max")
+        ak = out.get("argk")
+        if want_max and mx is None:
+            mx = torch.empty(self.n, dtype=torch.float32, device="cuda")
+            ak = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        bv = out.get("best_val")
+        bi = out.get("best_idx")
+        if bv is None:
+            bv = torch.empty(1, dtype=torch.float32, device="cuda")
+            bi = torch.empty(1, dtype=torch.int64, device="cuda")
+        sfw_certificate_grid(self.handle, _ptr(residual), lam, _ptr(eta) if want_eta else 0,
+                             _ptr(mx) if want_max else 0, _ptr(ak) if want_max else 0, _ptr(bv),
+                             _ptr(bi), _stream_ptr(stream))
+        return {"eta": eta if want_eta else None, "max": mx if want_max else None,
+                "argk": ak if want_max else None, "best_val": bv, "best_idx": bi}
+
+    def eta_points(self, residual, lam: float, theta, with_grad: bool = True, stream=None):
+        """eta (and d eta / d theta) at rows theta = (m0, m1, m2, sigma, d), FP32 sums."""
+        torch = _torch()
+        th = torch.as_tensor(theta, dtype=torch.float32, device="cuda").reshape(-1, 5).contiguous()
+        P = th.shape[0]
+        eta = torch.empty(P, dtype=torch.float64, device="cuda")
+        grad = torch.empty((P, 5), dtype=torch.float64, device="cuda") if with_grad else None
+        sfw_eta_points(self.handle, _ptr(residual), lam, P, _ptr(th), _ptr(eta), _ptr(grad),
+                       _stream_ptr(stream))
+        return (eta, grad) if with_grad else eta
+
+    def slide_loss_grad(self, y, atoms: AtomSet, lam: float, want_residual: bool = False,
+                        stream=None, out=None):
+        """(loss (1 double), grad (6N doubles), residual or None) of the sliding step."""
+        torch = _torch()
+        out = out or {}
+        loss = out.get("loss")
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        grad = out.get("grad")
+        if grad is None or grad.numel() != 6 * atoms.N:
+            grad = torch.empty(6 * atoms.N, dtype=torch.float64, device="cuda")
+        r = out.get("residual")
+        if want_residual and r is None:
+            r = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        sfw_slide_loss_grad(self.handle, _ptr(y), atoms.abi(), lam, _ptr(loss), _ptr(grad),
+                            _ptr(r) if want_residual else 0, _stream_ptr(stream))
+        return loss, grad, (r if want_residual else None)
+
+
+def argmax(values, topk: int = 1, stream=None) -> Tuple["torch.Tensor", "torch.Tensor"]:
+    """(values, flat indices) of the topk largest entries, ties to the lowest index."""
+    torch = _torch()
+    v = values.contiguous()
+    vals = torch.empty(topk, dtype=torch.float32, device="cuda")
+    idx = torch.empty(topk, dtype=torch.int64, device="cuda")
+    sfw_argmax(_ptr(v), v.numel(), topk, _ptr(vals), _ptr(idx), _stream_ptr(stream))
+    return vals, idx
+
+
+def launch_count() -> int:
+    """Kernels launched by libsfw in this process."""
+    return sfw_launch_count()

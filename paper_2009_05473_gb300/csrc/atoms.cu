@@ -1,0 +1,274 @@
+// Atom kernels: rendering of the measure's atoms on the extended grid (Eq. 2,
+// summed as inside Eq. 3) and the per-atom adjoint sums of the analytic
+// gradient of the criterion (Eq. 4; Section 2: "grad C is computed
+// analytically", "parallelized across atoms").
+//
+// Both evaluate g(rho) = exp(-(rho/sigma)^d / 2) as
+//     g = exp2(-log2(e)/2 * exp2((d/2) * log2(rho^2 / sigma^2))),
+// which needs no special case at rho = 0 (log2(0) = -inf gives g = 1).  An
+// atom is evaluated only inside its cut-off radius
+//     rho_max = sigma * (2 ln(1/eps))^(1/d),   g(rho_max) = eps.
+#include <math.h>
+
+#include "sfw_internal.cuh"
+
+namespace sfw {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
+
+__device__ __forceinline__ float atom_cut2(float sigma, float d, float log_inv_eps2) {
+    // rho_max^2 = sigma^2 (2 ln(1/eps))^(2/d)
+    return sigma * sigma * exp2f((2.0f / d) * log_inv_eps2);
+}
+
+// ------------------------------------------------------------------ render
+
+constexpr int kRX = 32, kRY = 4, kRZ = 2;  // tile: axis 2 x axis 1 x axis 0
+constexpr int kRenderThreads = kRX * kRY * kRZ;
+
+__global__ void __launch_bounds__(kRenderThreads)
+k_render(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2, float* f) {
+    __shared__ float s_m0[kRenderThreads], s_m1[kRenderThreads], s_m2[kRenderThreads];
+    __shared__ float s_is2[kRenderThreads], s_hd[kRenderThreads], s_w[kRenderThreads];
+    __shared__ float s_c2[kRenderThreads];
+    __shared__ int s_wcount[kRenderThreads / 32];
+    __shared__ int s_total;
+
+    const int tx = threadIdx.x % kRX;
+    const int ty = (threadIdx.x / kRX) % kRY;
+    const int tz = threadIdx.x / (kRX * kRY);
+    const int t2 = (int)blockIdx.x * kRX + tx;
+    const int t1 = (int)blockIdx.y * kRY + ty;
+    const int t0 = (int)blockIdx.z * kRZ + tz;
+    // grid coordinates of this voxel and of the tile's bounding box
+    const float x0 = (float)(t0 - R0), x1 = (float)(t1 - R1), x2 = (float)(t2 - R2);
+    const float b0lo = (float)((int)blockIdx.z * kRZ - R0), b0hi = b0lo + (kRZ - 1);
+    const float b1lo = (float)((int)blockIdx.y * kRY - R1), b1hi = b1lo + (kRY - 1);
+    const float b2lo = (float)((int)blockIdx.x * kRX - R2), b2hi = b2lo + (kRX - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    float acc = 0.f;
+    for (int base = 0; base < a.N; base += kRenderThreads) {
+        const int ai = base + threadIdx.x;
+        bool keep = false;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, sg = 1.f, dd = 2.f, w = 0.f, c2 = 0.f;
+        if (ai < a.N) {
+            m0 = a.m[a.ms * ai + 0];
+            m1 = a.m[a.ms * ai + 1];
+            m2 = a.m[a.ms * ai + 2];
+            sg = a.sigma[a.ps * ai];
+            dd = a.d[a.ps * ai];
+            w = a.w[a.ps * ai];
+            c2 = atom_cut2(sg, dd, log_inv_eps2);
+            const float e0 = m0 - fminf(fmaxf(m0, b0lo), b0hi);
+            const float e1 = m1 - fminf(fmaxf(m1, b1lo), b1hi);
+            const float e2 = m2 - fminf(fmaxf(m2, b2lo), b2hi);
+            keep = (e0 * e0 + e1 * e1 + e2 * e2) <= c2 && w != 0.f;
+        }
+        // order-preserving compaction of the kept atoms (deterministic sums)
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_wcount[warp] = __popc(ball);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int q = 0; q < kRenderThreads / 32; ++q) {
+                const int c = s_wcount[q];
+                s_wcount[q] = run;
+                run += c;
+            }
+            s_total = run;
+        }
+        __syncthreads();
+        if (keep) {
+            const int pos = s_wcount[warp] + __popc(ball & ((1u << lane) - 1u));
+            s_m0[pos] = m0;
+            s_m1[pos] = m1;
+            s_m2[pos] = m2;
+            s_is2[pos] = 1.0f / (sg * sg);
+            s_hd[pos] = 0.5f * dd;
+            s_w[pos] = w;
+            s_c2[pos] = c2;
+        }
+        __syncthreads();
+        const int cnt = s_total;
+        for (int q = 0; q < cnt; ++q) {
+            const float e0 = x0 - s_m0[q], e1 = x1 - s_m1[q], e2 = x2 - s_m2[q];
+            const float r2 = e0 * e0 + e1 * e1 + e2 * e2;
+            if (r2 <= s_c2[q]) {
+                const float u = exp2f(s_hd[q] * __log2f(r2 * s_is2[q]));
+                acc += s_w[q] * exp2f(-0.5f * kLog2e * u);
+            }
+        }
+        __syncthreads();
+    }
+    if (t0 < E0 && t1 < E1 && t2 < E2) f[((long long)t0 * E1 + t1) * E2 + t2] = acc;
+}
+
+sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], float eps, float* f,
+                         cudaStream_t st) {
+    dim3 grid((E[2] + kRX - 1) / kRX, (E[1] + kRY - 1) / kRY, (E[0] + kRZ - 1) / kRZ);
+    const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
+    k_render<<<grid, kRenderThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, f);
+    counted_launch();
+    return launch_check("k_render");
+}
+
+// ------------------------------------------------------------------ adjoint gradient
+
+constexpr int kGradThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kGradThreads / 32; ++q) t += s_red[q];
+    return t;
+}
+
+// grid = (N, kGradChunks): chunk c of atom n strides over the atom's box.
+__global__ void __launch_bounds__(kGradThreads)
+k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2,
+            const float* __restrict__ b, double* partials) {
+    __shared__ double s_red[kGradThreads / 32];
+    const int n = blockIdx.x;
+    const int c = blockIdx.y;
+    const float m0 = a.m[a.ms * n + 0], m1 = a.m[a.ms * n + 1], m2 = a.m[a.ms * n + 2];
+    const float sg = a.sigma[a.ps * n], dd = a.d[a.ps * n];
+    const float c2 = atom_cut2(sg, dd, log_inv_eps2);
+    const float rmax = sqrtf(c2);
+    const float is2 = 1.0f / (sg * sg);
+    const float hd = 0.5f * dd;
+    // box in E index coordinates (E index = grid coordinate + R)
+    const int lo0 = max(0, (int)ceilf(m0 + R0 - rmax)), hi0 = min(E0 - 1, (int)floorf(m0 + R0 + rmax));
+    const int lo1 = max(0, (int)ceilf(m1 + R1 - rmax)), hi1 = min(E1 - 1, (int)floorf(m1 + R1 + rmax));
+    const int lo2 = max(0, (int)ceilf(m2 + R2 - rmax)), hi2 = min(E2 - 1, (int)floorf(m2 + R2 + rmax));
+    const long long n0 = max(0, hi0 - lo0 + 1), n1 = max(0, hi1 - lo1 + 1), n2 = max(0, hi2 - lo2 + 1);
+    const long long nb = n0 * n1 * n2;
+
+    float sg_b = 0.f, sm0 = 0.f, sm1 = 0.f, sm2 = 0.f, ss = 0.f, sd = 0.f;
+    for (long long v = (long long)c * kGradThreads + threadIdx.x; v < nb;
+         v += (long long)gridDim.y * kGradThreads) {
+        const int i2 = (int)(v % n2);
+        const long long r = v / n2;
+        const int i1 = (int)(r % n1);
+        const int i0 = (int)(r / n1);
+        const int t0 = lo0 + i0, t1 = lo1 + i1, t2 = lo2 + i2;
+        const float e0 = m0 - (float)(t0 - R0), e1 = m1 - (float)(t1 - R1), e2 = m2 - (float)(t2 - R2);
+        const float r2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (r2 > c2) continue;
+        const float bt = b[((long long)t0 * E1 + t1) * E2 + t2];
+        const float lq = __log2f(r2 * is2);
+        const float u = 0.5f * exp2f(hd * lq);
+        const float g = exp2f(-kLog2e * u);
+        const float gb = g * bt;
+        sg_b += gb;
+        if (r2 > 0.f) {
+            // dg/dm_a = -g d u (m_a - x_a) / rho^2
+            const float cm = -gb * dd * u / r2;
+            sm0 += cm * e0;
+            sm1 += cm * e1;
+            sm2 += cm * e2;
+            ss += gb * (dd / sg) * u;              // dg/dsigma = g (d/sigma) u
+            sd += -gb * u * (0.5f * kLn2 * lq);    // dg/dd = -g u ln(rho/sigma)
+        }
+    }
+    double out[6] = {sm0, sm1, sm2, ss, sd, sg_b};
+    for (int q = 0; q < 6; ++q) {
+        const double t = block_sum(out[q], s_red);
+        if (threadIdx.x == 0) partials[((long long)n * gridDim.y + c) * 6 + q] = t;
+    }
+}
+
+__global__ void k_grad_finalize(AtomsDev a, int chunks, const double* partials, double lambda,
+                                double* grad) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N) return;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < chunks; ++c)
+        for (int q = 0; q < 6; ++q) s[q] += partials[((long long)n * chunks + c) * 6 + q];
+    const double w = a.w[a.ps * n];
+    const int N = a.N;
+    grad[3 * n + 0] = -w * s[0];
+    grad[3 * n + 1] = -w * s[1];
+    grad[3 * n + 2] = -w * s[2];
+    grad[3 * N + n] = -w * s[3];
+    grad[4 * N + n] = -w * s[4];
+    grad[5 * N + n] = lambda - s[5];
+}
+
+sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
+                            const float* b, double lambda, double* partials, double* grad,
+                            cudaStream_t st) {
+    if (a.N <= 0) return SFW_OK;
+    const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
+    dim3 grid(a.N, kGradChunks);
+    k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2,
+                                                b, partials);
+    counted_launch();
+    SFW_TRY(launch_check("k_atom_grad"));
+    k_grad_finalize<<<(a.N + 127) / 128, 128, 0, st>>>(a, kGradChunks, partials, lambda, grad);
+    counted_launch();
+    return launch_check("k_grad_finalize");
+}
+
+// eta and its gradient at parameter rows: the same per-atom sums, scaled by 1/lambda.
+__global__ void k_eta_finalize(int P, int chunks, const double* partials, double lambda,
+                               double* eta, double* grad) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= P) return;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < chunks; ++c)
+        for (int q = 0; q < 6; ++q) s[q] += partials[((long long)n * chunks + c) * 6 + q];
+    eta[n] = s[5] / lambda;
+    if (grad)
+        for (int q = 0; q < 5; ++q) grad[5 * n + q] = s[q] / lambda;
+}
+
+sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3], float eps,
+                             const float* b, double lambda, double* partials, double* eta,
+                             double* grad, cudaStream_t st) {
+    if (pts.N <= 0) return SFW_OK;
+    const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
+    dim3 grid(pts.N, kGradChunks);
+    k_atom_grad<<<grid, kGradThreads, 0, st>>>(pts, E[0], E[1], E[2], R[0], R[1], R[2],
+                                                log_inv_eps2, b, partials);
+    counted_launch();
+    SFW_TRY(launch_check("k_atom_grad"));
+    k_eta_finalize<<<(pts.N + 127) / 128, 128, 0, st>>>(pts.N, kGradChunks, partials, lambda, eta,
+                                                        grad);
+    counted_launch();
+    return launch_check("k_eta_finalize");
+}
+
+// ------------------------------------------------------------------ loss
+
+__global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, double lambda,
+                                double* loss) {
+    __shared__ double s_red[8];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
+    double wsum = 0.0;
+    for (int i = threadIdx.x; i < a.N; i += blockDim.x) wsum += (double)a.w[a.ps * i];
+    double v = 0.5 * acc + lambda * wsum;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += s_red[q];
+        *loss = t;
+    }
+}
+
+sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
+                                double lambda, double* loss, cudaStream_t st) {
+    k_loss_finalize<<<1, 256, 0, st>>>(partials, nparts, a, lambda, loss);
+    counted_launch();
+    return launch_check("k_loss_finalize");
+}
+
+}  // namespace sfw

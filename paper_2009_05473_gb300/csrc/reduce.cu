@@ -1,0 +1,284 @@
+// Reductions and layout kernels: arg-maximum / top-k of the certificate (the
+// grid maximum that seeds the local ascent of step 1, Algorithms 1 and 2),
+// circular placement of the PSF and of the kernel family on FFT grids, and
+// the conversions of the kernel-family table (Section 2's lookup table).
+#include <math.h>
+
+#include "sfw_internal.cuh"
+
+namespace sfw {
+
+// ------------------------------------------------------------------ circular placement
+
+// out[p] = H(u) with u_a = p_a if p_a <= R_a, p_a - P_a if p_a >= P_a - R_a, else 0.
+__global__ void k_wrap_psf(const float* psf, int R0, int R1, int R2, int P0, int P1, int P2,
+                           float* out) {
+    const long long total = (long long)P0 * P1 * P2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p2 = (int)(i % P2);
+        const long long r = i / P2;
+        const int p1 = (int)(r % P1);
+        const int p0 = (int)(r / P1);
+        const int u0 = p0 <= R0 ? p0 : (p0 >= P0 - R0 ? p0 - P0 : 1 << 30);
+        const int u1 = p1 <= R1 ? p1 : (p1 >= P1 - R1 ? p1 - P1 : 1 << 30);
+        const int u2 = p2 <= R2 ? p2 : (p2 >= P2 - R2 ? p2 - P2 : 1 << 30);
+        float v = 0.f;
+        if (u0 != (1 << 30) && u1 != (1 << 30) && u2 != (1 << 30))
+            v = psf[((long long)(u0 + R0) * (2 * R1 + 1) + (u1 + R1)) * (2 * R2 + 1) + (u2 + R2)];
+        out[i] = v;
+    }
+}
+
+sfw_status launch_wrap_psf(const float* psf, const int R[3], const int P[3], float* out,
+                           cudaStream_t st) {
+    k_wrap_psf<<<1024, 256, 0, st>>>(psf, R[0], R[1], R[2], P[0], P[1], P[2], out);
+    counted_launch();
+    return launch_check("k_wrap_psf");
+}
+
+// kx holds K(x) for |x_a| <= n_a - 1 at index x + (n - 1) (dense (2n-1)^3).
+// out[p] = K(-x) with x_a = p_a (p_a <= n_a - 1) or p_a - P_a (p_a >= P_a - n_a + 1), else 0:
+// the correlation kernel placed for a circular convolution on P.
+__global__ void k_wrap_kernel(const float* kx, int n0, int n1, int n2, int P0, int P1, int P2,
+                              float* out) {
+    const long long total = (long long)P0 * P1 * P2;
+    const int D1 = 2 * n1 - 1, D2 = 2 * n2 - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int p2 = (int)(i % P2);
+        const long long r = i / P2;
+        const int p1 = (int)(r % P1);
+        const int p0 = (int)(r / P1);
+        const int x0 = p0 <= n0 - 1 ? p0 : (p0 >= P0 - n0 + 1 ? p0 - P0 : 1 << 30);
+        const int x1 = p1 <= n1 - 1 ? p1 : (p1 >= P1 - n1 + 1 ? p1 - P1 : 1 << 30);
+        const int x2 = p2 <= n2 - 1 ? p2 : (p2 >= P2 - n2 + 1 ? p2 - P2 : 1 << 30);
+        float v = 0.f;
+        if (x0 != (1 << 30) && x1 != (1 << 30) && x2 != (1 << 30))
+            v = kx[((long long)(-x0 + n0 - 1) * D1 + (-x1 + n1 - 1)) * D2 + (-x2 + n2 - 1)];
+        out[i] = v;
+    }
+}
+
+sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int P[3], float* out,
+                              cudaStream_t st) {
+    k_wrap_kernel<<<1024, 256, 0, st>>>(kx, n[0], n[1], n[2], P[0], P[1], P[2], out);
+    counted_launch();
+    return launch_check("k_wrap_kernel");
+}
+
+// ------------------------------------------------------------------ arg-maximum (top-1)
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_down_sync(0xffffffffu, v, off);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v) {
+    __shared__ unsigned long long s[kRedThreads / 32];
+    v = warp_max_u64(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long r = 0ull;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kRedThreads / 32; ++q) r = s[q] > r ? s[q] : r;
+    return r;
+}
+
+// Pass 1: per-block max of candidate keys of v[i] (value, then lowest index).
+__global__ void __launch_bounds__(kRedThreads)
+k_argmax_keys(const float* __restrict__ v, long long count, unsigned long long* partial) {
+    unsigned long long best = 0ull;
+    for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < count;
+         i += (long long)gridDim.x * kRedThreads) {
+        const unsigned long long k = candidate_key(v[i], (unsigned long long)i);
+        best = k > best ? k : best;
+    }
+    best = block_max_u64(best);
+    if (threadIdx.x == 0) partial[blockIdx.x] = best;
+}
+
+// Pass 2: max over the partial keys, then decode.
+__global__ void __launch_bounds__(kRedThreads)
+k_argmax_final(const unsigned long long* partial, int n, float* val, int64_t* idx) {
+    unsigned long long best = 0ull;
+    for (int i = threadIdx.x; i < n; i += kRedThreads) best = partial[i] > best ? partial[i] : best;
+    best = block_max_u64(best);
+    if (threadIdx.x == 0) {
+        if (best == ~0ull || best == 0ull) {
+            *val = __int_as_float(0x7fc00000);
+            *idx = -1;
+        } else {
+            *val = float_from_order_key((unsigned int)(best >> 32));
+            *idx = (int64_t)(0xffffffffu - (unsigned int)(best & 0xffffffffu));
+        }
+    }
+}
+
+sfw_status launch_argmax_keys(const float* v, long long count, unsigned long long* partial,
+                              int nblocks, cudaStream_t st) {
+    k_argmax_keys<<<nblocks, kRedThreads, 0, st>>>(v, count, partial);
+    counted_launch();
+    return launch_check("k_argmax_keys");
+}
+
+sfw_status launch_argmax_final(const unsigned long long* partial, int n, float* val, int64_t* idx,
+                               cudaStream_t st) {
+    k_argmax_final<<<1, kRedThreads, 0, st>>>(partial, n, val, idx);
+    counted_launch();
+    return launch_check("k_argmax_final");
+}
+
+__global__ void k_key_decode(const unsigned long long* key, float* val, int64_t* idx) {
+    const unsigned long long best = *key;
+    if (best == ~0ull || best == 0ull) {
+        if (val) *val = __int_as_float(0x7fc00000);
+        if (idx) *idx = -1;
+    } else {
+        if (val) *val = float_from_order_key((unsigned int)(best >> 32));
+        if (idx) *idx = (int64_t)(0xffffffffu - (unsigned int)(best & 0xffffffffu));
+    }
+}
+
+sfw_status launch_key_decode(const unsigned long long* key, float* val, int64_t* idx,
+                             cudaStream_t st) {
+    k_key_decode<<<1, 1, 0, st>>>(key, val, idx);
+    counted_launch();
+    return launch_check("k_key_decode");
+}
+
+// ------------------------------------------------------------------ top-k (k <= 64)
+
+constexpr int kSortN = 4096;  // keys sorted per block
+
+// Sort kSortN keys descending in shared memory (bitonic network).
+__device__ void bitonic_desc(unsigned long long* s) {
+    for (int size = 2; size <= kSortN; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < kSortN / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool desc = ((lo & size) == 0);
+                const unsigned long long a = s[lo], b = s[hi];
+                if ((a < b) == desc) {
+                    s[lo] = b;
+                    s[hi] = a;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Each block takes kSortN consecutive inputs (values -> keys when `v` is set,
+// else keys from `kin`), sorts them and writes its top `k` keys.
+__global__ void __launch_bounds__(kRedThreads)
+k_topk_block(const float* v, const unsigned long long* kin, long long count, int k,
+             unsigned long long* kout) {
+    __shared__ unsigned long long s[kSortN];
+    const long long base = (long long)blockIdx.x * kSortN;
+    for (int i = threadIdx.x; i < kSortN; i += kRedThreads) {
+        const long long g = base + i;
+        unsigned long long key = 0ull;
+        if (g < count) key = v ? candidate_key(v[g], (unsigned long long)g) : kin[g];
+        s[i] = key;
+    }
+    bitonic_desc(s);
+    for (int i = threadIdx.x; i < k; i += kRedThreads) kout[(long long)blockIdx.x * k + i] = s[i];
+}
+
+__global__ void k_topk_decode(const unsigned long long* keys, int k, float* val, int64_t* idx) {
+    const int i = threadIdx.x;
+    if (i >= k) return;
+    const unsigned long long key = keys[i];
+    bool nan_seen = keys[0] == ~0ull;
+    if (nan_seen || key == 0ull) {
+        val[i] = __int_as_float(0x7fc00000);
+        idx[i] = -1;
+    } else {
+        val[i] = float_from_order_key((unsigned int)(key >> 32));
+        idx[i] = (int64_t)(0xffffffffu - (unsigned int)(key & 0xffffffffu));
+    }
+}
+
+sfw_status launch_topk(const float* v, long long count, int topk, unsigned long long* scratch,
+                       long long scratch_len, float* val_out, int64_t* idx_out, cudaStream_t st) {
+    // ping-pong halves of scratch
+    long long blocks = (count + kSortN - 1) / kSortN;
+    long long half = scratch_len / 2;
+    if (blocks * topk > half) return fail(SFW_ERR_SHAPE, "topk scratch too small");
+    unsigned long long* a = scratch;
+    unsigned long long* b = scratch + half;
+    k_topk_block<<<(unsigned)blocks, kRedThreads, 0, st>>>(v, nullptr, count, topk, a);
+    counted_launch();
+    SFW_TRY(launch_check("k_topk_block"));
+    long long n = blocks * topk;
+    while (n > kSortN) {
+        blocks = (n + kSortN - 1) / kSortN;
+        k_topk_block<<<(unsigned)blocks, kRedThreads, 0, st>>>(nullptr, a, n, topk, b);
+        counted_launch();
+        SFW_TRY(launch_check("k_topk_block"));
+        n = blocks * topk;
+        unsigned long long* t = a;
+        a = b;
+        b = t;
+    }
+    k_topk_block<<<1, kRedThreads, 0, st>>>(nullptr, a, n, topk, b);
+    counted_launch();
+    SFW_TRY(launch_check("k_topk_block"));
+    k_topk_decode<<<1, 64, 0, st>>>(b, topk, val_out, idx_out);
+    counted_launch();
+    return launch_check("k_topk_decode");
+}
+
+// ------------------------------------------------------------------ table statistics / conversion
+
+__global__ void k_spec_stats(const float2* s, long long count, float* stats) {
+    float re = 0.f, im = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        re = fmaxf(re, fabsf(s[i].x));
+        im = fmaxf(im, fabsf(s[i].y));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        re = fmaxf(re, __shfl_down_sync(0xffffffffu, re, off));
+        im = fmaxf(im, __shfl_down_sync(0xffffffffu, im, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative floats order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned int*>(stats), __float_as_uint(re));
+        atomicMax(reinterpret_cast<unsigned int*>(stats) + 1, __float_as_uint(im));
+    }
+}
+
+sfw_status launch_spec_stats(const float2* s, long long count, float* stats, cudaStream_t st) {
+    k_spec_stats<<<1024, 256, 0, st>>>(s, count, stats);
+    counted_launch();
+    return launch_check("k_spec_stats");
+}
+
+__global__ void k_spec_convert(const float2* s, long long count, int kind, void* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = s[i];
+        if (kind == SPEC_R32) reinterpret_cast<float*>(out)[i] = v.x;
+        else if (kind == SPEC_CBF16) reinterpret_cast<__nv_bfloat162*>(out)[i] = __float22bfloat162_rn(v);
+        else if (kind == SPEC_RBF16) reinterpret_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v.x);
+        else reinterpret_cast<float2*>(out)[i] = v;
+    }
+}
+
+sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out,
+                               cudaStream_t st) {
+    k_spec_convert<<<1024, 256, 0, st>>>(s, count, kind, out);
+    counted_launch();
+    return launch_check("k_spec_convert");
+}
+
+}  // namespace sfw

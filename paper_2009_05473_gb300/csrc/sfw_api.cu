@@ -1,0 +1,909 @@
+// C ABI of libsfw: plans and the hot-path entry points of the sliding
+// Frank-Wolfe solver (arXiv 2009.05473).  Every step of the path runs in the
+// kernels of this library; this file only checks arguments, owns device
+// memory and sequences the launches on the caller's stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "sfw_internal.cuh"
+
+namespace sfw {
+
+// ------------------------------------------------------------------ errors
+
+static thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+
+sfw_status fail(sfw_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sfw_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? SFW_ERR_ALLOC : SFW_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+void clear_error() { g_err[0] = 0; }
+
+sfw_status launch_check(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return SFW_OK;
+}
+
+// ------------------------------------------------------------------ geometry of a blur
+
+// Transform grid of a blur whose input lives on the box E and whose output
+// (the observation grid) is the sub-box [R, R + n) of E.
+struct BlurGeom {
+    int n[3], R[3], E[3], P[3], H2;
+    Factors fac[3];
+    const float2* tw[3];
+};
+
+static sfw_status make_blur_geom(TwiddleCache& tc, const int n[3], const int R[3], BlurGeom* g) {
+    for (int a = 0; a < 3; ++a) {
+        g->n[a] = n[a];
+        g->R[a] = R[a];
+        g->E[a] = n[a] + 2 * R[a];
+        g->P[a] = next_smooth_even(g->E[a]);
+        if (g->P[a] > kMaxLen) return fail(SFW_ERR_SHAPE, "FFT length %d > %d", g->P[a], kMaxLen);
+        if (!factorize(g->P[a], &g->fac[a])) return fail(SFW_ERR_SHAPE, "cannot factor %d", g->P[a]);
+        SFW_TRY(tc.get(g->P[a], &g->tw[a]));
+    }
+    g->H2 = g->P[2] / 2 + 1;
+    return SFW_OK;
+}
+
+static size_t blur_buf_elems(const BlurGeom& g) {
+    return (size_t)g.E[0] * g.P[1] * g.H2;  // >= every intermediate of forward and transpose
+}
+
+static LineSet ls(long long Sa, long long Sb, long long Sj, long long B) {
+    LineSet s;
+    s.Sa = Sa;
+    s.Sb = Sb;
+    s.Sj = Sj;
+    s.B = B;
+    return s;
+}
+
+// Blur forward: f on E (dense) -> observation grid through C2R epilogue `ep`
+// (fields in/lin/nlines/L/fac/tw/out_off/out_len/lout filled here).
+static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* spec, int spec_kind,
+                               float2* bufA, float2* bufB, C2RPass ep, cudaStream_t st,
+                               int* c2r_blocks_out) {
+    const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2];
+    const int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2], H2 = g.H2;
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    {   // axis 2: real lines of f -> half spectra (E0, E1, H2)
+        R2CPass p;
+        p.in = f;
+        p.lin = ls((long long)E1 * E2, E2, 1, E1);
+        p.nlines = (long long)E0 * E1;
+        p.in_off = 0;
+        p.in_len = E2;
+        p.L = P2;
+        p.fac = g.fac[2];
+        p.tw = g.tw[2];
+        p.out = bufA;
+        p.lout = ls((long long)E1 * H2, H2, 1, E1);
+        SFW_TRY(launch_r2c(p, st));
+    }
+    {   // axis 1 forward: (E0, E1, H2) -> (E0, P1, H2)
+        C2CPass p;
+        p.in = bufA;
+        p.out = bufB;
+        p.lin = ls((long long)E1 * H2, 1, H2, H2);
+        p.lout = ls((long long)P1 * H2, 1, H2, H2);
+        p.nlines = (long long)E0 * H2;
+        p.L = P1;
+        p.in_off = 0;
+        p.in_len = E1;
+        p.out_off = 0;
+        p.out_len = P1;
+        p.dir = -1;
+        p.scale = 1.f;
+        p.fac = g.fac[1];
+        p.tw = g.tw[1];
+        SFW_TRY(launch_c2c(p, st));
+    }
+    {   // axis 0: forward, times H^, inverse, keep rows [R0, R0 + n0) -> (n0, P1, H2)
+        MulPass p;
+        const long long nl = (long long)P1 * H2;
+        p.in = bufB;
+        p.lin = ls(0, 1, nl, nl);
+        p.in_off = 0;
+        p.in_len = E0;
+        p.nlines = nl;
+        p.L = P0;
+        p.fac = g.fac[0];
+        p.tw = g.tw[0];
+        p.spec = spec;
+        p.lspec = ls(0, 1, nl, nl);
+        p.spec_stride = 0;
+        p.nspec = 1;
+        p.spec_kind = spec_kind;
+        p.conj_spec = 0;
+        p.out = bufA;
+        p.lout = ls(0, 1, nl, nl);
+        p.out_stride = 0;
+        p.out_off = g.R[0];
+        p.out_len = n0;
+        SFW_TRY(launch_mul(p, st));
+    }
+    {   // axis 1 inverse: (n0, P1, H2) -> (n0, n1, H2), rows [R1, R1 + n1)
+        C2CPass p;
+        p.in = bufA;
+        p.out = bufB;
+        p.lin = ls((long long)P1 * H2, 1, H2, H2);
+        p.lout = ls((long long)n1 * H2, 1, H2, H2);
+        p.nlines = (long long)n0 * H2;
+        p.L = P1;
+        p.in_off = 0;
+        p.in_len = P1;
+        p.out_off = g.R[1];
+        p.out_len = n1;
+        p.dir = 1;
+        p.scale = 1.f;
+        p.fac = g.fac[1];
+        p.tw = g.tw[1];
+        SFW_TRY(launch_c2c(p, st));
+    }
+    // axis 2 inverse with the epilogue: (n0, n1, H2) -> grid (n0, n1, n2)
+    ep.in = bufB;
+    ep.lin = ls((long long)n1 * H2, H2, 1, n1);
+    ep.nlines = (long long)n0 * n1;
+    ep.in_spec_stride = 0;
+    if (ep.mode != C2R_CERTMAX) ep.nspec = 1;
+    ep.L = P2;
+    ep.fac = g.fac[2];
+    ep.tw = g.tw[2];
+    ep.out_off = g.R[2];
+    ep.out_len = n2;
+    ep.lout = ls((long long)n1 * n2, n2, 1, n1);
+    return launch_c2r(ep, st, c2r_blocks_out);
+}
+
+// Transpose of the blur: r on the grid -> b on E (dense), b(t) = sum_s H(s - t) r(s).
+static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* spec,
+                                 int spec_kind, float2* bufA, float2* bufB, float* b,
+                                 cudaStream_t st) {
+    const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2];
+    const int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2], H2 = g.H2;
+    const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    {   // axis 2: grid lines of r placed at rows [R2, R2 + n2) -> (n0, n1, H2)
+        R2CPass p;
+        p.in = r;
+        p.lin = ls((long long)n1 * n2, n2, 1, n1);
+        p.nlines = (long long)n0 * n1;
+        p.in_off = g.R[2];
+        p.in_len = n2;
+        p.L = P2;
+        p.fac = g.fac[2];
+        p.tw = g.tw[2];
+        p.out = bufA;
+        p.lout = ls((long long)n1 * H2, H2, 1, n1);
+        SFW_TRY(launch_r2c(p, st));
+    }
+    {   // axis 1 forward, rows at [R1, R1 + n1): (n0, n1, H2) -> (n0, P1, H2)
+        C2CPass p;
+        p.in = bufA;
+        p.out = bufB;
+        p.lin = ls((long long)n1 * H2, 1, H2, H2);
+        p.lout = ls((long long)P1 * H2, 1, H2, H2);
+        p.nlines = (long long)n0 * H2;
+        p.L = P1;
+        p.in_off = g.R[1];
+        p.in_len = n1;
+        p.out_off = 0;
+        p.out_len = P1;
+        p.dir = -1;
+        p.scale = 1.f;
+        p.fac = g.fac[1];
+        p.tw = g.tw[1];
+        SFW_TRY(launch_c2c(p, st));
+    }
+    {   // axis 0: forward (rows at [R0, R0 + n0)), times conj(H^), inverse -> (E0, P1, H2)
+        MulPass p;
+        const long long nl = (long long)P1 * H2;
+        p.in = bufB;
+        p.lin = ls(0, 1, nl, nl);
+        p.in_off = g.R[0];
+        p.in_len = n0;
+        p.nlines = nl;
+        p.L = P0;
+        p.fac = g.fac[0];
+        p.tw = g.tw[0];
+        p.spec = spec;
+        p.lspec = ls(0, 1, nl, nl);
+        p.spec_stride = 0;
+        p.nspec = 1;
+        p.spec_kind = spec_kind;
+        p.conj_spec = 1;
+        p.out = bufA;
+        p.lout = ls(0, 1, nl, nl);
+        p.out_stride = 0;
+        p.out_off = 0;
+        p.out_len = E0;
+        SFW_TRY(launch_mul(p, st));
+    }
+    {   // axis 1 inverse: (E0, P1, H2) -> (E0, E1, H2)
+        C2CPass p;
+        p.in = bufA;
+        p.out = bufB;
+        p.lin = ls((long long)P1 * H2, 1, H2, H2);
+        p.lout = ls((long long)E1 * H2, 1, H2, H2);
+        p.nlines = (long long)E0 * H2;
+        p.L = P1;
+        p.in_off = 0;
+        p.in_len = P1;
+        p.out_off = 0;
+        p.out_len = E1;
+        p.dir = 1;
+        p.scale = 1.f;
+        p.fac = g.fac[1];
+        p.tw = g.tw[1];
+        SFW_TRY(launch_c2c(p, st));
+    }
+    C2RPass p;
+    memset(&p, 0, sizeof(p));
+    p.in = bufB;
+    p.lin = ls((long long)E1 * H2, H2, 1, E1);
+    p.nlines = (long long)E0 * E1;
+    p.nspec = 1;
+    p.L = P2;
+    p.fac = g.fac[2];
+    p.tw = g.tw[2];
+    p.out_off = 0;
+    p.out_len = E2;
+    p.lout = ls((long long)E1 * E2, E2, 1, E1);
+    p.scale = 1.f;
+    p.mode = C2R_STORE;
+    p.out = b;
+    return launch_c2r(p, st, nullptr);
+}
+
+// Full forward transform of a dense real volume on the grid P (no padding):
+// out (P0, P1, P2/2 + 1) complex, scaled by `scale`.  tmp holds P0*P1*H2.
+static sfw_status fft3_forward(const int P[3], const Factors fac[3], const float2* const tw[3],
+                               const float* in, float2* tmp, float2* out, float scale,
+                               cudaStream_t st) {
+    const int P0 = P[0], P1 = P[1], P2 = P[2], H2 = P2 / 2 + 1;
+    {
+        R2CPass p;
+        p.in = in;
+        p.lin = ls((long long)P1 * P2, P2, 1, P1);
+        p.nlines = (long long)P0 * P1;
+        p.in_off = 0;
+        p.in_len = P2;
+        p.L = P2;
+        p.fac = fac[2];
+        p.tw = tw[2];
+        p.out = out;
+        p.lout = ls((long long)P1 * H2, H2, 1, P1);
+        SFW_TRY(launch_r2c(p, st));
+    }
+    {
+        C2CPass p;
+        p.in = out;
+        p.out = tmp;
+        p.lin = ls((long long)P1 * H2, 1, H2, H2);
+        p.lout = p.lin;
+        p.nlines = (long long)P0 * H2;
+        p.L = P1;
+        p.in_off = 0;
+        p.in_len = P1;
+        p.out_off = 0;
+        p.out_len = P1;
+        p.dir = -1;
+        p.scale = 1.f;
+        p.fac = fac[1];
+        p.tw = tw[1];
+        SFW_TRY(launch_c2c(p, st));
+    }
+    {
+        C2CPass p;
+        const long long nl = (long long)P1 * H2;
+        p.in = tmp;
+        p.out = out;
+        p.lin = ls(0, 1, nl, nl);
+        p.lout = p.lin;
+        p.nlines = nl;
+        p.L = P0;
+        p.in_off = 0;
+        p.in_len = P0;
+        p.out_off = 0;
+        p.out_len = P0;
+        p.dir = -1;
+        p.scale = scale;
+        p.fac = fac[0];
+        p.tw = tw[0];
+        SFW_TRY(launch_c2c(p, st));
+    }
+    return SFW_OK;
+}
+
+}  // namespace sfw
+
+using namespace sfw;
+
+// ------------------------------------------------------------------ the plan
+
+struct sfw_plan {
+    int n[3], R[3], E[3];
+    long long V, VE;
+    float eps;
+    int precision;
+    TwiddleCache tw;
+    BlurGeom blur;
+    // certificate grid
+    int K;
+    std::vector<float> sigmas, ds;  // per kernel k
+    int Pc[3], H2c;
+    Factors facc[3];
+    const float2* twc[3];
+    void* table;        // K x Pc0 x Pc1 x H2c spectra
+    int table_kind;
+    size_t table_bytes;
+    int real_table;
+    // device buffers
+    float* psf;
+    float2* Hspec;      // P0 x P1 x H2 (complex64), scaled by 1/|P|
+    float2* bufA;
+    float2* bufB;
+    float* fE;          // rendered atoms on E
+    float* bE;          // back-projected residual on E
+    float* r;           // residual on the grid
+    double* loss_parts;
+    int loss_parts_len;
+    double* grad_parts;
+    int grad_parts_atoms;
+    float2* cA;
+    float2* cB;
+    float2* cC;
+    unsigned long long* best_key;
+    unsigned long long* red_scratch;
+    long long red_scratch_len;
+    size_t ws_bytes;
+    std::vector<void*> allocations;
+};
+
+static sfw_status plan_alloc(sfw_plan* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SFW_ERR_ALLOC, "cudaMalloc(%zu bytes) failed", bytes);
+    }
+    p->allocations.push_back(*ptr);
+    p->ws_bytes += bytes;
+    return SFW_OK;
+}
+
+template <typename T>
+static sfw_status plan_alloc_t(sfw_plan* p, T** ptr, size_t count) {
+    void* v = nullptr;
+    SFW_TRY(plan_alloc(p, &v, sizeof(T) * count));
+    *ptr = static_cast<T*>(v);
+    return SFW_OK;
+}
+
+static void plan_free(sfw_plan* p) {
+    if (!p) return;
+    for (void* q : p->allocations) cudaFree(q);
+    p->allocations.clear();
+    p->tw.release();
+}
+
+// Build the kernel-family table: for each k, K_k = H * g_k at every grid
+// displacement |x_a| <= n_a - 1 (a blur of one centred atom on the grid of
+// shape 2n - 1), placed for correlation on Pc and transformed.
+static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
+    const int K = p->K;
+    if (K == 0) return SFW_OK;
+    int n2[3];
+    for (int a = 0; a < 3; ++a) n2[a] = 2 * p->n[a] - 1;
+    BlurGeom g;
+    SFW_TRY(make_blur_geom(p->tw, n2, p->R, &g));
+    const long long Pc_tot = (long long)p->Pc[0] * p->Pc[1] * p->Pc[2];
+    const long long spec_elems = (long long)p->Pc[0] * p->Pc[1] * p->H2c;
+    const long long Pg_tot = (long long)g.P[0] * g.P[1] * g.P[2];
+    const long long Eg_tot = (long long)g.E[0] * g.E[1] * g.E[2];
+    const long long Ng_tot = (long long)n2[0] * n2[1] * n2[2];
+    // temporaries
+    std::vector<void*> tmp;
+    auto talloc = [&](void** q, size_t bytes) -> sfw_status {
+        cudaError_t e = cudaMalloc(q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SFW_ERR_ALLOC, "table build: cudaMalloc(%zu) failed", bytes);
+        }
+        tmp.push_back(*q);
+        return SFW_OK;
+    };
+    sfw_status st_ret = SFW_OK;
+    float2 *Hg = nullptr, *gA = nullptr, *gB = nullptr, *full = nullptr, *ftmp = nullptr;
+    float *fE = nullptr, *kx = nullptr, *wrapped = nullptr, *stats = nullptr;
+    float* atom = nullptr;
+    do {
+        const size_t gspec = (size_t)g.P[0] * g.P[1] * g.H2;
+        const size_t gbuf = blur_buf_elems(g) > gspec ? blur_buf_elems(g) : gspec;
+        if ((st_ret = talloc((void**)&Hg, sizeof(float2) * gspec))) break;
+        if ((st_ret = talloc((void**)&gA, sizeof(float2) * gbuf))) break;
+        if ((st_ret = talloc((void**)&gB, sizeof(float2) * gbuf))) break;
+        if ((st_ret = talloc((void**)&fE, sizeof(float) * (size_t)(Eg_tot > Pg_tot ? Eg_tot : Pg_tot)))) break;
+        if ((st_ret = talloc((void**)&kx, sizeof(float) * (size_t)Ng_tot))) break;
+        if ((st_ret = talloc((void**)&wrapped, sizeof(float) * (size_t)Pc_tot))) break;
+        if ((st_ret = talloc((void**)&full, sizeof(float2) * (size_t)K * spec_elems))) break;
+        if ((st_ret = talloc((void**)&ftmp, sizeof(float2) * (size_t)spec_elems))) break;
+        if ((st_ret = talloc((void**)&stats, sizeof(float) * 2))) break;
+        if ((st_ret = talloc((void**)&atom, sizeof(float) * 6))) break;
+        // H on the blur grid of the shape 2n - 1
+        if ((st_ret = launch_wrap_psf(p->psf, p->R, g.P, fE, st))) break;
+        if ((st_ret = fft3_forward(g.P, g.fac, g.tw, fE, gA, Hg, 1.0f / (float)Pg_tot, st))) break;
+        for (int k = 0; k < K && st_ret == SFW_OK; ++k) {
+            // one unit atom at the centre (n - 1) of the (2n - 1) grid
+            float h_atom[6] = {(float)(p->n[0] - 1), (float)(p->n[1] - 1), (float)(p->n[2] - 1),
+                               p->sigmas[k], p->ds[k], 1.0f};
+            cudaError_t e = cudaMemcpyAsync(atom, h_atom, sizeof(h_atom), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) {
+                st_ret = cuda_fail(e, "table atom upload");
+                break;
+            }
+            AtomsDev a;
+            a.N = 1;
+            a.m = atom;
+            a.sigma = atom + 3;
+            a.d = atom + 4;
+            a.w = atom + 5;
+            if ((st_ret = launch_render(a, g.E, g.R, p->eps, fE, st))) break;
+            C2RPass ep;
+            memset(&ep, 0, sizeof(ep));
+            ep.mode = C2R_STORE;
+            ep.scale = 1.f;
+            ep.out = kx;
+            if ((st_ret = blur_forward(g, fE, Hg, SPEC_C64, gA, gB, ep, st, nullptr))) break;
+            if ((st_ret = launch_wrap_kernel(kx, p->n, p->Pc, wrapped, st))) break;
+            if ((st_ret = fft3_forward(p->Pc, p->facc, p->twc, wrapped, ftmp, full + (size_t)k * spec_elems,
+                                       1.0f / (float)Pc_tot, st)))
+                break;
+            e = cudaStreamSynchronize(st);  // the atom slot is rewritten next iteration
+            if (e != cudaSuccess) {
+                st_ret = cuda_fail(e, "table build");
+                break;
+            }
+        }
+        if (st_ret) break;
+        // real spectra when the family is even (symmetric H): keep Re only
+        cudaMemsetAsync(stats, 0, sizeof(float) * 2, st);
+        if ((st_ret = launch_spec_stats(full, (long long)K * spec_elems, stats, st))) break;
+        float h_stats[2];
+        cudaError_t e = cudaMemcpyAsync(h_stats, stats, sizeof(h_stats), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            st_ret = cuda_fail(e, "table stats");
+            break;
+        }
+        p->real_table = h_stats[1] <= 1e-6f * h_stats[0];
+        int kind;
+        size_t esz;
+        if (p->precision == SFW_PREC_BF16) {
+            kind = p->real_table ? SPEC_RBF16 : SPEC_CBF16;
+            esz = p->real_table ? 2 : 4;
+        } else {
+            kind = p->real_table ? SPEC_R32 : SPEC_C64;
+            esz = p->real_table ? 4 : 8;
+        }
+        p->table_kind = kind;
+        p->table_bytes = esz * (size_t)K * spec_elems;
+        if ((st_ret = plan_alloc(p, &p->table, p->table_bytes))) break;
+        if ((st_ret = launch_spec_convert(full, (long long)K * spec_elems, kind, p->table, st))) break;
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) st_ret = cuda_fail(e, "table build");
+    } while (0);
+    cudaStreamSynchronize(st);
+    for (void* q : tmp) cudaFree(q);
+    return st_ret;
+}
+
+static sfw_status check_atoms(const sfw_atoms* a, bool need_nonempty) {
+    if (!a) return fail(SFW_ERR_ARG, "atoms is NULL");
+    if (a->N < 0 || a->N > 4096) return fail(SFW_ERR_ARG, "atom count %d outside [0, 4096]", a->N);
+    if (need_nonempty && a->N == 0) return fail(SFW_ERR_ARG, "atom count must be >= 1");
+    if (a->N > 0 && (!a->m || !a->sigma || !a->d || !a->w))
+        return fail(SFW_ERR_ARG, "atom arrays must be non-NULL");
+    return SFW_OK;
+}
+
+static AtomsDev to_dev(const sfw_atoms* a) {
+    AtomsDev d;
+    d.N = a->N;
+    d.m = a->m;
+    d.sigma = a->sigma;
+    d.d = a->d;
+    d.w = a->w;
+    return d;
+}
+
+extern "C" {
+
+const char* sfw_last_error(void) { return g_err; }
+
+int64_t sfw_launch_count(void) { return g_launches.load(); }
+
+const char* sfw_version(void) { return "sfw-gb300 0.1 (sm_103a)"; }
+
+sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
+    clear_error();
+    if (!desc || !out) return fail(SFW_ERR_ARG, "desc and out must be non-NULL");
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a) {
+        if (desc->n[a] < 4 || desc->n[a] > 1024) return fail(SFW_ERR_SHAPE, "n[%d]=%d outside [4, 1024]", a, desc->n[a]);
+        if (desc->R[a] < 0 || desc->R[a] > 64) return fail(SFW_ERR_SHAPE, "R[%d]=%d outside [0, 64]", a, desc->R[a]);
+    }
+    if (!desc->psf) return fail(SFW_ERR_ARG, "psf is NULL");
+    if (desc->n_sigma < 0 || desc->n_d < 0) return fail(SFW_ERR_ARG, "negative grid size");
+    const int K = desc->n_sigma * desc->n_d;
+    if (K > 0 && (!desc->sigmas || !desc->ds)) return fail(SFW_ERR_ARG, "grid arrays are NULL");
+    if (K > 256) return fail(SFW_ERR_SHAPE, "K=%d > 256 kernels", K);
+    for (int i = 0; i < desc->n_sigma; ++i)
+        if (!(desc->sigmas[i] >= 0.25f && desc->sigmas[i] <= 16.f)) return fail(SFW_ERR_ARG, "grid sigma outside [0.25, 16]");
+    for (int i = 0; i < desc->n_d; ++i)
+        if (!(desc->ds[i] >= 0.5f && desc->ds[i] <= 4.f)) return fail(SFW_ERR_ARG, "grid d outside [0.5, 4]");
+    if (desc->precision != SFW_PREC_FP32 && desc->precision != SFW_PREC_BF16)
+        return fail(SFW_ERR_ARG, "unknown precision %d", desc->precision);
+    if (!(desc->eps >= 0.f && desc->eps < 0.1f)) return fail(SFW_ERR_ARG, "eps outside [0, 0.1)");
+
+    sfw_plan* p = new (std::nothrow) sfw_plan();
+    if (!p) return fail(SFW_ERR_ALLOC, "host allocation");
+    p->eps = desc->eps > 0.f ? desc->eps : 1e-9f;
+    p->precision = desc->precision;
+    for (int a = 0; a < 3; ++a) {
+        p->n[a] = desc->n[a];
+        p->R[a] = desc->R[a];
+        p->E[a] = desc->n[a] + 2 * desc->R[a];
+    }
+    p->V = (long long)p->n[0] * p->n[1] * p->n[2];
+    p->VE = (long long)p->E[0] * p->E[1] * p->E[2];
+    p->K = K;
+    for (int i = 0; i < desc->n_sigma; ++i)
+        for (int j = 0; j < desc->n_d; ++j) {
+            p->sigmas.push_back(desc->sigmas[i]);
+            p->ds.push_back(desc->ds[j]);
+        }
+    if ((long long)K * p->V >= 0xffffffffll) {
+        delete p;
+        return fail(SFW_ERR_SHAPE, "K * V must stay below 2^32");
+    }
+    cudaStream_t st = nullptr;
+    sfw_status s = SFW_OK;
+    do {
+        if ((s = make_blur_geom(p->tw, p->n, p->R, &p->blur))) break;
+        if (K > 0) {
+            for (int a = 0; a < 3; ++a) {
+                p->Pc[a] = next_smooth_even(2 * p->n[a] - 1);
+                if (p->Pc[a] > kMaxLen) {
+                    s = fail(SFW_ERR_SHAPE, "certificate FFT length %d > %d", p->Pc[a], kMaxLen);
+                    break;
+                }
+                if (!factorize(p->Pc[a], &p->facc[a])) {
+                    s = fail(SFW_ERR_SHAPE, "cannot factor %d", p->Pc[a]);
+                    break;
+                }
+                if ((s = p->tw.get(p->Pc[a], &p->twc[a]))) break;
+            }
+            if (s) break;
+            if (p->n[2] > 256) {
+                s = fail(SFW_ERR_SHAPE, "certificate needs n[2] <= 256");
+                break;
+            }
+            p->H2c = p->Pc[2] / 2 + 1;
+        }
+        const int nh = (2 * p->R[0] + 1) * (2 * p->R[1] + 1) * (2 * p->R[2] + 1);
+        if ((s = plan_alloc_t(p, &p->psf, nh))) break;
+        cudaError_t e = cudaMemcpy(p->psf, desc->psf, sizeof(float) * nh, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            s = cuda_fail(e, "psf upload");
+            break;
+        }
+        const BlurGeom& g = p->blur;
+        const long long Ptot = (long long)g.P[0] * g.P[1] * g.P[2];
+        const size_t hs = (size_t)g.P[0] * g.P[1] * g.H2;
+        const size_t bb = blur_buf_elems(g);
+        if ((s = plan_alloc_t(p, &p->Hspec, hs))) break;
+        if ((s = plan_alloc_t(p, &p->bufA, bb > hs ? bb : hs))) break;
+        if ((s = plan_alloc_t(p, &p->bufB, bb > hs ? bb : hs))) break;
+        if ((s = plan_alloc_t(p, &p->fE, (size_t)(p->VE > Ptot ? p->VE : Ptot)))) break;
+        if ((s = plan_alloc_t(p, &p->bE, (size_t)p->VE))) break;
+        if ((s = plan_alloc_t(p, &p->r, (size_t)p->V))) break;
+        p->loss_parts_len = (int)(((long long)p->n[0] * p->n[1] + 15) / 16) + 16;
+        if ((s = plan_alloc_t(p, &p->loss_parts, (size_t)p->loss_parts_len))) break;
+        p->grad_parts_atoms = 4096;
+        if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;
+        if ((s = plan_alloc_t(p, &p->best_key, 2))) break;
+        p->red_scratch_len = 1 << 20;
+        if ((s = plan_alloc_t(p, &p->red_scratch, (size_t)p->red_scratch_len))) break;
+        if (K > 0) {
+            const size_t a_el = (size_t)K * p->n[0] * p->n[1] * p->H2c;
+            const size_t b_el = (size_t)p->n[0] * p->Pc[1] * p->H2c;
+            const size_t c_el = (size_t)K * p->n[0] * p->Pc[1] * p->H2c;
+            if ((s = plan_alloc_t(p, &p->cA, a_el))) break;
+            if ((s = plan_alloc_t(p, &p->cB, b_el))) break;
+            if ((s = plan_alloc_t(p, &p->cC, c_el))) break;
+        }
+        // H^ on the blur grid, scaled by 1/|P| (folds the inverse normalisation)
+        if ((s = launch_wrap_psf(p->psf, p->R, g.P, p->fE, st))) break;
+        if ((s = fft3_forward(g.P, g.fac, g.tw, p->fE, p->bufA, p->Hspec, 1.0f / (float)Ptot, st))) break;
+        if ((s = build_table(p, st))) break;
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) s = cuda_fail(e, "plan create");
+    } while (0);
+    if (s != SFW_OK) {
+        cudaDeviceSynchronize();
+        plan_free(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return SFW_OK;
+}
+
+sfw_status sfw_plan_destroy(sfw_plan* plan) {
+    clear_error();
+    if (!plan) return SFW_OK;
+    cudaDeviceSynchronize();
+    plan_free(plan);
+    delete plan;
+    return SFW_OK;
+}
+
+sfw_status sfw_plan_query(const sfw_plan* p, sfw_plan_info* info) {
+    clear_error();
+    if (!p || !info) return fail(SFW_ERR_ARG, "plan and info must be non-NULL");
+    for (int a = 0; a < 3; ++a) {
+        info->E[a] = p->E[a];
+        info->P_conv[a] = p->blur.P[a];
+        info->P_cert[a] = p->K ? p->Pc[a] : 0;
+    }
+    info->K = p->K;
+    info->real_table = p->real_table;
+    info->table_bytes = p->table_bytes;
+    info->workspace_bytes = p->ws_bytes - p->table_bytes;
+    return SFW_OK;
+}
+
+sfw_status sfw_forward(sfw_plan* p, const sfw_atoms* atoms, float* y_out, void* stream) {
+    clear_error();
+    if (!p || !y_out) return fail(SFW_ERR_ARG, "plan and y_out must be non-NULL");
+    SFW_TRY(check_atoms(atoms, false));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AtomsDev a = to_dev(atoms);
+    SFW_TRY(launch_render(a, p->E, p->R, p->eps, p->fE, st));
+    C2RPass ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.mode = C2R_STORE;
+    ep.scale = 1.f;
+    ep.out = y_out;
+    return blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, nullptr);
+}
+
+sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                               double* loss_out, double* grad_out, float* residual_out,
+                               void* stream) {
+    clear_error();
+    if (!p || !y || !loss_out || !grad_out) return fail(SFW_ERR_ARG, "plan, y, loss_out, grad_out must be non-NULL");
+    SFW_TRY(check_atoms(atoms, true));
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and >= 0");
+    if (atoms->N > p->grad_parts_atoms) return fail(SFW_ERR_ARG, "too many atoms");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AtomsDev a = to_dev(atoms);
+    float* r = residual_out ? residual_out : p->r;
+    SFW_TRY(launch_render(a, p->E, p->R, p->eps, p->fE, st));
+    C2RPass ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.mode = C2R_RESIDUAL;
+    ep.scale = 1.f;
+    ep.out = r;
+    ep.y = y;
+    ep.partials = p->loss_parts;
+    int blocks = 0;
+    SFW_TRY(blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, &blocks));
+    if (blocks > p->loss_parts_len) return fail(SFW_ERR_SHAPE, "loss partial buffer too small");
+    SFW_TRY(launch_loss_finalize(p->loss_parts, blocks, a, lambda, loss_out, st));
+    SFW_TRY(blur_transpose(p->blur, r, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
+    return launch_atom_grad(a, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, grad_out, st);
+}
+
+sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambda, float* eta_out,
+                                float* max_out, int32_t* argk_out, float* best_val,
+                                int64_t* best_idx, void* stream) {
+    clear_error();
+    if (!p || !residual) return fail(SFW_ERR_ARG, "plan and residual must be non-NULL");
+    if (p->K == 0) return fail(SFW_ERR_ARG, "plan has no certificate grid");
+    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+    const int P0 = p->Pc[0], P1 = p->Pc[1], P2 = p->Pc[2], H2 = p->H2c;
+    const int K = p->K;
+    {   // axis 2 forward of r: (n0, n1, n2) -> (n0, n1, H2)
+        R2CPass q;
+        q.in = residual;
+        q.lin = ls((long long)n1 * n2, n2, 1, n1);
+        q.nlines = (long long)n0 * n1;
+        q.in_off = 0;
+        q.in_len = n2;
+        q.L = P2;
+        q.fac = p->facc[2];
+        q.tw = p->twc[2];
+        q.out = p->cA;
+        q.lout = ls((long long)n1 * H2, H2, 1, n1);
+        SFW_TRY(launch_r2c(q, st));
+    }
+    {   // axis 1 forward: -> (n0, P1, H2)
+        C2CPass q;
+        q.in = p->cA;
+        q.out = p->cB;
+        q.lin = ls((long long)n1 * H2, 1, H2, H2);
+        q.lout = ls((long long)P1 * H2, 1, H2, H2);
+        q.nlines = (long long)n0 * H2;
+        q.L = P1;
+        q.in_off = 0;
+        q.in_len = n1;
+        q.out_off = 0;
+        q.out_len = P1;
+        q.dir = -1;
+        q.scale = 1.f;
+        q.fac = p->facc[1];
+        q.tw = p->twc[1];
+        SFW_TRY(launch_c2c(q, st));
+    }
+    {   // axis 0: forward once, then for each kernel k: times table_k, inverse -> (K, n0, P1, H2)
+        MulPass q;
+        const long long nl = (long long)P1 * H2;
+        q.in = p->cB;
+        q.lin = ls(0, 1, nl, nl);
+        q.in_off = 0;
+        q.in_len = n0;
+        q.nlines = nl;
+        q.L = P0;
+        q.fac = p->facc[0];
+        q.tw = p->twc[0];
+        q.spec = p->table;
+        q.lspec = ls(0, 1, nl, nl);
+        q.spec_stride = (long long)P0 * nl;
+        q.nspec = K;
+        q.spec_kind = p->table_kind;
+        q.conj_spec = 0;
+        q.out = p->cC;
+        q.lout = ls(0, 1, nl, nl);
+        q.out_stride = (long long)n0 * nl;
+        q.out_off = 0;
+        q.out_len = n0;
+        SFW_TRY(launch_mul(q, st));
+    }
+    {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
+        C2CPass q;
+        q.in = p->cC;
+        q.out = p->cA;
+        q.lin = ls((long long)P1 * H2, 1, H2, H2);
+        q.lout = ls((long long)n1 * H2, 1, H2, H2);
+        q.nlines = (long long)K * n0 * H2;
+        q.L = P1;
+        q.in_off = 0;
+        q.in_len = P1;
+        q.out_off = 0;
+        q.out_len = n1;
+        q.dir = 1;
+        q.scale = 1.f;
+        q.fac = p->facc[1];
+        q.tw = p->twc[1];
+        SFW_TRY(launch_c2c(q, st));
+    }
+    if (best_val || best_idx) {
+        cudaError_t e = cudaMemsetAsync(p->best_key, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    C2RPass q;
+    memset(&q, 0, sizeof(q));
+    q.in = p->cA;
+    q.lin = ls((long long)n1 * H2, H2, 1, n1);
+    q.nlines = (long long)n0 * n1;
+    q.in_spec_stride = (long long)n0 * n1 * H2;
+    q.nspec = K;
+    q.L = P2;
+    q.fac = p->facc[2];
+    q.tw = p->twc[2];
+    q.out_off = 0;
+    q.out_len = n2;
+    q.lout = ls((long long)n1 * n2, n2, 1, n1);
+    q.scale = (float)(1.0 / lambda);
+    q.mode = C2R_CERTMAX;
+    q.eta_out = eta_out;
+    q.V = p->V;
+    q.max_out = max_out;
+    q.argk_out = argk_out;
+    q.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+    SFW_TRY(launch_c2r(q, st, nullptr));
+    if (best_val || best_idx) SFW_TRY(launch_key_decode(p->best_key, best_val, best_idx, st));
+    return SFW_OK;
+}
+
+sfw_status sfw_eta_points(sfw_plan* p, const float* residual, double lambda, int P,
+                          const float* theta, double* eta_out, double* grad_out, void* stream) {
+    clear_error();
+    if (!p || !residual || !theta || !eta_out) return fail(SFW_ERR_ARG, "plan, residual, theta, eta_out must be non-NULL");
+    if (P < 1 || P > p->grad_parts_atoms) return fail(SFW_ERR_ARG, "P must be in [1, %d]", p->grad_parts_atoms);
+    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SFW_TRY(blur_transpose(p->blur, residual, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
+    AtomsDev pts;
+    pts.N = P;
+    pts.m = theta;
+    pts.sigma = theta + 3;
+    pts.d = theta + 4;
+    pts.w = theta + 3;  // unused by the sums
+    pts.ms = 5;
+    pts.ps = 5;
+    return launch_eta_points(pts, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, eta_out,
+                             grad_out, st);
+}
+
+// Test hook (not part of the public header): copy an internal plan buffer to
+// host memory.  which: 0 = rendered atoms on E, 1 = H spectrum, 2 = back-projection on E.
+sfw_status sfw_debug_read(const sfw_plan* p, int which, void* host, size_t bytes) {
+    clear_error();
+    if (!p || !host) return fail(SFW_ERR_ARG, "NULL");
+    const void* src = which == 0 ? (const void*)p->fE : which == 1 ? (const void*)p->Hspec : (const void*)p->bE;
+    SFW_CUDA(cudaDeviceSynchronize());
+    SFW_CUDA(cudaMemcpy(host, src, bytes, cudaMemcpyDeviceToHost));
+    return SFW_OK;
+}
+
+sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_out,
+                      int64_t* idx_out, void* stream) {
+    clear_error();
+    if (!values || !val_out || !idx_out) return fail(SFW_ERR_ARG, "pointers must be non-NULL");
+    if (count < 1 || count >= 0xffffffffll) return fail(SFW_ERR_ARG, "count must be in [1, 2^32 - 1)");
+    if (topk < 1 || topk > 64 || topk > count) return fail(SFW_ERR_ARG, "topk must be in [1, min(64, count)]");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // scratch: a small per-device buffer owned by the library (grown on demand)
+    static thread_local unsigned long long* scratch = nullptr;
+    static thread_local long long scratch_len = 0;
+    static thread_local int scratch_dev = -1;
+    int dev = 0;
+    SFW_CUDA(cudaGetDevice(&dev));
+    const long long blocks = (count + 4095) / 4096;
+    const long long need = topk == 1 ? 1024 : 2 * (blocks * topk + 64);
+    if (scratch_len < need || scratch_dev != dev) {
+        if (scratch) {
+            cudaStreamSynchronize(st);
+            cudaFree(scratch);
+        }
+        scratch = nullptr;
+        scratch_len = 0;
+        cudaError_t e = cudaMalloc(&scratch, sizeof(unsigned long long) * (size_t)need);
+        if (e != cudaSuccess) return cuda_fail(e, "argmax scratch");
+        scratch_len = need;
+        scratch_dev = dev;
+    }
+    if (topk == 1) {
+        int nb = (int)((count + 255) / 256);
+        if (nb > 1024) nb = 1024;
+        SFW_TRY(launch_argmax_keys(values, count, scratch, nb, st));
+        return launch_argmax_final(scratch, nb, val_out, idx_out, st);
+    }
+    return launch_topk(values, count, topk, scratch, scratch_len, val_out, idx_out, st);
+}
+
+}  // extern "C"

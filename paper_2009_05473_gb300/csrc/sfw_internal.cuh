@@ -1,0 +1,240 @@
+// Internal declarations shared by the CUDA translation units of libsfw.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <vector>
+
+#include "sfw.h"
+
+namespace sfw {
+
+// ------------------------------------------------------------------ errors
+sfw_status fail(sfw_status st, const char* fmt, ...);
+sfw_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define SFW_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t e__ = (call);                             \
+        if (e__ != cudaSuccess) return ::sfw::cuda_fail(e__, #call); \
+    } while (0)
+
+#define SFW_TRY(expr)                         \
+    do {                                      \
+        sfw_status s__ = (expr);              \
+        if (s__ != SFW_OK) return s__;        \
+    } while (0)
+
+// Kernels launched by the library (process-wide counter).
+extern std::atomic<int64_t> g_launches;
+inline void counted_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// Check the launch that was just issued.
+sfw_status launch_check(const char* what);
+
+// ------------------------------------------------------------------ FFT plans
+constexpr int kMaxFactors = 16;
+constexpr int kMaxLen = 1024;
+
+struct Factors {
+    int n;
+    int r[kMaxFactors];
+};
+
+// Split L into radices 8, 4, 2, 3, 5 (false if another prime divides L).
+bool factorize(int L, Factors* f);
+// Smallest 2-3-5 smooth even integer >= x.
+int next_smooth_even(int x);
+
+// Line addressing of a batched 1-D transform: line l -> a = l / B, b = l % B,
+// base offset a * Sa + b * Sb; consecutive points of a line are Sj apart.
+struct LineSet {
+    long long Sa, Sb, Sj;
+    long long B;
+};
+
+__host__ __device__ inline long long line_offset(const LineSet& s, long long l) {
+    long long a = l / s.B;
+    long long b = l - a * s.B;
+    return a * s.Sa + b * s.Sb;
+}
+
+// Twiddle tables exp(-2 pi i j / L), j < L, one per length (device, float2).
+struct TwiddleCache {
+    std::map<int, float2*> tables;
+    sfw_status get(int L, const float2** out);
+    void release();
+};
+
+// Spectrum element formats for the fused multiply.
+enum SpecKind { SPEC_C64 = 0, SPEC_R32 = 1, SPEC_CBF16 = 2, SPEC_RBF16 = 3 };
+
+// ---- pass descriptors (kernel parameters, by value) ----
+
+// Complex-to-complex transform along a strided axis, zero-padded input rows
+// [in_off, in_off + in_len), output rows [out_off, out_off + out_len).
+struct C2CPass {
+    const float2* in;
+    float2* out;
+    LineSet lin, lout;
+    long long nlines;
+    int L, in_off, in_len, out_off, out_len;
+    int dir;  // -1 forward, +1 inverse
+    float scale;
+    Factors fac;
+    const float2* tw;
+};
+
+// Forward transform along a strided axis, then for each of nspec spectra:
+// multiply, inverse transform and write the cropped rows.
+struct MulPass {
+    const float2* in;
+    LineSet lin;
+    int in_off, in_len;
+    long long nlines;
+    int L;
+    Factors fac;
+    const float2* tw;
+    const void* spec;
+    LineSet lspec;
+    long long spec_stride;  // elements between consecutive spectra
+    int nspec;
+    int spec_kind;
+    int conj_spec;
+    float2* out;
+    LineSet lout;
+    long long out_stride;   // elements between consecutive outputs
+    int out_off, out_len;
+};
+
+// Real lines along the contiguous axis -> half spectra (L/2 + 1 points).
+struct R2CPass {
+    const float* in;
+    LineSet lin;          // real lines, Sj = 1
+    long long nlines;     // real lines
+    int in_off, in_len;
+    int L;
+    Factors fac;
+    const float2* tw;
+    float2* out;
+    LineSet lout;         // half-spectrum lines, Sj = 1
+};
+
+enum C2RMode { C2R_STORE = 0, C2R_RESIDUAL = 1, C2R_CERTMAX = 2 };
+
+// Half spectra -> real lines along the contiguous axis, cropped rows, with an
+// epilogue: store, residual + squared-norm partials, or certificate max.
+struct C2RPass {
+    const float2* in;
+    LineSet lin;          // half-spectrum lines, Sj = 1
+    long long nlines;     // real output lines
+    long long in_spec_stride;
+    int nspec;
+    int L;
+    Factors fac;
+    const float2* tw;
+    int out_off, out_len;
+    LineSet lout;         // real lines, Sj = 1 (also voxel index for dense outputs)
+    float scale;
+    int mode;
+    float* out;           // STORE: output; RESIDUAL: residual (may be NULL)
+    const float* y;       // RESIDUAL: observation
+    double* partials;     // RESIDUAL: one double per block
+    float* eta_out;       // CERTMAX: K x V or NULL
+    long long V;
+    float* max_out;       // CERTMAX: V or NULL
+    int* argk_out;        // CERTMAX: V or NULL
+    unsigned long long* best_key;  // CERTMAX: one key or NULL
+};
+
+// launchers (fft_kernels.cu)
+sfw_status launch_c2c(const C2CPass& p, cudaStream_t st);
+sfw_status launch_mul(const MulPass& p, cudaStream_t st);
+sfw_status launch_r2c(const R2CPass& p, cudaStream_t st);
+// returns the number of blocks used (for the residual partials) via *blocks
+sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks);
+int c2r_blocks(const C2RPass& p);
+
+// ------------------------------------------------------------------ atoms (atoms.cu)
+struct AtomsDev {
+    int N;
+    const float* m;      // atom i at m[i * ms + a]
+    const float* sigma;  // atom i at sigma[i * ps] (same for d, w)
+    const float* d;
+    const float* w;
+    int ms = 3;
+    int ps = 1;
+};
+
+// f on the box of shape E (dense), E index t <-> grid coordinate t - R.
+sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], float eps, float* f,
+                         cudaStream_t st);
+// Per-atom adjoint sums -> gradient (6N doubles) given b on E.
+constexpr int kGradChunks = 32;
+sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
+                            const float* b, double lambda, double* partials, double* grad,
+                            cudaStream_t st);
+// eta(theta_p) = <g_p, b>/lambda and its gradient for P parameter rows (m, sigma, d).
+sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3], float eps,
+                             const float* b, double lambda, double* partials, double* eta,
+                             double* grad, cudaStream_t st);
+// sum_n w_n added to the loss: loss = 0.5 * sum(partials) + lambda * sum w
+sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
+                                double lambda, double* loss, cudaStream_t st);
+
+// ------------------------------------------------------------------ misc kernels (reduce.cu)
+// dst[p] = src box value with circular placement (see definitions in reduce.cu)
+sfw_status launch_wrap_psf(const float* psf, const int R[3], const int P[3], float* out,
+                           cudaStream_t st);
+sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int P[3], float* out,
+                              cudaStream_t st);
+sfw_status launch_argmax_keys(const float* v, long long count, unsigned long long* partial,
+                              int nblocks, cudaStream_t st);
+sfw_status launch_argmax_final(const unsigned long long* partial, int n, float* val, int64_t* idx,
+                               cudaStream_t st);
+sfw_status launch_topk(const float* v, long long count, int topk, unsigned long long* scratch,
+                       long long scratch_len, float* val_out, int64_t* idx_out, cudaStream_t st);
+sfw_status launch_key_decode(const unsigned long long* key, float* val, int64_t* idx,
+                             cudaStream_t st);
+sfw_status launch_spec_stats(const float2* s, long long count, float* stats /*2 floats*/,
+                             cudaStream_t st);
+sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out,
+                               cudaStream_t st);
+
+// Monotone map of a float to an unsigned key (NaN handled by callers).
+__host__ __device__ inline unsigned int float_order_key(float v) {
+    unsigned int u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(v);
+#else
+    union { float f; unsigned int i; } c;
+    c.f = v;
+    u = c.i;
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ inline float float_from_order_key(unsigned int k) {
+    unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    union { float f; unsigned int i; } c;
+    c.i = u;
+    return c.f;
+#endif
+}
+
+// Candidate key: value order in the high word, inverted index in the low word,
+// so that max(key) = largest value, then lowest index.  NaN -> all ones.
+__host__ __device__ inline unsigned long long candidate_key(float v, unsigned long long idx) {
+    if (v != v) return ~0ull;
+    return ((unsigned long long)float_order_key(v) << 32) |
+           (unsigned long long)(0xffffffffu - (unsigned int)idx);
+}
+
+}  // namespace sfw

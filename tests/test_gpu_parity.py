@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances (FP32 path): 1e-5 relative to the largest magnitude of the compared
+quantity (``|gpu - oracle|_inf / |oracle|_inf``) for the forward operator, the grid
+certificate and the loss; the argmax must be the same flat index k*V + lin(m)."""
+
+import numpy as np
+import pytest
+
+import sfw_inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+def _rel_inf(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def sfw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2009_05473_gb300 as m
+    m.build_library()
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+# ragged sizes: not multiples of any tile, odd and even axes, unequal R
+SMALL_CASES = [
+    ((13, 17, 22), (2, 3, 4), (1.1, 1.3, 1.8), 3),
+    ((16, 16, 16), (3, 3, 3), (1.5, 1.5, 1.5), 2),
+    ((9, 20, 11), (1, 4, 2), (0.9, 1.7, 1.2), 4),
+]
+
+
+def _case(oracle_mod, n, R, psf_sigma, N, seed=0, kernels_s=(1.0, 2.0, 3.0), kernels_d=(1.5, 2.0, 2.5)):
+    vol = sfw_inputs.make_volume("t", n, R, psf_sigma, N, seed=seed, grid_sigmas=kernels_s,
+                                 grid_ds=kernels_d, min_sep=2.0)
+    rng = np.random.default_rng(seed + 100)
+    # an asymmetric PSF exercises the complex (non-even) spectra
+    psf = vol.psf * (1.0 + 0.3 * rng.random(vol.psf.shape))
+    psf /= psf.sum()
+    vol.psf = psf
+    y = oracle_mod.observe(vol, fft=False)
+    return vol, y
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_forward_matches_oracle(sfw, oracle_mod, case):
+    n, R, ps, N = case
+    vol, _ = _case(oracle_mod, n, R, ps, N)
+    plan = sfw.Plan(n, R, vol.psf)
+    atoms = sfw.AtomSet.from_numpy(vol.m, vol.sigma, vol.d, vol.w)
+    y = plan.forward(atoms).cpu().numpy()
+    ref = oracle_mod.forward(n, R, vol.psf, vol.m, vol.sigma, vol.d, vol.w)
+    assert _rel_inf(y, ref) <= RTOL
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_certificate_grid_matches_definition(sfw, oracle_mod, torch_mod, case):
+    """eta_k(m) by FFT correlation with the kernel-family table == the direct definition of
+    Eq. 5 at every voxel (faces included) and kernel; argmax == brute-force scan."""
+    n, R, ps, N = case
+    vol, y = _case(oracle_mod, n, R, ps, N)
+    kernels = vol.grid_kernels()
+    lam = oracle_mod.lambda_rule(n, R, vol.psf, y, kernels, fft=False)
+    # residual of a perturbed measure, so that eta has both signs
+    r = y - oracle_mod.forward(n, R, vol.psf, vol.m[:1], vol.sigma[:1], vol.d[:1], vol.w[:1])
+    plan = sfw.Plan(n, R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+    assert not plan.info["real_table"]
+    out = plan.certificate(torch_mod.tensor(r, dtype=torch_mod.float32, device="cuda"), lam,
+                           want_eta=True)
+    eta = out["eta"].cpu().numpy()
+    ref = oracle_mod.eta_grid(n, R, vol.psf, r.astype(np.float32).astype(np.float64), lam, kernels)
+    assert _rel_inf(eta, ref) <= RTOL
+    assert int(out["best_idx"].item()) == int(np.argmax(eta))
+    flat = int(np.argmax(ref))
+    assert int(out["best_idx"].item()) == flat or abs(eta.ravel()[flat] - eta.max()) <= RTOL * np.abs(ref).max()
+    mx = out["max"].cpu().numpy()
+    ak = out["argk"].cpu().numpy()
+    np.testing.assert_array_equal(mx, eta.max(axis=0))
+    np.testing.assert_array_equal(ak, eta.argmax(axis=0))
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_slide_loss_grad_matches_oracle(sfw, oracle_mod, torch_mod, case):
+    n, R, ps, N = case
+    vol, y = _case(oracle_mod, n, R, ps, N)
+    lam = 0.37
+    # evaluate away from the truth (perturbed atoms) so that every gradient term is active
+    rng = np.random.default_rng(7)
+    m = vol.m + rng.normal(0, 0.3, vol.m.shape)
+    s = vol.sigma * 1.1
+    d = np.clip(vol.d + 0.1, 1.3, 2.9)
+    w = vol.w * 0.9
+    plan = sfw.Plan(n, R, vol.psf)
+    atoms = sfw.AtomSet.from_numpy(m, s, d, w)
+    # oracle on the FP32-rounded parameters the GPU sees
+    m32, s32, d32, w32 = (np.asarray(a, np.float32).astype(np.float64) for a in (m, s, d, w))
+    y32 = y.astype(np.float32).astype(np.float64)
+    C, g, r = oracle_mod.loss_and_grad(n, R, vol.psf, y32, m32, s32, d32, w32, lam)
+    loss, grad, res = plan.slide_loss_grad(torch_mod.tensor(y32, dtype=torch_mod.float32, device="cuda"),
+                                           atoms, lam, want_residual=True)
+    assert abs(loss.item() - C) <= RTOL * abs(C)
+    assert _rel_inf(res.cpu().numpy(), r) <= RTOL * 10
+    gg = grad.cpu().numpy()
+    assert _rel_inf(gg, g) <= 1e-4
+    # each block of 6 (m, sigma, d, w) on its own scale
+    Nn = w.size
+    for blk in (slice(0, 3 * Nn), slice(3 * Nn, 4 * Nn), slice(4 * Nn, 5 * Nn), slice(5 * Nn, 6 * Nn)):
+        assert _rel_inf(gg[blk], g[blk]) <= 1e-3
+
+
+def test_eta_points_match_oracle(sfw, oracle_mod, torch_mod):
+    n, R, ps, N = SMALL_CASES[0]
+    vol, y = _case(oracle_mod, n, R, ps, N)
+    plan = sfw.Plan(n, R, vol.psf)
+    th = np.concatenate([vol.m + 0.37, (vol.sigma * 0.9)[:, None], (vol.d * 1.05)[:, None]], 1)
+    lam = 0.5
+    y32 = y.astype(np.float32).astype(np.float64)
+    th32 = th.astype(np.float32).astype(np.float64)
+    b = oracle_mod.backproject(n, R, vol.psf, y32)
+    e_ref, g_ref = oracle_mod.eta_points(n, R, b, lam, th32, with_grad=True)
+    e, g = plan.eta_points(torch_mod.tensor(y32, dtype=torch_mod.float32, device="cuda"), lam, th)
+    assert _rel_inf(e.cpu().numpy(), e_ref) <= RTOL
+    assert _rel_inf(g.cpu().numpy(), g_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("count", [1, 37, 4096, 100003, 3 * 2 ** 20 + 5])
+def test_argmax_topk_bruteforce_with_ties(sfw, oracle_mod, torch_mod, count):
+    rng = np.random.default_rng(count)
+    v = rng.standard_normal(count).astype(np.float32)
+    if count > 10:
+        top = v.max() + 1.0
+        picks = rng.choice(count, 6, replace=False)
+        v[picks] = top
+    dv = torch_mod.tensor(v, device="cuda")
+    val, idx = sfw.argmax(dv, 1)
+    assert int(idx.item()) == oracle_mod.argmax(v.astype(np.float64)) == int(np.argmax(v))
+    assert float(val.item()) == float(v.max())
+    k = min(64, count)
+    val, idx = sfw.argmax(dv, k)
+    order = np.lexsort((np.arange(count), -v.astype(np.float64)))[:k]   # value desc, index asc
+    np.testing.assert_array_equal(idx.cpu().numpy(), order)
+    np.testing.assert_array_equal(val.cpu().numpy(), v[order])
+
+
+def test_argmax_nan_is_reported(sfw, torch_mod):
+    v = torch_mod.zeros(1000, device="cuda")
+    v[417] = float("nan")
+    val, idx = sfw.argmax(v, 1)
+    assert int(idx.item()) == -1
+    val, idx = sfw.argmax(v, 8)
+    assert int(idx[0].item()) == -1
+
+
+def test_certificate_nan_residual_reports_minus_one(sfw, oracle_mod, torch_mod):
+    n, R, ps, N = SMALL_CASES[1]
+    vol, y = _case(oracle_mod, n, R, ps, N)
+    plan = sfw.Plan(n, R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+    r = torch_mod.tensor(y, dtype=torch_mod.float32, device="cuda")
+    r[3, 4, 5] = float("nan")
+    out = plan.certificate(r, 1.0)
+    assert int(out["best_idx"].item()) == -1
