@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark of the sliding Frank-Wolfe hot path on one GB300 per rank.
+
+One step = one SFW iteration's data-parallel hot path on the 64^3 workload
+(PSF sigma (1.5, 1.5, 3) on 15x15x31, N = 10 atoms, certificate grid of 5 sigma
+x 3 d = 15 kernels):
+  1. sliding-step loss and adjoint gradient at the current atoms (render on E,
+     blur, residual + loss, transposed blur, per-atom adjoint sums);
+  2. grid certificate of the new residual over all voxels x 15 kernels, with
+     the fused device argmax (the seed of the next local ascent).
+Metric: eta-grid candidates/s = V K / step time (also reported: steps/s,
+i.e. SFW iterations/s of this hot path).
+
+The timed region replays a CUDA graph of the step; L2 (129 MB) is flushed by a
+256 MB write between steps, outside the per-step CUDA events.  The library
+records graph event nodes around each kernel, so every kernel's duration is
+measured inside the timed region (roofline of the dominant kernel).
+`--impl reference` times the FP64 CPU oracle on the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sfw_inputs  # noqa: E402
+
+WORKLOAD = "vol64_aniso_n10_k15"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline model
+
+def algorithmic_bytes(tag: str, plan, vol) -> float:
+    """Bytes a pass must read and write (its inputs and outputs, once), per launch."""
+    n0, n1, n2 = vol.n
+    V = n0 * n1 * n2
+    E = plan.info["E"]
+    VE = E[0] * E[1] * E[2]
+    P = plan.info["P_conv"]
+    H2 = P[2] // 2 + 1
+    Pc = plan.info["P_cert"]
+    H2c = Pc[2] // 2 + 1
+    K = plan.K
+    c8 = 8
+    esz = (4 if plan.info["real_table"] else 8) // (2 if plan.precision == "bf16" else 1)
+    table = {
+        "cert_r2c": V * 4 + n0 * n1 * H2c * c8,
+        "cert_c2c_fwd": n0 * n1 * H2c * c8 + n0 * Pc[1] * H2c * c8,
+        "cert_axis0": n0 * Pc[1] * H2c * c8 + K * Pc[0] * Pc[1] * H2c * esz + K * n0 * Pc[1] * H2c * c8,
+        "cert_c2c_inv": K * n0 * Pc[1] * H2c * c8 + K * n0 * n1 * H2c * c8,
+        "cert_c2r_max": K * n0 * n1 * H2c * c8 + V * 8,
+        "blur_r2c": VE * 4 + E[0] * E[1] * H2 * c8,
+        "blur_c2c_fwd": E[0] * E[1] * H2 * c8 + E[0] * P[1] * H2 * c8,
+        "blur_axis0": E[0] * P[1] * H2 * c8 + P[0] * P[1] * H2 * c8 + n0 * P[1] * H2 * c8,
+        "blur_c2c_inv": n0 * P[1] * H2 * c8 + n0 * n1 * H2 * c8,
+        "blur_c2r": n0 * n1 * H2 * c8 + V * 8,
+        "bp_r2c": V * 4 + n0 * n1 * H2 * c8,
+        "bp_c2c_fwd": n0 * n1 * H2 * c8 + n0 * P[1] * H2 * c8,
+        "bp_axis0": n0 * P[1] * H2 * c8 + P[0] * P[1] * H2 * c8 + E[0] * P[1] * H2 * c8,
+        "bp_c2c_inv": E[0] * P[1] * H2 * c8 + E[0] * E[1] * H2 * c8,
+        "bp_c2r": E[0] * E[1] * H2 * c8 + VE * 4,
+        "k_render": VE * 4,
+    }
+    return float(table.get(tag, 0.0))
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2009_05473_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2009_05473_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(tag: str):
+    """DRAM bytes per launch of `tag` from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except ValueError:
+        return None
+    if rec.get("source_digest") != source_digest() or rec.get("workload") != WORKLOAD:
+        return None
+    return rec.get("bytes_per_launch", {}).get(tag)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import paper_2009_05473_gb300 as sfw
+    if rank == 0:
+        sfw.build_library()
+    if world > 1:
+        dist.barrier()
+
+    # each replica solves its own synthetic volume (seed = rank): replicas only
+    vol = sfw_inputs.WORKLOADS[args.workload](seed=rank)
+    plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+    V, K = vol.V, plan.K
+    dev = torch.device("cuda", local_rank)
+
+    # observation y = Phi mu* + noise, made on the device by the library's own forward operator
+    truth = sfw.AtomSet.from_numpy(vol.m, vol.sigma, vol.d, vol.w, device=dev)
+    y = plan.forward(truth)
+    y += vol.noise_frac * y.max() * torch.tensor(vol.noise, dtype=torch.float32, device=dev)
+    # lambda = 0.05 * max over the grid of Phi^T y  (first certificate max = 20)
+    c0 = plan.certificate(y, 1.0, want_max=False)
+    lam = 0.05 * float(c0["best_val"].item())
+    # the current iterate of a sliding step: atoms near, not at, the truth
+    rng = np.random.default_rng(1000 + rank)
+    est = sfw.AtomSet.from_numpy(vol.m + rng.normal(0, 0.4, vol.m.shape), vol.sigma * 1.05,
+                                 np.clip(vol.d + 0.05, 1.3, 2.9), vol.w * 0.9, device=dev)
+
+    bufs = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
+            "grad": torch.empty(6 * vol.N, dtype=torch.float64, device=dev),
+            "residual": torch.empty(vol.n, dtype=torch.float32, device=dev)}
+    cbufs = {"max": torch.empty(vol.n, dtype=torch.float32, device=dev),
+             "argk": torch.empty(vol.n, dtype=torch.int32, device=dev),
+             "best_val": torch.empty(1, dtype=torch.float32, device=dev),
+             "best_idx": torch.empty(1, dtype=torch.int64, device=dev)}
+
+    def step():
+        plan.slide_loss_grad(y, est, lam, want_residual=True, out=bufs)
+        plan.certificate(bufs["residual"], lam, out=cbufs)
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (also sets every kernel attribute before capture)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # capture one step; the library's profiler puts event-record nodes around every kernel,
+    # so each replay times each kernel (collected after every timed replay)
+    cap_stream = torch.cuda.Stream(device=dev)
+    graph = torch.cuda.CUDAGraph()
+    sfw._abi.sfw_profile_start(256)
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph, stream=cap_stream):
+            step()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        flush.fill_(1.0)
+        graph.replay()
+    torch.cuda.synchronize()
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernels_per_step = None
+    with ClockSampler(local_rank) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))            # evict L2 between steps (outside the step events)
+            ev_s[i].record()
+            graph.replay()
+            ev_e[i].record()
+            ev_e[i].synchronize()
+            sfw._abi.sfw_profile_collect()   # kernel durations of this replay
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        if world > 1:
+            dist.barrier()
+    prof = sfw._abi.sfw_profile_stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
+    t_ms = float(np.sum(step_ms))
+    # one graph replay launches the kernels that one captured step launched
+    kernels_per_step = int(sum(v["launches"] for v in prof.values()) // max(1, args.steps))
+    gpu_launches = kernels_per_step * args.steps
+    if world > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_ms
+    cands = V * K
+    value = world * args.steps * cands / (t_max / 1e3)
+
+    # roofline of the dominant kernel (largest total time in the timed region)
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    tag, rec = dom
+    avg_s = rec["ms"] / rec["launches"] / 1e3
+    peak, peak_kind = measured_peaks()
+    alg = algorithmic_bytes(tag, plan, vol)
+    achieved = alg / avg_s / 1e9
+    traffic = ncu_traffic(tag)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timing
+    y_host = y.cpu().pin_memory()
+    p_host = {k: getattr(est, k).cpu().pin_memory() for k in ("m", "sigma", "d", "w")}
+    y_dev = torch.empty_like(y)
+    a_dev = sfw.AtomSet(*(torch.empty_like(getattr(est, k)) for k in ("m", "sigma", "d", "w")))
+    out_host = {"loss": torch.empty(1, dtype=torch.float64).pin_memory(),
+                "grad": torch.empty(6 * vol.N, dtype=torch.float64).pin_memory(),
+                "best_val": torch.empty(1, dtype=torch.float32).pin_memory(),
+                "best_idx": torch.empty(1, dtype=torch.int64).pin_memory()}
+    h2d = y_host.numel() * 4 + sum(t.numel() * 4 for t in p_host.values())
+    d2h = 8 + 8 * 6 * vol.N + 4 + 8
+    e2e_t = 0.0
+    for i in range(args.e2e_steps + 3):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y_dev.copy_(y_host, non_blocking=True)
+        for k in ("m", "sigma", "d", "w"):
+            getattr(a_dev, k).copy_(p_host[k], non_blocking=True)
+        loss, grad, r = plan.slide_loss_grad(y_dev, a_dev, lam, want_residual=True, out=bufs)
+        c = plan.certificate(r, lam, want_max=False, out=cbufs)
+        out_host["loss"].copy_(loss, non_blocking=True)
+        out_host["grad"].copy_(grad, non_blocking=True)
+        out_host["best_val"].copy_(c["best_val"], non_blocking=True)
+        out_host["best_idx"].copy_(c["best_idx"], non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= 3:
+            e2e_t += time.perf_counter() - t0
+    e2e_value = world * args.e2e_steps * cands / e2e_t if world == 1 else None
+    if world > 1:
+        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_value = world * args.e2e_steps * cands / float(tt.item())
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": "eta-grid candidates/s (grid certificate + argmax + sliding loss/grad per step)",
+            "value": value,
+            "unit": "candidates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded; Gaussian PSF stands in for the paper's TDM PSF)",
+            "config": {"workload": args.workload, "volume": list(vol.n), "psf_support": [2 * r + 1 for r in vol.R],
+                       "atoms": vol.N, "kernels": K, "candidates_per_step": cands,
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
+                       "timing": "CUDA graph replay per step, CUDA events per step"},
+            "sfw_iters_per_s": world * args.steps / (t_max / 1e3),
+            "slide_evals_per_s": world * args.steps / (t_max / 1e3),
+            "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches,
+            "kernels_per_step": kernels_per_step,
+            "roofline": {"bound": "hbm", "kernel": tag, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+            "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in
+                                    sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+            "clocks": clocks.summary(),
+            "wall_s_timed_region": wall1 - wall0,
+        }
+    plan.close()
+    if world > 1:
+        dist.barrier()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_step(vol, y, lam, m, s, d, w, kernels, oracle, kernel_subset=None):
+    """One step of the FP64 oracle on the same workload: sliding loss + gradient (render and
+    adjoint by direct sums, blur and its transpose through the FFT), then the grid certificate
+    through the FFT and its argmax.  Returns the number of candidates evaluated."""
+    C, g, r = oracle.loss_and_grad(vol.n, vol.R, vol.psf, y, m, s, d, w, lam, fft=True)
+    ks = kernels if kernel_subset is None else [kernels[i] for i in kernel_subset]
+    eta = oracle.eta_grid_fft(vol.n, vol.R, vol.psf, r, lam, ks)
+    oracle.grid_argmax(eta)
+    return len(ks) * vol.V
+
+
+def _oracle_setup(workload):
+    import oracle
+    oracle.build_oracle()
+    vol = sfw_inputs.WORKLOADS[workload](seed=0)
+    y = oracle.observe(vol, fft=True)
+    kernels = vol.grid_kernels()
+    rng = np.random.default_rng(1000)
+    m = vol.m + rng.normal(0, 0.4, vol.m.shape)
+    s = vol.sigma * 1.05
+    d = np.clip(vol.d + 0.05, 1.3, 2.9)
+    w = vol.w * 0.9
+    lam = 1.0   # lambda only rescales eta; the work per step does not depend on it
+    return oracle, vol, y, lam, m, s, d, w, kernels
+
+
+def cpu_baseline(workload):
+    oracle, vol, y, lam, m, s, d, w, kernels = _oracle_setup(workload)
+    t0 = time.perf_counter()
+    cands = oracle_step(vol, y, lam, m, s, d, w, kernels, oracle)
+    t = time.perf_counter() - t0
+    return {"value": cands / t, "unit": "candidates/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"one full step of the FP64 oracle on {workload} ({cands} candidates; "
+                       f"{t:.1f} s): direct-sum render/adjoint on {oracle.num_threads()} OpenMP "
+                       "threads, numpy FFT (1 thread) for the blur and the grid certificate")}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    oracle, vol, y, lam, m, s, d, w, kernels = _oracle_setup(args.workload)
+    # size each step so that warm-up + timed steps stay within ~3 minutes
+    t0 = time.perf_counter()
+    oracle_step(vol, y, lam, m, s, d, w, kernels, oracle, kernel_subset=[0])
+    t_one = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    per_step = int(max(1, min(len(kernels), budget / max(t_one, 1e-3))))
+    for i in range(max(0, args.warmup - 1)):
+        oracle_step(vol, y, lam, m, s, d, w, kernels, oracle, kernel_subset=[i % len(kernels)])
+    cands = 0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        sub = [(i * per_step + j) % len(kernels) for j in range(per_step)]
+        cands += oracle_step(vol, y, lam, m, s, d, w, kernels, oracle, kernel_subset=sub)
+    t = time.perf_counter() - t0
+    value = cands / t
+    line = {"impl": "reference", "metric": "eta-grid candidates/s (grid certificate + argmax + sliding loss/grad per step)",
+            "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": args.workload, "volume": list(vol.n), "kernels": len(kernels),
+                       "kernels_per_step": per_step, "parallelism": "rank 0 host cores"},
+            "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step: oracle sliding loss/grad + certificate over {per_step} of {len(kernels)} kernels"},
+            "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -22,7 +22,9 @@ SFW_PREC_BF16 = 1
 # every symbol declared in include/sfw.h
 EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
            "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_slide_loss_grad",
-           "sfw_last_error", "sfw_launch_count", "sfw_version")
+           "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
+           "sfw_launch_count",
+           "sfw_version")
 
 
 class SfwError(RuntimeError):
@@ -70,8 +72,12 @@ def lib() -> ctypes.CDLL:
     L.sfw_eta_points.argtypes = [vp, vp, dbl, i32, vp, vp, vp, vp]
     L.sfw_argmax.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
+    L.sfw_profile_start.argtypes = [i32]
+    L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    L.sfw_profile_collect.argtypes = []
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
-                 "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_slide_loss_grad"):
+                 "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_slide_loss_grad",
+                 "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop"):
         getattr(L, name).restype = ctypes.c_int
     L.sfw_last_error.restype = ctypes.c_char_p
     L.sfw_last_error.argtypes = []
@@ -130,6 +136,21 @@ def sfw_slide_loss_grad(plan: int, y: int, atoms: Atoms, lam: float, loss_out: i
                         residual_out: int, stream: int) -> None:
     check(lib().sfw_slide_loss_grad(plan, y, ctypes.byref(atoms), float(lam), loss_out, grad_out,
                                     residual_out, stream), "sfw_slide_loss_grad")
+
+
+def sfw_profile_start(max_launches: int) -> None:
+    check(lib().sfw_profile_start(int(max_launches)), "sfw_profile_start")
+
+
+def sfw_profile_collect() -> None:
+    check(lib().sfw_profile_collect(), "sfw_profile_collect")
+
+
+def sfw_profile_stop() -> dict:
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    check(lib().sfw_profile_stop(buf, len(buf)), "sfw_profile_stop")
+    return {k: {"launches": v[0], "ms": v[1]} for k, v in json.loads(buf.value.decode()).items()}
 
 
 def sfw_launch_count() -> int:

@@ -109,8 +109,7 @@ sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], floa
                          cudaStream_t st) {
     dim3 grid((E[2] + kRX - 1) / kRX, (E[1] + kRY - 1) / kRY, (E[0] + kRZ - 1) / kRZ);
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
-    k_render<<<grid, kRenderThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, f);
-    counted_launch();
+    SFW_LAUNCH(st, "k_render", k_render<<<grid, kRenderThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, f));
     return launch_check("k_render");
 }
 
@@ -206,12 +205,10 @@ sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], f
     if (a.N <= 0) return SFW_OK;
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
     dim3 grid(a.N, kGradChunks);
-    k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2,
-                                                b, partials);
-    counted_launch();
+    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2,
+                                                b, partials));
     SFW_TRY(launch_check("k_atom_grad"));
-    k_grad_finalize<<<(a.N + 127) / 128, 128, 0, st>>>(a, kGradChunks, partials, lambda, grad);
-    counted_launch();
+    SFW_LAUNCH(st, "k_grad_finalize", k_grad_finalize<<<(a.N + 127) / 128, 128, 0, st>>>(a, kGradChunks, partials, lambda, grad));
     return launch_check("k_grad_finalize");
 }
 
@@ -234,13 +231,11 @@ sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3]
     if (pts.N <= 0) return SFW_OK;
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
     dim3 grid(pts.N, kGradChunks);
-    k_atom_grad<<<grid, kGradThreads, 0, st>>>(pts, E[0], E[1], E[2], R[0], R[1], R[2],
-                                                log_inv_eps2, b, partials);
-    counted_launch();
+    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(pts, E[0], E[1], E[2], R[0], R[1], R[2],
+                                                log_inv_eps2, b, partials));
     SFW_TRY(launch_check("k_atom_grad"));
-    k_eta_finalize<<<(pts.N + 127) / 128, 128, 0, st>>>(pts.N, kGradChunks, partials, lambda, eta,
-                                                        grad);
-    counted_launch();
+    SFW_LAUNCH(st, "k_eta_finalize", k_eta_finalize<<<(pts.N + 127) / 128, 128, 0, st>>>(pts.N, kGradChunks, partials, lambda, eta,
+                                                        grad));
     return launch_check("k_eta_finalize");
 }
 
@@ -266,8 +261,7 @@ __global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, 
 
 sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
                                 double lambda, double* loss, cudaStream_t st) {
-    k_loss_finalize<<<1, 256, 0, st>>>(partials, nparts, a, lambda, loss);
-    counted_launch();
+    SFW_LAUNCH(st, "k_loss_finalize", k_loss_finalize<<<1, 256, 0, st>>>(partials, nparts, a, lambda, loss));
     return launch_check("k_loss_finalize");
 }
 

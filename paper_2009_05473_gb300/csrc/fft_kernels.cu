@@ -13,6 +13,10 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "sfw_internal.cuh"
 
 namespace sfw {
@@ -495,13 +499,22 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
 
 static int tile_width(int L) { return L <= 256 ? 16 : 8; }
 
+// Raise a kernel's dynamic shared-memory limit once per (device, kernel, size):
+// the attribute call is kept out of stream captures after the first use.
 template <typename KernelT>
 static sfw_status prepare(KernelT kernel, size_t smem) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-    }
+    if (smem <= 48 * 1024) return SFW_OK;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    SFW_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= smem) return SFW_OK;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
+    done[key] = smem;
     return SFW_OK;
 }
 
@@ -517,7 +530,7 @@ sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
 #define SFW_C2C(WW, DD)                                              \
     do {                                                             \
         SFW_TRY(prepare(k_c2c<WW, DD>, smem));                       \
-        k_c2c<WW, DD><<<blocks, kThreads, smem, st>>>(p);            \
+        SFW_LAUNCH(st, "k_c2c", k_c2c<WW, DD><<<blocks, kThreads, smem, st>>>(p)); \
     } while (0)
     if (W == 16) {
         if (p.dir < 0) SFW_C2C(16, -1); else SFW_C2C(16, 1);
@@ -525,7 +538,6 @@ sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
         if (p.dir < 0) SFW_C2C(8, -1); else SFW_C2C(8, 1);
     }
 #undef SFW_C2C
-    counted_launch();
     return launch_check("k_c2c");
 }
 
@@ -537,7 +549,7 @@ sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
 #define SFW_MUL(WW, KK)                                              \
     do {                                                             \
         SFW_TRY(prepare(k_mul<WW, KK>, smem));                       \
-        k_mul<WW, KK><<<blocks, kThreads, smem, st>>>(p);            \
+        SFW_LAUNCH(st, "k_mul", k_mul<WW, KK><<<blocks, kThreads, smem, st>>>(p)); \
     } while (0)
     switch (p.spec_kind) {
         case SPEC_C64: if (W == 16) SFW_MUL(16, SPEC_C64); else SFW_MUL(8, SPEC_C64); break;
@@ -546,7 +558,6 @@ sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
         default: if (W == 16) SFW_MUL(16, SPEC_RBF16); else SFW_MUL(8, SPEC_RBF16); break;
     }
 #undef SFW_MUL
-    counted_launch();
     return launch_check("k_mul");
 }
 
@@ -557,12 +568,11 @@ sfw_status launch_r2c(const R2CPass& p, cudaStream_t st) {
     const unsigned blocks = (unsigned)((p.nlines + 2 * W - 1) / (2 * W));
     if (W == 16) {
         SFW_TRY(prepare(k_r2c<16>, smem));
-        k_r2c<16><<<blocks, kThreads, smem, st>>>(p);
+        SFW_LAUNCH(st, "k_r2c", k_r2c<16><<<blocks, kThreads, smem, st>>>(p));
     } else {
         SFW_TRY(prepare(k_r2c<8>, smem));
-        k_r2c<8><<<blocks, kThreads, smem, st>>>(p);
+        SFW_LAUNCH(st, "k_r2c", k_r2c<8><<<blocks, kThreads, smem, st>>>(p));
     }
-    counted_launch();
     return launch_check("k_r2c");
 }
 
@@ -589,7 +599,7 @@ sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
 #define SFW_C2R(WW, MM)                                              \
     do {                                                             \
         SFW_TRY(prepare(k_c2r<WW, MM>, smem));                       \
-        k_c2r<WW, MM><<<blocks, kThreads, smem, st>>>(p);            \
+        SFW_LAUNCH(st, "k_c2r", k_c2r<WW, MM><<<blocks, kThreads, smem, st>>>(p)); \
     } while (0)
     switch (p.mode) {
         case C2R_STORE: if (W == 16) SFW_C2R(16, C2R_STORE); else SFW_C2R(8, C2R_STORE); break;
@@ -597,7 +607,6 @@ sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
         default: if (W == 16) SFW_C2R(16, C2R_CERTMAX); else SFW_C2R(8, C2R_CERTMAX); break;
     }
 #undef SFW_C2R
-    counted_launch();
     return launch_check("k_c2r");
 }
 

@@ -32,8 +32,7 @@ __global__ void k_wrap_psf(const float* psf, int R0, int R1, int R2, int P0, int
 
 sfw_status launch_wrap_psf(const float* psf, const int R[3], const int P[3], float* out,
                            cudaStream_t st) {
-    k_wrap_psf<<<1024, 256, 0, st>>>(psf, R[0], R[1], R[2], P[0], P[1], P[2], out);
-    counted_launch();
+    SFW_LAUNCH(st, "k_wrap_psf", k_wrap_psf<<<1024, 256, 0, st>>>(psf, R[0], R[1], R[2], P[0], P[1], P[2], out));
     return launch_check("k_wrap_psf");
 }
 
@@ -62,8 +61,7 @@ __global__ void k_wrap_kernel(const float* kx, int n0, int n1, int n2, int P0, i
 
 sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int P[3], float* out,
                               cudaStream_t st) {
-    k_wrap_kernel<<<1024, 256, 0, st>>>(kx, n[0], n[1], n[2], P[0], P[1], P[2], out);
-    counted_launch();
+    SFW_LAUNCH(st, "k_wrap_kernel", k_wrap_kernel<<<1024, 256, 0, st>>>(kx, n[0], n[1], n[2], P[0], P[1], P[2], out));
     return launch_check("k_wrap_kernel");
 }
 
@@ -122,15 +120,13 @@ k_argmax_final(const unsigned long long* partial, int n, float* val, int64_t* id
 
 sfw_status launch_argmax_keys(const float* v, long long count, unsigned long long* partial,
                               int nblocks, cudaStream_t st) {
-    k_argmax_keys<<<nblocks, kRedThreads, 0, st>>>(v, count, partial);
-    counted_launch();
+    SFW_LAUNCH(st, "k_argmax_keys", k_argmax_keys<<<nblocks, kRedThreads, 0, st>>>(v, count, partial));
     return launch_check("k_argmax_keys");
 }
 
 sfw_status launch_argmax_final(const unsigned long long* partial, int n, float* val, int64_t* idx,
                                cudaStream_t st) {
-    k_argmax_final<<<1, kRedThreads, 0, st>>>(partial, n, val, idx);
-    counted_launch();
+    SFW_LAUNCH(st, "k_argmax_final", k_argmax_final<<<1, kRedThreads, 0, st>>>(partial, n, val, idx));
     return launch_check("k_argmax_final");
 }
 
@@ -147,8 +143,7 @@ __global__ void k_key_decode(const unsigned long long* key, float* val, int64_t*
 
 sfw_status launch_key_decode(const unsigned long long* key, float* val, int64_t* idx,
                              cudaStream_t st) {
-    k_key_decode<<<1, 1, 0, st>>>(key, val, idx);
-    counted_launch();
+    SFW_LAUNCH(st, "k_key_decode", k_key_decode<<<1, 1, 0, st>>>(key, val, idx));
     return launch_check("k_key_decode");
 }
 
@@ -215,25 +210,21 @@ sfw_status launch_topk(const float* v, long long count, int topk, unsigned long 
     if (blocks * topk > half) return fail(SFW_ERR_SHAPE, "topk scratch too small");
     unsigned long long* a = scratch;
     unsigned long long* b = scratch + half;
-    k_topk_block<<<(unsigned)blocks, kRedThreads, 0, st>>>(v, nullptr, count, topk, a);
-    counted_launch();
+    SFW_LAUNCH(st, "k_topk_block", k_topk_block<<<(unsigned)blocks, kRedThreads, 0, st>>>(v, nullptr, count, topk, a));
     SFW_TRY(launch_check("k_topk_block"));
     long long n = blocks * topk;
     while (n > kSortN) {
         blocks = (n + kSortN - 1) / kSortN;
-        k_topk_block<<<(unsigned)blocks, kRedThreads, 0, st>>>(nullptr, a, n, topk, b);
-        counted_launch();
+        SFW_LAUNCH(st, "k_topk_block", k_topk_block<<<(unsigned)blocks, kRedThreads, 0, st>>>(nullptr, a, n, topk, b));
         SFW_TRY(launch_check("k_topk_block"));
         n = blocks * topk;
         unsigned long long* t = a;
         a = b;
         b = t;
     }
-    k_topk_block<<<1, kRedThreads, 0, st>>>(nullptr, a, n, topk, b);
-    counted_launch();
+    SFW_LAUNCH(st, "k_topk_block", k_topk_block<<<1, kRedThreads, 0, st>>>(nullptr, a, n, topk, b));
     SFW_TRY(launch_check("k_topk_block"));
-    k_topk_decode<<<1, 64, 0, st>>>(b, topk, val_out, idx_out);
-    counted_launch();
+    SFW_LAUNCH(st, "k_topk_decode", k_topk_decode<<<1, 64, 0, st>>>(b, topk, val_out, idx_out));
     return launch_check("k_topk_decode");
 }
 
@@ -258,8 +249,7 @@ __global__ void k_spec_stats(const float2* s, long long count, float* stats) {
 }
 
 sfw_status launch_spec_stats(const float2* s, long long count, float* stats, cudaStream_t st) {
-    k_spec_stats<<<1024, 256, 0, st>>>(s, count, stats);
-    counted_launch();
+    SFW_LAUNCH(st, "k_spec_stats", k_spec_stats<<<1024, 256, 0, st>>>(s, count, stats));
     return launch_check("k_spec_stats");
 }
 
@@ -276,8 +266,7 @@ __global__ void k_spec_convert(const float2* s, long long count, int kind, void*
 
 sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out,
                                cudaStream_t st) {
-    k_spec_convert<<<1024, 256, 0, st>>>(s, count, kind, out);
-    counted_launch();
+    SFW_LAUNCH(st, "k_spec_convert", k_spec_convert<<<1024, 256, 0, st>>>(s, count, kind, out));
     return launch_check("k_spec_convert");
 }
 

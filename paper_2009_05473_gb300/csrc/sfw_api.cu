@@ -7,7 +7,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "sfw_internal.cuh"
@@ -40,6 +42,75 @@ sfw_status launch_check(const char* what) {
     return SFW_OK;
 }
 
+// ------------------------------------------------------------------ profiler
+
+namespace {
+struct ProfRec {
+    const char* tag;
+    cudaEvent_t a, b;
+};
+struct ProfAcc {
+    std::string tag;
+    long long count;
+    double ms;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfRec> g_prof;      // event pool
+size_t g_prof_used = 0;           // records in use
+bool g_prof_dropped = false;
+bool g_prof_collected = false;
+std::vector<ProfAcc> g_prof_acc;  // per-tag totals
+thread_local const char* t_tag = nullptr;
+thread_local ProfRec* t_open = nullptr;
+
+void prof_accumulate(const char* tag, double ms) {
+    for (auto& a : g_prof_acc)
+        if (a.tag == tag) {
+            a.count += 1;
+            a.ms += ms;
+            return;
+        }
+    g_prof_acc.push_back(ProfAcc{tag, 1, ms});
+}
+}  // namespace
+
+LaunchTag::LaunchTag(const char* tag) : prev(t_tag) { t_tag = tag; }
+LaunchTag::~LaunchTag() { t_tag = prev; }
+
+// Events are recorded with cudaEventRecordExternal so that, inside a stream
+// capture, they become event-record nodes of the graph and time every replay.
+void prof_begin(cudaStream_t st, const char* name) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_used >= g_prof.size()) {
+        g_prof_dropped = true;
+        return;
+    }
+    ProfRec& r = g_prof[g_prof_used++];
+    r.tag = t_tag ? t_tag : name;
+    cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
+    t_open = &r;
+}
+
+void prof_end(cudaStream_t st) {
+    if (!t_open) return;
+    cudaEventRecordWithFlags(t_open->b, st, cudaEventRecordExternal);
+    t_open = nullptr;
+}
+
+static sfw_status prof_collect_locked() {
+    for (size_t i = 0; i < g_prof_used; ++i) {
+        ProfRec& r = g_prof[i];
+        SFW_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        SFW_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        prof_accumulate(r.tag, t);
+    }
+    g_prof_collected = true;
+    return SFW_OK;
+}
+
 // ------------------------------------------------------------------ geometry of a blur
 
 // Transform grid of a blur whose input lives on the box E and whose output
@@ -68,6 +139,19 @@ static size_t blur_buf_elems(const BlurGeom& g) {
     return (size_t)g.E[0] * g.P[1] * g.H2;  // >= every intermediate of forward and transpose
 }
 
+// Profiling tags of the five passes of a blur (or of its transpose).
+struct PassTags {
+    const char* r2c;
+    const char* fwd1;
+    const char* axis0;
+    const char* inv1;
+    const char* c2r;
+};
+static const PassTags kBlurTags = {"blur_r2c", "blur_c2c_fwd", "blur_axis0", "blur_c2c_inv", "blur_c2r"};
+static const PassTags kBackTags = {"bp_r2c", "bp_c2c_fwd", "bp_axis0", "bp_c2c_inv", "bp_c2r"};
+static const PassTags kTableTags = {"table_r2c", "table_c2c_fwd", "table_axis0", "table_c2c_inv", "table_c2r"};
+static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max"};
+
 static LineSet ls(long long Sa, long long Sb, long long Sj, long long B) {
     LineSet s;
     s.Sa = Sa;
@@ -81,7 +165,7 @@ static LineSet ls(long long Sa, long long Sb, long long Sj, long long B) {
 // (fields in/lin/nlines/L/fac/tw/out_off/out_len/lout filled here).
 static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* spec, int spec_kind,
                                float2* bufA, float2* bufB, C2RPass ep, cudaStream_t st,
-                               int* c2r_blocks_out) {
+                               int* c2r_blocks_out, const PassTags& tg = kBlurTags) {
     const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2];
     const int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2], H2 = g.H2;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
@@ -97,7 +181,10 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         p.tw = g.tw[2];
         p.out = bufA;
         p.lout = ls((long long)E1 * H2, H2, 1, E1);
-        SFW_TRY(launch_r2c(p, st));
+        {
+            LaunchTag lt__(tg.r2c);
+            SFW_TRY(launch_r2c(p, st));
+        }
     }
     {   // axis 1 forward: (E0, E1, H2) -> (E0, P1, H2)
         C2CPass p;
@@ -115,7 +202,10 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         p.scale = 1.f;
         p.fac = g.fac[1];
         p.tw = g.tw[1];
-        SFW_TRY(launch_c2c(p, st));
+        {
+            LaunchTag lt__(tg.fwd1);
+            SFW_TRY(launch_c2c(p, st));
+        }
     }
     {   // axis 0: forward, times H^, inverse, keep rows [R0, R0 + n0) -> (n0, P1, H2)
         MulPass p;
@@ -139,7 +229,10 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         p.out_stride = 0;
         p.out_off = g.R[0];
         p.out_len = n0;
-        SFW_TRY(launch_mul(p, st));
+        {
+            LaunchTag lt__(tg.axis0);
+            SFW_TRY(launch_mul(p, st));
+        }
     }
     {   // axis 1 inverse: (n0, P1, H2) -> (n0, n1, H2), rows [R1, R1 + n1)
         C2CPass p;
@@ -157,7 +250,10 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         p.scale = 1.f;
         p.fac = g.fac[1];
         p.tw = g.tw[1];
-        SFW_TRY(launch_c2c(p, st));
+        {
+            LaunchTag lt__(tg.inv1);
+            SFW_TRY(launch_c2c(p, st));
+        }
     }
     // axis 2 inverse with the epilogue: (n0, n1, H2) -> grid (n0, n1, n2)
     ep.in = bufB;
@@ -171,13 +267,14 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
     ep.out_off = g.R[2];
     ep.out_len = n2;
     ep.lout = ls((long long)n1 * n2, n2, 1, n1);
+    LaunchTag lt__(tg.c2r);
     return launch_c2r(ep, st, c2r_blocks_out);
 }
 
 // Transpose of the blur: r on the grid -> b on E (dense), b(t) = sum_s H(s - t) r(s).
 static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* spec,
                                  int spec_kind, float2* bufA, float2* bufB, float* b,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const PassTags& tg = kBackTags) {
     const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2];
     const int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2], H2 = g.H2;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
@@ -193,7 +290,10 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
         p.tw = g.tw[2];
         p.out = bufA;
         p.lout = ls((long long)n1 * H2, H2, 1, n1);
-        SFW_TRY(launch_r2c(p, st));
+        {
+            LaunchTag lt__(tg.r2c);
+            SFW_TRY(launch_r2c(p, st));
+        }
     }
     {   // axis 1 forward, rows at [R1, R1 + n1): (n0, n1, H2) -> (n0, P1, H2)
         C2CPass p;
@@ -211,7 +311,10 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
         p.scale = 1.f;
         p.fac = g.fac[1];
         p.tw = g.tw[1];
-        SFW_TRY(launch_c2c(p, st));
+        {
+            LaunchTag lt__(tg.fwd1);
+            SFW_TRY(launch_c2c(p, st));
+        }
     }
     {   // axis 0: forward (rows at [R0, R0 + n0)), times conj(H^), inverse -> (E0, P1, H2)
         MulPass p;
@@ -235,7 +338,10 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
         p.out_stride = 0;
         p.out_off = 0;
         p.out_len = E0;
-        SFW_TRY(launch_mul(p, st));
+        {
+            LaunchTag lt__(tg.axis0);
+            SFW_TRY(launch_mul(p, st));
+        }
     }
     {   // axis 1 inverse: (E0, P1, H2) -> (E0, E1, H2)
         C2CPass p;
@@ -253,7 +359,10 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
         p.scale = 1.f;
         p.fac = g.fac[1];
         p.tw = g.tw[1];
-        SFW_TRY(launch_c2c(p, st));
+        {
+            LaunchTag lt__(tg.inv1);
+            SFW_TRY(launch_c2c(p, st));
+        }
     }
     C2RPass p;
     memset(&p, 0, sizeof(p));
@@ -270,6 +379,7 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
     p.scale = 1.f;
     p.mode = C2R_STORE;
     p.out = b;
+    LaunchTag lt__(tg.c2r);
     return launch_c2r(p, st, nullptr);
 }
 
@@ -291,7 +401,10 @@ static sfw_status fft3_forward(const int P[3], const Factors fac[3], const float
         p.tw = tw[2];
         p.out = out;
         p.lout = ls((long long)P1 * H2, H2, 1, P1);
-        SFW_TRY(launch_r2c(p, st));
+        {
+            LaunchTag lt__("fft3_r2c");
+            SFW_TRY(launch_r2c(p, st));
+        }
     }
     {
         C2CPass p;
@@ -309,7 +422,10 @@ static sfw_status fft3_forward(const int P[3], const Factors fac[3], const float
         p.scale = 1.f;
         p.fac = fac[1];
         p.tw = tw[1];
-        SFW_TRY(launch_c2c(p, st));
+        {
+            LaunchTag lt__("fft3_c2c1");
+            SFW_TRY(launch_c2c(p, st));
+        }
     }
     {
         C2CPass p;
@@ -328,7 +444,10 @@ static sfw_status fft3_forward(const int P[3], const Factors fac[3], const float
         p.scale = scale;
         p.fac = fac[0];
         p.tw = tw[0];
-        SFW_TRY(launch_c2c(p, st));
+        {
+            LaunchTag lt__("fft3_c2c0");
+            SFW_TRY(launch_c2c(p, st));
+        }
     }
     return SFW_OK;
 }
@@ -473,7 +592,7 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
             ep.mode = C2R_STORE;
             ep.scale = 1.f;
             ep.out = kx;
-            if ((st_ret = blur_forward(g, fE, Hg, SPEC_C64, gA, gB, ep, st, nullptr))) break;
+            if ((st_ret = blur_forward(g, fE, Hg, SPEC_C64, gA, gB, ep, st, nullptr, kTableTags))) break;
             if ((st_ret = launch_wrap_kernel(kx, p->n, p->Pc, wrapped, st))) break;
             if ((st_ret = fft3_forward(p->Pc, p->facc, p->twc, wrapped, ftmp, full + (size_t)k * spec_elems,
                                        1.0f / (float)Pc_tot, st)))
@@ -539,6 +658,61 @@ static AtomsDev to_dev(const sfw_atoms* a) {
 extern "C" {
 
 const char* sfw_last_error(void) { return g_err; }
+
+sfw_status sfw_profile_start(int max_launches) {
+    clear_error();
+    if (max_launches < 1 || max_launches > (1 << 20)) return fail(SFW_ERR_ARG, "max_launches outside [1, 2^20]");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    while ((int)g_prof.size() < max_launches) {
+        ProfRec r;
+        r.tag = nullptr;
+        SFW_CUDA(cudaEventCreate(&r.a));
+        cudaError_t e = cudaEventCreate(&r.b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(r.a);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+        g_prof.push_back(r);
+    }
+    g_prof_used = 0;
+    g_prof_dropped = false;
+    g_prof_collected = false;
+    g_prof_acc.clear();
+    g_prof_on = true;
+    return SFW_OK;
+}
+
+sfw_status sfw_profile_collect(void) {
+    clear_error();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return prof_collect_locked();
+}
+
+sfw_status sfw_profile_stop(char* json, size_t len) {
+    clear_error();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    if (!g_prof_collected) SFW_TRY(prof_collect_locked());
+    std::string out = "{";
+    for (size_t k = 0; k < g_prof_acc.size(); ++k) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "%s\"%s\": [%lld, %.6f]", k ? ", " : "", g_prof_acc[k].tag.c_str(),
+                 g_prof_acc[k].count, g_prof_acc[k].ms);
+        out += buf;
+    }
+    out += "}";
+    const bool dropped = g_prof_dropped;
+    g_prof_used = 0;
+    g_prof_acc.clear();
+    g_prof_collected = false;
+    if (json && len) {
+        if (out.size() + 1 > len) return fail(SFW_ERR_ARG, "profile report needs %zu bytes", out.size() + 1);
+        memcpy(json, out.c_str(), out.size() + 1);
+    }
+    if (dropped) return fail(SFW_ERR_ARG, "profile buffer full: some launches were not recorded");
+    return SFW_OK;
+}
 
 int64_t sfw_launch_count(void) { return g_launches.load(); }
 
@@ -748,7 +922,10 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         q.tw = p->twc[2];
         q.out = p->cA;
         q.lout = ls((long long)n1 * H2, H2, 1, n1);
-        SFW_TRY(launch_r2c(q, st));
+        {
+            LaunchTag lt__(kCertTags.r2c);
+            SFW_TRY(launch_r2c(q, st));
+        }
     }
     {   // axis 1 forward: -> (n0, P1, H2)
         C2CPass q;
@@ -766,7 +943,10 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         q.scale = 1.f;
         q.fac = p->facc[1];
         q.tw = p->twc[1];
-        SFW_TRY(launch_c2c(q, st));
+        {
+            LaunchTag lt__(kCertTags.fwd1);
+            SFW_TRY(launch_c2c(q, st));
+        }
     }
     {   // axis 0: forward once, then for each kernel k: times table_k, inverse -> (K, n0, P1, H2)
         MulPass q;
@@ -790,7 +970,10 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         q.out_stride = (long long)n0 * nl;
         q.out_off = 0;
         q.out_len = n0;
-        SFW_TRY(launch_mul(q, st));
+        {
+            LaunchTag lt__(kCertTags.axis0);
+            SFW_TRY(launch_mul(q, st));
+        }
     }
     {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
         C2CPass q;
@@ -808,7 +991,10 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         q.scale = 1.f;
         q.fac = p->facc[1];
         q.tw = p->twc[1];
-        SFW_TRY(launch_c2c(q, st));
+        {
+            LaunchTag lt__(kCertTags.inv1);
+            SFW_TRY(launch_c2c(q, st));
+        }
     }
     if (best_val || best_idx) {
         cudaError_t e = cudaMemsetAsync(p->best_key, 0, sizeof(unsigned long long), st);
@@ -834,7 +1020,10 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     q.max_out = max_out;
     q.argk_out = argk_out;
     q.best_key = (best_val || best_idx) ? p->best_key : nullptr;
-    SFW_TRY(launch_c2r(q, st, nullptr));
+    {
+        LaunchTag lt__(kCertTags.c2r);
+        SFW_TRY(launch_c2r(q, st, nullptr));
+    }
     if (best_val || best_idx) SFW_TRY(launch_key_decode(p->best_key, best_val, best_idx, st));
     return SFW_OK;
 }

@@ -33,6 +33,25 @@ void clear_error();
 // Kernels launched by the library (process-wide counter).
 extern std::atomic<int64_t> g_launches;
 inline void counted_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Optional per-launch timing (sfw_profile_start): CUDA events recorded on the
+// launching stream around every kernel, aggregated per tag.  The tag is the
+// innermost active LaunchTag of this thread, else the kernel's own name.
+void prof_begin(cudaStream_t st, const char* name);
+void prof_end(cudaStream_t st);
+struct LaunchTag {
+    const char* prev;
+    explicit LaunchTag(const char* tag);
+    ~LaunchTag();
+};
+
+#define SFW_LAUNCH(st, name, ...)          \
+    do {                                   \
+        ::sfw::prof_begin((st), (name));   \
+        __VA_ARGS__;                       \
+        ::sfw::prof_end(st);               \
+        ::sfw::counted_launch();           \
+    } while (0)
 // Check the launch that was just issued.
 sfw_status launch_check(const char* what);
 
