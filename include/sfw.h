@@ -168,6 +168,23 @@ sfw_status sfw_eta_points(sfw_plan* plan, const float* residual, double lambda, 
 sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_out,
                       int64_t* idx_out, void* stream);
 
+/* sfw_argmax without any device allocation.  (The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate.)
+ * Same arguments, results and NaN reporting as sfw_argmax.  sfw_argmax
+ * allocates its key scratch with cudaMalloc on first use; this variant uses a
+ * 2 MiB static device array of the library instead and never calls cudaMalloc
+ * or cudaFree -- for code running under a global-mode stream capture, for
+ * applications whose device memory belongs to another allocator, and for loops
+ * where a cudaFree would synchronise the device.
+ * Limit: topk == 1 accepts any count; topk > 1 needs
+ * ceil(count / 4096) * topk <= 131072 (e.g. count <= 8 388 608 for topk = 64),
+ * else SFW_ERR_SHAPE.  The first call on each device looks up the array's
+ * address (make it before any stream capture).  All calls share the array:
+ * calls whose kernels overlap on the GPU race and must be ordered by the
+ * caller. */
+sfw_status sfw_argmax_noalloc(const float* values, int64_t count, int topk, float* val_out,
+                              int64_t* idx_out, void* stream);
+
 /* Loss and analytic gradient of the sliding step (step 4 of Algorithm 1,
  * step 2b of Algorithm 2; Section 2: "grad C computed analytically").
  *   y         device n0*n1*n2 floats (observation)

@@ -21,8 +21,8 @@ SFW_PREC_BF16 = 1
 
 # every symbol declared in include/sfw.h
 EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
-           "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_slide_loss_grad",
-           "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
+           "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
+           "sfw_slide_loss_grad", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
            "sfw_launch_count",
            "sfw_version")
 
@@ -71,13 +71,15 @@ def lib() -> ctypes.CDLL:
     L.sfw_certificate_grid.argtypes = [vp, vp, dbl, vp, vp, vp, vp, vp, vp]
     L.sfw_eta_points.argtypes = [vp, vp, dbl, i32, vp, vp, vp, vp]
     L.sfw_argmax.argtypes = [vp, i64, i32, vp, vp, vp]
+    L.sfw_argmax_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
     L.sfw_profile_start.argtypes = [i32]
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
-                 "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_slide_loss_grad",
-                 "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop"):
+                 "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
+                 "sfw_slide_loss_grad", "sfw_profile_start", "sfw_profile_collect",
+                 "sfw_profile_stop"):
         getattr(L, name).restype = ctypes.c_int
     L.sfw_last_error.restype = ctypes.c_char_p
     L.sfw_last_error.argtypes = []
@@ -130,6 +132,15 @@ def sfw_eta_points(plan: int, residual: int, lam: float, P: int, theta: int, eta
 
 def sfw_argmax(values: int, count: int, topk: int, val_out: int, idx_out: int, stream: int) -> None:
     check(lib().sfw_argmax(values, int(count), int(topk), val_out, idx_out, stream), "sfw_argmax")
+
+
+def sfw_argmax_noalloc(values: int, count: int, topk: int, val_out: int, idx_out: int,
+                       stream: int) -> None:
+    """sfw_argmax for callers that cannot allocate device memory: its scratch is a static
+    2 MiB device array of the library (see include/sfw.h for the size limit and the
+    sharing rules)."""
+    check(lib().sfw_argmax_noalloc(values, int(count), int(topk), val_out, idx_out, stream),
+          "sfw_argmax_noalloc")
 
 
 def sfw_slide_loss_grad(plan: int, y: int, atoms: Atoms, lam: float, loss_out: int, grad_out: int,
