@@ -203,7 +203,8 @@ sfw_status sfw_slide_loss_grad(sfw_plan* plan, const float* y, const sfw_atoms* 
 
 /* Per-launch timing.  sfw_profile_start records a CUDA event pair on the
  * launching stream around each of the next max_launches kernels this library
- * launches (any thread).  The events are recorded as external events, so a
+ * launches (any thread) whose tag equals only_tag (host string; NULL = every
+ * kernel).  The events are recorded as external events, so a
  * stream capture turns them into event-record nodes that time every replay
  * of the graph.  sfw_profile_collect waits for the recorded events and adds
  * their durations to per-tag totals (call it after each replay to time
@@ -212,7 +213,7 @@ sfw_status sfw_slide_loss_grad(sfw_plan* plan, const float* y, const sfw_atoms* 
  * into json (host, len bytes, NUL-terminated).  Tags name the pass of the hot
  * path (e.g. "cert_axis0", "blur_c2r", "k_atom_grad").  SFW_ERR_ARG if json
  * is too small or launches were dropped (pool full). */
-sfw_status sfw_profile_start(int max_launches);
+sfw_status sfw_profile_start(int max_launches, const char* only_tag);
 sfw_status sfw_profile_collect(void);
 sfw_status sfw_profile_stop(char* json, size_t len);
 

@@ -73,7 +73,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_argmax.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_argmax_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
-    L.sfw_profile_start.argtypes = [i32]
+    L.sfw_profile_start.argtypes = [i32, ctypes.c_char_p]
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
@@ -149,8 +149,9 @@ def sfw_slide_loss_grad(plan: int, y: int, atoms: Atoms, lam: float, loss_out: i
                                     residual_out, stream), "sfw_slide_loss_grad")
 
 
-def sfw_profile_start(max_launches: int) -> None:
-    check(lib().sfw_profile_start(int(max_launches)), "sfw_profile_start")
+def sfw_profile_start(max_launches: int, only_tag: str = None) -> None:
+    check(lib().sfw_profile_start(int(max_launches), only_tag.encode() if only_tag else None),
+          "sfw_profile_start")
 
 
 def sfw_profile_collect() -> None:

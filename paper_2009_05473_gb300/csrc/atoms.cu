@@ -182,13 +182,25 @@ k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float lo
     }
 }
 
+// One warp per atom: lane c sums chunk c (c < 32 = kGradChunks), then a fixed-order
+// shuffle tree (deterministic).
+__device__ __forceinline__ void warp_chunk_sums(int n, int chunks, const double* partials, double s[6]) {
+    const int lane = threadIdx.x & 31;
+    for (int q = 0; q < 6; ++q) {
+        double v = 0.0;
+        for (int c = lane; c < chunks; c += 32) v += partials[((long long)n * chunks + c) * 6 + q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        s[q] = v;
+    }
+}
+
 __global__ void k_grad_finalize(AtomsDev a, int chunks, const double* partials, double lambda,
                                 double* grad) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= a.N) return;
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int c = 0; c < chunks; ++c)
-        for (int q = 0; q < 6; ++q) s[q] += partials[((long long)n * chunks + c) * 6 + q];
+    double s[6];
+    warp_chunk_sums(n, chunks, partials, s);
+    if ((threadIdx.x & 31) != 0) return;
     const double w = a.w[a.ps * n];
     const int N = a.N;
     grad[3 * n + 0] = -w * s[0];
@@ -208,18 +220,18 @@ sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], f
     SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2,
                                                 b, partials));
     SFW_TRY(launch_check("k_atom_grad"));
-    SFW_LAUNCH(st, "k_grad_finalize", k_grad_finalize<<<(a.N + 127) / 128, 128, 0, st>>>(a, kGradChunks, partials, lambda, grad));
+    SFW_LAUNCH(st, "k_grad_finalize", k_grad_finalize<<<(a.N + 3) / 4, 128, 0, st>>>(a, kGradChunks, partials, lambda, grad));
     return launch_check("k_grad_finalize");
 }
 
 // eta and its gradient at parameter rows: the same per-atom sums, scaled by 1/lambda.
 __global__ void k_eta_finalize(int P, int chunks, const double* partials, double lambda,
                                double* eta, double* grad) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (n >= P) return;
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int c = 0; c < chunks; ++c)
-        for (int q = 0; q < 6; ++q) s[q] += partials[((long long)n * chunks + c) * 6 + q];
+    double s[6];
+    warp_chunk_sums(n, chunks, partials, s);
+    if ((threadIdx.x & 31) != 0) return;
     eta[n] = s[5] / lambda;
     if (grad)
         for (int q = 0; q < 5; ++q) grad[5 * n + q] = s[q] / lambda;
@@ -234,7 +246,7 @@ sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3]
     SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(pts, E[0], E[1], E[2], R[0], R[1], R[2],
                                                 log_inv_eps2, b, partials));
     SFW_TRY(launch_check("k_atom_grad"));
-    SFW_LAUNCH(st, "k_eta_finalize", k_eta_finalize<<<(pts.N + 127) / 128, 128, 0, st>>>(pts.N, kGradChunks, partials, lambda, eta,
+    SFW_LAUNCH(st, "k_eta_finalize", k_eta_finalize<<<(pts.N + 3) / 4, 128, 0, st>>>(pts.N, kGradChunks, partials, lambda, eta,
                                                         grad));
     return launch_check("k_eta_finalize");
 }

@@ -4,12 +4,15 @@
 // correlation against the kernel-family table (Section 2: "convolutions are
 // made in Fourier domain").
 //
-// A CTA owns a tile of W lines.  Shared memory holds the tile point-major,
-// row j of the tile at [j * (W + 1)], so that the W lines of a row are
-// contiguous (coalesced loads of strided axes) and rows are padded by one
-// element against bank conflicts.  Radix-R stages read R points L/R apart and
-// write them Ns apart (Stockham), so no bit reversal is needed and the result
-// is in natural order after the last stage.
+// A CTA owns a tile of W lines (W a multiple of 8).  Shared memory holds the
+// tile line-major with an odd pitch L + 1 (no bank conflicts along a line or
+// across lines).  The CTA loads and stores the tile cooperatively (rows of W
+// lines for strided axes, whole lines for the contiguous axis); in between,
+// each warp owns W / 8 lines and runs the butterfly stages on them alone, with
+// __syncwarp between stages.  Radix-R stages read R points L/R apart and write
+// them Ns apart (Stockham), so no bit reversal is needed.  The first stage
+// reads its inputs through a functor, which fuses the spectrum multiply of a
+// convolution or the Hermitian rebuild of a real inverse transform into it.
 #include <math.h>
 #include <stdio.h>
 
@@ -26,8 +29,8 @@ namespace sfw {
 bool factorize(int L, Factors* f) {
     f->n = 0;
     if (L < 1 || L > kMaxLen) return false;
-    const int radices[5] = {8, 4, 2, 3, 5};
-    for (int q = 0; q < 5; ++q) {
+    const int radices[6] = {16, 8, 4, 2, 3, 5};
+    for (int q = 0; q < 6; ++q) {
         int r = radices[q];
         while (L % r == 0 && L > 1) {
             if (f->n >= kMaxFactors) return false;
@@ -164,30 +167,79 @@ __device__ __forceinline__ void dft5(float2* v) {
     v[3] = csub(a2, b2);
 }
 
+// a * (c + DIR i s)
+template <int DIR>
+__device__ __forceinline__ float2 cmulc(float2 a, float c, float s) {
+    return make_float2(a.x * c - DIR * a.y * s, a.y * c + DIR * a.x * s);
+}
+
+// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* v) {
+    float2 a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        float2 x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
+        dft4v<DIR>(x0, x1, x2, x3);
+        a[n2][0] = x0;
+        a[n2][1] = x1;
+        a[n2][2] = x2;
+        a[n2][3] = x3;
+    }
+    const float c1 = 0.92387953251128675613f;  // cos(pi / 8)
+    const float s1 = 0.38268343236508977173f;  // sin(pi / 8)
+    const float h = 0.70710678118654752440f;
+    a[1][1] = cmulc<DIR>(a[1][1], c1, s1);    // W16^1
+    a[1][2] = cmulc<DIR>(a[1][2], h, h);      // W16^2
+    a[1][3] = cmulc<DIR>(a[1][3], s1, c1);    // W16^3
+    a[2][1] = cmulc<DIR>(a[2][1], h, h);      // W16^2
+    a[2][2] = mul_i<DIR>(a[2][2]);            // W16^4
+    a[2][3] = cmulc<DIR>(a[2][3], -h, h);     // W16^6
+    a[3][1] = cmulc<DIR>(a[3][1], s1, c1);    // W16^3
+    a[3][2] = cmulc<DIR>(a[3][2], -h, h);     // W16^6
+    a[3][3] = cmulc<DIR>(a[3][3], -c1, -s1);  // W16^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 y0 = a[0][k1], y1 = a[1][k1], y2 = a[2][k1], y3 = a[3][k1];
+        dft4v<DIR>(y0, y1, y2, y3);
+        v[k1] = y0;
+        v[k1 + 4] = y1;
+        v[k1 + 8] = y2;
+        v[k1 + 12] = y3;
+    }
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void dft(float2* v) {
     if constexpr (R == 2) dft2<DIR>(v);
     else if constexpr (R == 3) dft3<DIR>(v);
     else if constexpr (R == 4) dft4<DIR>(v);
     else if constexpr (R == 5) dft5<DIR>(v);
-    else dft8<DIR>(v);
+    else if constexpr (R == 8) dft8<DIR>(v);
+    else dft16<DIR>(v);
 }
 
-// One Stockham radix-R stage over the W lines of the tile.
-template <int R, int DIR, int W>
-__device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                          int L, int Ns, const float2* __restrict__ tw) {
-    constexpr int WS = W + 1;
+// ------------------------------------------------------------------ warp-level stages
+
+// Radix-R Stockham stage over lines [li0, li0 + nl) of a line-major tile (pitch LS).
+template <int R, int DIR, bool FIRST, class Load>
+__device__ __forceinline__ void wstage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                       int L, int LS, int li0, int nl, int Ns,
+                                       const float2* __restrict__ tw, const Load& load) {
     const int LR = L / R;
     const int tstep = L / (Ns * R);
-    const int total = LR * W;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int i = t % W;
-        const int jj = t / W;
+    const int total = LR * nl;
+    for (int t = (int)(threadIdx.x & 31); t < total; t += 32) {
+        const int lq = t / LR;
+        const int jj = t - lq * LR;
+        const int li = li0 + lq;
         const int k = jj % Ns;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(jj + r * LR) * WS + i];
+        for (int r = 0; r < R; ++r) {
+            if constexpr (FIRST) v[r] = load(li, jj + r * LR);
+            else v[r] = src[li * LS + jj + r * LR];
+        }
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -199,35 +251,65 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2
         dft<R, DIR>(v);
         const int base = (jj - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * WS + i] = v[r];
+        for (int r = 0; r < R; ++r) dst[li * LS + base + r * Ns] = v[r];
+    }
+    __syncwarp();
+}
+
+template <int DIR, bool FIRST, class Load>
+__device__ __forceinline__ void wstage_any(int R, const float2* src, float2* dst, int L, int LS,
+                                           int li0, int nl, int Ns, const float2* tw, const Load& load) {
+    switch (R) {
+        case 16: wstage<16, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
+        case 8: wstage<8, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
+        case 4: wstage<4, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
+        case 2: wstage<2, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
+        case 3: wstage<3, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
+        default: wstage<5, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
     }
 }
 
-// Full transform of the tile held in `a`; returns the buffer holding the result.
-template <int DIR, int W>
-__device__ float2* fft_tile(float2* a, float2* b, int L, const Factors& fac, const float2* tw) {
+// Transform of this warp's lines.  Stage 0 reads through `load` and writes b;
+// later stages alternate a <- b <- a ...  Returns the buffer with the result.
+template <int DIR, class Load>
+__device__ float2* warp_fft(float2* a, float2* b, int L, int LS, int li0, int nl,
+                            const Factors& fac, const float2* tw, const Load& load) {
     int Ns = 1;
-    for (int s = 0; s < fac.n; ++s) {
-        const int R = fac.r[s];
-        switch (R) {
-            case 8: fft_stage<8, DIR, W>(a, b, L, Ns, tw); break;
-            case 4: fft_stage<4, DIR, W>(a, b, L, Ns, tw); break;
-            case 2: fft_stage<2, DIR, W>(a, b, L, Ns, tw); break;
-            case 3: fft_stage<3, DIR, W>(a, b, L, Ns, tw); break;
-            default: fft_stage<5, DIR, W>(a, b, L, Ns, tw); break;
-        }
-        __syncthreads();
-        float2* t = a;
-        a = b;
-        b = t;
-        Ns *= R;
+    wstage_any<DIR, true>(fac.r[0], nullptr, b, L, LS, li0, nl, Ns, tw, load);
+    Ns *= fac.r[0];
+    float2* src = b;
+    float2* dst = a;
+    for (int s = 1; s < fac.n; ++s) {
+        wstage_any<DIR, false>(fac.r[s], src, dst, L, LS, li0, nl, Ns, tw, load);
+        Ns *= fac.r[s];
+        float2* t = src;
+        src = dst;
+        dst = t;
     }
-    return a;
+    return src;
 }
+
+struct SmemLoad {
+    const float2* a;
+    int LS;
+    __device__ __forceinline__ float2 operator()(int li, int j) const { return a[li * LS + j]; }
+};
 
 __device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* tw, int L) {
     for (int j = threadIdx.x; j < L; j += blockDim.x) s_tw[j] = tw[j];
 }
+
+// ------------------------------------------------------------------ cp.async helpers
+
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 // ------------------------------------------------------------------ kernels
 
@@ -235,11 +317,12 @@ constexpr int kThreads = 256;
 
 template <int W, int DIR>
 __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
-    constexpr int WS = W + 1;
+    constexpr int NL = W / 8;
+    const int LS = p.L + 1;
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
-    float2* B = A + p.L * WS;
+    float2* B = A + W * LS;
     __shared__ long long off_in[W], off_out[W];
     const long long l0 = (long long)blockIdx.x * W;
     if (threadIdx.x < W) {
@@ -256,39 +339,117 @@ __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
         const int jj = j - p.in_off;
         float2 v = make_float2(0.f, 0.f);
         if (l0 + i < p.nlines && jj >= 0 && jj < p.in_len) v = p.in[off_in[i] + jj * p.lin.Sj];
-        A[j * WS + i] = v;
+        A[i * LS + j] = v;
     }
     __syncthreads();
-    float2* res = fft_tile<DIR, W>(A, B, p.L, p.fac, s_tw);
+    const int warp = threadIdx.x >> 5;
+    float2* res = warp_fft<DIR>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
+    __syncthreads();
     for (int e = threadIdx.x; e < p.out_len * W; e += blockDim.x) {
         const int i = e % W, j = e / W;
         if (l0 + i < p.nlines)
-            p.out[off_out[i] + j * p.lout.Sj] = cscale(res[(j + p.out_off) * WS + i], p.scale);
+            p.out[off_out[i] + j * p.lout.Sj] = cscale(res[i * LS + j + p.out_off], p.scale);
     }
 }
 
 template <int KIND>
-__device__ __forceinline__ float2 load_spec(const void* base, long long idx) {
+struct SpecInfo;
+template <> struct SpecInfo<SPEC_C64> { static constexpr int bytes = 8; };
+template <> struct SpecInfo<SPEC_R32> { static constexpr int bytes = 4; };
+template <> struct SpecInfo<SPEC_CBF16> { static constexpr int bytes = 4; };
+template <> struct SpecInfo<SPEC_RBF16> { static constexpr int bytes = 2; };
+
+template <int KIND>
+__device__ __forceinline__ float2 spec_value(const unsigned char* base, int idx) {
     if constexpr (KIND == SPEC_C64) {
         return reinterpret_cast<const float2*>(base)[idx];
     } else if constexpr (KIND == SPEC_R32) {
         return make_float2(reinterpret_cast<const float*>(base)[idx], 0.f);
     } else if constexpr (KIND == SPEC_CBF16) {
-        __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(base)[idx];
-        return __bfloat1622float2(h);
+        return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[idx]);
     } else {
         return make_float2(__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[idx]), 0.f);
     }
 }
 
+// X[li][j] times the staged spectrum tile S[j][li] (row pitch SW), optionally conjugated.
+template <int KIND>
+struct MulLoad {
+    const float2* X;
+    int LS;
+    const unsigned char* S;
+    int SW;
+    int conj;
+    __device__ __forceinline__ float2 operator()(int li, int j) const {
+        float2 h = spec_value<KIND>(S, j * SW + li);
+        if (conj) h.y = -h.y;
+        return cmul(X[li * LS + j], h);
+    }
+};
+
+// Row pitch (elements) of a staged spectrum tile: W lines padded to a multiple of 16 bytes
+// plus 16 bytes, so rows can be filled with 16-byte copies and read without bank conflicts.
+template <int W, int ES>
+struct SpecPitch {
+    static constexpr int value = W + 16 / ES;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+
+// Stage spectrum s of the tile (rows j < L of W lines) into shared memory S[j][i].
+// A row whose W values are all present and 16-byte aligned travels as 16-byte
+// cp.async chunks; other rows are copied element by element.
+template <int W, int KIND>
+__device__ __forceinline__ void stage_spec(const MulPass& p, int s, const long long* off_spec,
+                                           long long l0, unsigned char* S) {
+    constexpr int ES = SpecInfo<KIND>::bytes;
+    constexpr int SW = SpecPitch<W, ES>::value;
+    constexpr int CH = W * ES / 16;   // 16-byte chunks per full row
+    const unsigned char* base = reinterpret_cast<const unsigned char*>(p.spec);
+    const long long sbase = (long long)s * p.spec_stride;
+    const bool full = l0 + W <= p.nlines && off_spec[W - 1] == off_spec[0] + (W - 1);
+    for (int e = threadIdx.x; e < p.L * CH; e += blockDim.x) {
+        const int j = e / CH, c = e - (e / CH) * CH;
+        unsigned char* drow = S + (size_t)j * SW * ES;
+        const unsigned char* srow = base + (size_t)(sbase + off_spec[0] + j * p.lspec.Sj) * ES;
+        if (full && ((reinterpret_cast<uintptr_t>(srow) & 15) == 0)) {
+            cp_async16(drow + 16 * c, srow + 16 * c);
+        } else {
+            // element-wise: chunk c covers lines [c * 16 / ES, (c + 1) * 16 / ES)
+            for (int i = c * (16 / ES); i < (c + 1) * (16 / ES); ++i) {
+                unsigned char* dst = drow + (size_t)i * ES;
+                if (l0 + i < p.nlines) {
+                    const unsigned char* src = base + (size_t)(sbase + off_spec[i] + j * p.lspec.Sj) * ES;
+                    if constexpr (ES == 8) *reinterpret_cast<float2*>(dst) = *reinterpret_cast<const float2*>(src);
+                    else if constexpr (ES == 4) *reinterpret_cast<float*>(dst) = *reinterpret_cast<const float*>(src);
+                    else *reinterpret_cast<unsigned short*>(dst) = *reinterpret_cast<const unsigned short*>(src);
+                } else {
+                    if constexpr (ES == 8) *reinterpret_cast<float2*>(dst) = make_float2(0.f, 0.f);
+                    else if constexpr (ES == 4) *reinterpret_cast<float*>(dst) = 0.f;
+                    else *reinterpret_cast<unsigned short*>(dst) = 0;
+                }
+            }
+        }
+    }
+}
+
 template <int W, int KIND>
 __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
-    constexpr int WS = W + 1;
+    constexpr int NL = W / 8;
+    constexpr int ES = SpecInfo<KIND>::bytes;
+    constexpr int SW = SpecPitch<W, ES>::value;
+    const int LS = p.L + 1;
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
-    float2* B = A + p.L * WS;
-    float2* C = B + p.L * WS;
+    float2* B = A + W * LS;
+    float2* C = B + W * LS;
+    const size_t sp_bytes = (((size_t)p.L * SW * ES) + 15) & ~(size_t)15;
+    unsigned char* SP0 = reinterpret_cast<unsigned char*>(C + W * LS);
+    unsigned char* SP1 = SP0 + sp_bytes;
     __shared__ long long off_in[W], off_out[W], off_spec[W];
     const long long l0 = (long long)blockIdx.x * W;
     if (threadIdx.x < W) {
@@ -301,43 +462,49 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
     }
     load_twiddles(s_tw, p.tw, p.L);
     __syncthreads();
+    // grid.y splits the spectra into groups of p.nspec
+    const int k0 = (int)blockIdx.y * p.nspec;
+    const int nspec = min(p.nspec, p.ktotal - k0);
+    // the first spectrum travels while the forward transform runs
+    stage_spec<W, KIND>(p, k0, off_spec, l0, SP0);
+    cp_async_commit();
     for (int e = threadIdx.x; e < p.L * W; e += blockDim.x) {
         const int i = e % W, j = e / W;
         const int jj = j - p.in_off;
         float2 v = make_float2(0.f, 0.f);
         if (l0 + i < p.nlines && jj >= 0 && jj < p.in_len) v = p.in[off_in[i] + jj * p.lin.Sj];
-        A[j * WS + i] = v;
+        A[i * LS + j] = v;
     }
     __syncthreads();
-    float2* X = fft_tile<-1, W>(A, B, p.L, p.fac, s_tw);
-    float2* S0 = (X == A) ? B : A;
-    for (int s = 0; s < p.nspec; ++s) {
-        const long long sbase = (long long)s * p.spec_stride;
-        for (int e = threadIdx.x; e < p.L * W; e += blockDim.x) {
-            const int i = e % W, j = e / W;
-            float2 h = make_float2(0.f, 0.f);
-            if (l0 + i < p.nlines) h = load_spec<KIND>(p.spec, sbase + off_spec[i] + j * p.lspec.Sj);
-            if (p.conj_spec) h.y = -h.y;
-            S0[j * WS + i] = cmul(X[j * WS + i], h);
-        }
+    const int warp = threadIdx.x >> 5;
+    float2* X = warp_fft<-1>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
+    float2* U = (X == A) ? B : A;
+    float2* V = C;
+    for (int s = 0; s < nspec; ++s) {
+        if (s + 1 < nspec) stage_spec<W, KIND>(p, k0 + s + 1, off_spec, l0, (s & 1) ? SP0 : SP1);
+        cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
-        float2* res = fft_tile<1, W>(S0, C, p.L, p.fac, s_tw);
-        float2* outp = p.out + (long long)s * p.out_stride;
+        const unsigned char* S = (s & 1) ? SP1 : SP0;
+        float2* res = warp_fft<1>(V, U, p.L, LS, warp * NL, NL, p.fac, s_tw,
+                                  MulLoad<KIND>{X, LS, S, SW, p.conj_spec});
+        __syncthreads();
+        float2* outp = p.out + (long long)(k0 + s) * p.out_stride;
         for (int e = threadIdx.x; e < p.out_len * W; e += blockDim.x) {
             const int i = e % W, j = e / W;
-            if (l0 + i < p.nlines) outp[off_out[i] + j * p.lout.Sj] = res[(j + p.out_off) * WS + i];
+            if (l0 + i < p.nlines) outp[off_out[i] + j * p.lout.Sj] = res[i * LS + j + p.out_off];
         }
-        __syncthreads();
     }
 }
 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
-    constexpr int WS = W + 1;
+    constexpr int NL = W / 8;
+    const int LS = p.L + 1;
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
-    float2* B = A + p.L * WS;
+    float2* B = A + W * LS;
     __shared__ long long off_in[2 * W], off_out[2 * W];
     const long long l0 = (long long)blockIdx.x * (2 * W);
     if (threadIdx.x < 2 * W) {
@@ -355,15 +522,17 @@ __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
         const int jj = j - p.in_off;
         float v = 0.f;
         if (l0 + q < p.nlines && jj >= 0 && jj < p.in_len) v = p.in[off_in[q] + jj];
-        Af[(j * WS + (q >> 1)) * 2 + (q & 1)] = v;
+        Af[((q >> 1) * LS + j) * 2 + (q & 1)] = v;
     }
     __syncthreads();
-    float2* Z = fft_tile<-1, W>(A, B, p.L, p.fac, s_tw);
+    const int warp = threadIdx.x >> 5;
+    float2* Z = warp_fft<-1>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
+    __syncthreads();
     const int H = p.L / 2 + 1;
     for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
         const int i = e / H, k = e - (e / H) * H;
-        const float2 z = Z[k * WS + i];
-        const float2 zm = Z[((p.L - k) % p.L) * WS + i];
+        const float2 z = Z[i * LS + k];
+        const float2 zm = Z[i * LS + ((p.L - k) % p.L)];
         // a = FFT of line 2i, b = FFT of line 2i+1 (two real lines in one complex FFT)
         const float2 a = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
         const float2 b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
@@ -372,15 +541,46 @@ __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
     }
 }
 
-constexpr int kC2RMaxSlots = 16;  // output values per thread in the certificate epilogue
+// Z = A + i B for complex line li from the staged half spectra of real lines
+// 2 li (A) and 2 li + 1 (B), with the Hermitian extension on (L/2, L).
+struct HermLoad {
+    const float2* R;   // raw half spectra, real line q at q * HS
+    int HS, L;
+    __device__ __forceinline__ float2 operator()(int li, int j) const {
+        const bool lo = 2 * j <= L;
+        const int k = lo ? j : L - j;
+        const float2 a = R[(2 * li) * HS + k];
+        const float2 b = R[(2 * li + 1) * HS + k];
+        return lo ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
+    }
+};
 
-template <int W, int MODE>
+constexpr int kC2RMaxSlots = 16;  // max outputs per lane in the certificate epilogue
+
+template <int W>
+__device__ __forceinline__ void stage_half(const C2RPass& p, int s, const long long* off_in,
+                                           long long l0, float2* R, int HS) {
+    const int H = p.L / 2 + 1;
+    const float2* in = p.in + (long long)s * p.in_spec_stride;
+    for (int e = threadIdx.x; e < 2 * W * H; e += blockDim.x) {
+        const int q = e / H, k = e - (e / H) * H;
+        if (l0 + q < p.nlines) cp_async(R + q * HS + k, in + off_in[q] + k, 8);
+        else R[q * HS + k] = make_float2(0.f, 0.f);
+    }
+}
+
+template <int W, int MODE, int SLOTS>
 __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
-    constexpr int WS = W + 1;
+    constexpr int NL = W / 8;
+    const int LS = p.L + 1;
+    const int H = p.L / 2 + 1;
+    const int HS = H + 1;
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
-    float2* B = A + p.L * WS;
+    float2* B = A + W * LS;
+    float2* R0 = B + W * LS;
+    float2* R1 = R0 + 2 * W * HS;
     __shared__ long long off_in[2 * W], off_out[2 * W];
     __shared__ double s_red[kThreads / 32];
     const long long l0 = (long long)blockIdx.x * (2 * W);
@@ -392,40 +592,38 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
         }
     }
     load_twiddles(s_tw, p.tw, p.L);
-    const int H = p.L / 2 + 1;
-    const int nout = 2 * W * p.out_len;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q0 = 2 * NL * warp;                // first real output line of this warp
+    const int nout = 2 * NL * p.out_len;         // outputs of this warp
 
-    float mx[kC2RMaxSlots];
-    int ak[kC2RMaxSlots];
+    float mx[SLOTS];
+    int ak[SLOTS];
     bool saw_nan = false;
     double acc = 0.0;
-    if constexpr (MODE == C2R_CERTMAX) {
 #pragma unroll
-        for (int it = 0; it < kC2RMaxSlots; ++it) {
-            mx[it] = -INFINITY;
-            ak[it] = 0;
-        }
+    for (int it = 0; it < SLOTS; ++it) {
+        mx[it] = -INFINITY;
+        ak[it] = 0;
     }
-    const int nspec = (MODE == C2R_CERTMAX) ? p.nspec : 1;
+    // certificate: grid.y splits the kernels into groups of p.nspec
+    const int k0 = (MODE == C2R_CERTMAX) ? (int)blockIdx.y * p.nspec : 0;
+    const int nspec = (MODE == C2R_CERTMAX) ? min(p.nspec, p.ktotal - k0) : 1;
+    stage_half<W>(p, k0, off_in, l0, R0, HS);
+    cp_async_commit();
     for (int s = 0; s < nspec; ++s) {
+        if (s + 1 < nspec) stage_half<W>(p, k0 + s + 1, off_in, l0, (s & 1) ? R0 : R1, HS);
+        cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
-        const float2* in = p.in + (long long)s * p.in_spec_stride;
-        for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
-            const int i = e / H, k = e - (e / H) * H;
-            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-            if (l0 + 2 * i < p.nlines) a = in[off_in[2 * i] + k];
-            if (l0 + 2 * i + 1 < p.nlines) b = in[off_in[2 * i + 1] + k];
-            // Z = A + i B on [0, L/2], Hermitian extension on (L/2, L)
-            A[k * WS + i] = make_float2(a.x - b.y, a.y + b.x);
-            if (k > 0 && k < p.L - k) A[(p.L - k) * WS + i] = make_float2(a.x + b.y, b.x - a.y);
-        }
-        __syncthreads();
-        float2* z = fft_tile<1, W>(A, B, p.L, p.fac, s_tw);
+        const float2* Rs = (s & 1) ? R1 : R0;
+        float2* z = warp_fft<1>(B, A, p.L, LS, warp * NL, NL, p.fac, s_tw, HermLoad{Rs, HS, p.L});
         if constexpr (MODE != C2R_CERTMAX) {
-            for (int e = threadIdx.x; e < nout; e += blockDim.x) {
-                const int q = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+            for (int e = lane; e < nout; e += 32) {
+                const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+                const int q = q0 + qq;
                 if (l0 + q >= p.nlines) continue;
-                const float2 zz = z[(j + p.out_off) * WS + (q >> 1)];
+                const float2 zz = z[(q >> 1) * LS + j + p.out_off];
                 const float v = ((q & 1) ? zz.y : zz.x) * p.scale;
                 const long long o = off_out[q] + j;
                 if constexpr (MODE == C2R_STORE) {
@@ -437,29 +635,31 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
                 }
             }
         } else {
+            const int kk = k0 + s;
 #pragma unroll
-            for (int it = 0; it < kC2RMaxSlots; ++it) {
-                const int e = threadIdx.x + it * kThreads;
+            for (int it = 0; it < SLOTS; ++it) {
+                const int e = lane + 32 * it;
                 if (e < nout) {
-                    const int q = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+                    const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+                    const int q = q0 + qq;
                     if (l0 + q < p.nlines) {
-                        const float2 zz = z[(j + p.out_off) * WS + (q >> 1)];
+                        const float2 zz = z[(q >> 1) * LS + j + p.out_off];
                         const float v = ((q & 1) ? zz.y : zz.x) * p.scale;
-                        const long long o = off_out[q] + j;
-                        if (p.eta_out) p.eta_out[(long long)s * p.V + o] = v;
+                        if (p.eta_out) p.eta_out[(long long)kk * p.V + off_out[q] + j] = v;
                         if (v != v) saw_nan = true;
                         if (v > mx[it]) {
                             mx[it] = v;
-                            ak[it] = s;
+                            ak[it] = kk;
                         }
                     }
                 }
             }
         }
+        __syncthreads();   // the staged buffer of spectrum s is refilled at s + 2
     }
     if constexpr (MODE == C2R_RESIDUAL) {
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+        if (lane == 0) s_red[warp] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
@@ -470,16 +670,16 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
     if constexpr (MODE == C2R_CERTMAX) {
         unsigned long long best = 0ull;
 #pragma unroll
-        for (int it = 0; it < kC2RMaxSlots; ++it) {
-            const int e = threadIdx.x + it * kThreads;
+        for (int it = 0; it < SLOTS; ++it) {
+            const int e = lane + 32 * it;
             if (e < nout) {
-                const int q = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+                const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+                const int q = q0 + qq;
                 if (l0 + q < p.nlines) {
                     const long long o = off_out[q] + j;
-                    if (p.max_out) p.max_out[o] = mx[it];
-                    if (p.argk_out) p.argk_out[o] = ak[it];
-                    unsigned long long key =
+                    const unsigned long long key =
                         candidate_key(mx[it], (unsigned long long)ak[it] * p.V + o);
+                    if (p.vox_key) atomicMax(p.vox_key + o, key);
                     if (key > best) best = key;
                 }
             }
@@ -490,13 +690,35 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
                 unsigned long long o2 = __shfl_down_sync(0xffffffffu, best, off);
                 if (o2 > best) best = o2;
             }
-            if ((threadIdx.x & 31) == 0 && best) atomicMax(p.best_key, best);
+            if (lane == 0 && best) atomicMax(p.best_key, best);
         }
+    }
+}
+
+// Per-voxel keys -> max over k and its k.
+__global__ void k_vox_decode(const unsigned long long* key, long long V, float* max_out,
+                             int* argk_out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = key[i];
+        float v;
+        int a;
+        if (k == ~0ull) {
+            v = __int_as_float(0x7fc00000);
+            a = 0;
+        } else {
+            v = float_from_order_key((unsigned int)(k >> 32));
+            const unsigned long long flat = 0xffffffffu - (unsigned int)(k & 0xffffffffu);
+            a = (int)(flat / V);
+        }
+        if (max_out) max_out[i] = v;
+        if (argk_out) argk_out[i] = a;
     }
 }
 
 // ------------------------------------------------------------------ launchers
 
+// Lines per CTA: 16 up to length 256, else 8 (shared memory).
 static int tile_width(int L) { return L <= 256 ? 16 : 8; }
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel, size):
@@ -518,14 +740,18 @@ static sfw_status prepare(KernelT kernel, size_t smem) {
     return SFW_OK;
 }
 
-static size_t smem_bytes(int L, int W, int nbuf) {
-    return sizeof(float2) * ((size_t)L + (size_t)nbuf * L * (W + 1));
+static size_t tile_bytes(int L, int W, int nbuf) {
+    return sizeof(float2) * ((size_t)L + (size_t)nbuf * W * (L + 1));
+}
+
+static int spec_bytes(int kind) {
+    return kind == SPEC_C64 ? 8 : kind == SPEC_RBF16 ? 2 : 4;
 }
 
 sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
     if (p.nlines <= 0) return SFW_OK;
     const int W = tile_width(p.L);
-    const size_t smem = smem_bytes(p.L, W, 2);
+    const size_t smem = tile_bytes(p.L, W, 2);
     const unsigned blocks = (unsigned)((p.nlines + W - 1) / W);
 #define SFW_C2C(WW, DD)                                              \
     do {                                                             \
@@ -544,12 +770,15 @@ sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
 sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
     if (p.nlines <= 0) return SFW_OK;
     const int W = tile_width(p.L);
-    const size_t smem = smem_bytes(p.L, W, 3);
+    const int es = spec_bytes(p.spec_kind);
+    const size_t sp = ((size_t)p.L * (W + 16 / es) * es + 15) & ~(size_t)15;
+    const size_t smem = tile_bytes(p.L, W, 3) + 2 * sp;
     const unsigned blocks = (unsigned)((p.nlines + W - 1) / W);
+    const dim3 grid(blocks, (unsigned)((p.ktotal + p.nspec - 1) / p.nspec));
 #define SFW_MUL(WW, KK)                                              \
     do {                                                             \
         SFW_TRY(prepare(k_mul<WW, KK>, smem));                       \
-        SFW_LAUNCH(st, "k_mul", k_mul<WW, KK><<<blocks, kThreads, smem, st>>>(p)); \
+        SFW_LAUNCH(st, "k_mul", k_mul<WW, KK><<<grid, kThreads, smem, st>>>(p)); \
     } while (0)
     switch (p.spec_kind) {
         case SPEC_C64: if (W == 16) SFW_MUL(16, SPEC_C64); else SFW_MUL(8, SPEC_C64); break;
@@ -564,7 +793,7 @@ sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
 sfw_status launch_r2c(const R2CPass& p, cudaStream_t st) {
     if (p.nlines <= 0) return SFW_OK;
     const int W = tile_width(p.L);
-    const size_t smem = smem_bytes(p.L, W, 2);
+    const size_t smem = tile_bytes(p.L, W, 2);
     const unsigned blocks = (unsigned)((p.nlines + 2 * W - 1) / (2 * W));
     if (W == 16) {
         SFW_TRY(prepare(k_r2c<16>, smem));
@@ -576,11 +805,11 @@ sfw_status launch_r2c(const R2CPass& p, cudaStream_t st) {
     return launch_check("k_r2c");
 }
 
-// The certificate epilogue keeps 2W * out_len running maxima in registers.
+// The certificate epilogue keeps 2 (W / 8) * out_len running maxima per warp in
+// registers: SLOTS per lane (4, 8 or 16).  Its tiles are 8 lines wide (more CTAs,
+// fewer registers); the other modes use tile_width.
 static int c2r_width(const C2RPass& p) {
-    int W = tile_width(p.L);
-    if (p.mode == C2R_CERTMAX && 2 * W * p.out_len > kC2RMaxSlots * kThreads) W = 8;
-    return W;
+    return p.mode == C2R_CERTMAX ? 8 : tile_width(p.L);
 }
 
 int c2r_blocks(const C2RPass& p) {
@@ -593,21 +822,35 @@ sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
     const int blocks = c2r_blocks(p);
     if (blocks_out) *blocks_out = blocks;
     if (p.nlines <= 0) return SFW_OK;
-    if (p.mode == C2R_CERTMAX && 2 * W * p.out_len > kC2RMaxSlots * kThreads)
+    const int need = (2 * (W / 8) * p.out_len + 31) / 32;
+    if (p.mode == C2R_CERTMAX && need > kC2RMaxSlots)
         return fail(SFW_ERR_SHAPE, "c2r: %d outputs per line exceed the epilogue tile", p.out_len);
-    const size_t smem = smem_bytes(p.L, W, 2);
-#define SFW_C2R(WW, MM)                                              \
+    const int H = p.L / 2 + 1;
+    const size_t smem = tile_bytes(p.L, W, 2) + sizeof(float2) * 2 * 2 * (size_t)W * (H + 1);
+    const int groups = p.mode == C2R_CERTMAX ? (p.ktotal + p.nspec - 1) / p.nspec : 1;
+    const dim3 grid((unsigned)blocks, (unsigned)groups);
+#define SFW_C2R(WW, MM, SS)                                          \
     do {                                                             \
-        SFW_TRY(prepare(k_c2r<WW, MM>, smem));                       \
-        SFW_LAUNCH(st, "k_c2r", k_c2r<WW, MM><<<blocks, kThreads, smem, st>>>(p)); \
+        SFW_TRY(prepare(k_c2r<WW, MM, SS>, smem));                   \
+        SFW_LAUNCH(st, "k_c2r", k_c2r<WW, MM, SS><<<grid, kThreads, smem, st>>>(p)); \
     } while (0)
     switch (p.mode) {
-        case C2R_STORE: if (W == 16) SFW_C2R(16, C2R_STORE); else SFW_C2R(8, C2R_STORE); break;
-        case C2R_RESIDUAL: if (W == 16) SFW_C2R(16, C2R_RESIDUAL); else SFW_C2R(8, C2R_RESIDUAL); break;
-        default: if (W == 16) SFW_C2R(16, C2R_CERTMAX); else SFW_C2R(8, C2R_CERTMAX); break;
+        case C2R_STORE: if (W == 16) SFW_C2R(16, C2R_STORE, 1); else SFW_C2R(8, C2R_STORE, 1); break;
+        case C2R_RESIDUAL: if (W == 16) SFW_C2R(16, C2R_RESIDUAL, 1); else SFW_C2R(8, C2R_RESIDUAL, 1); break;
+        default:
+            if (need <= 4) SFW_C2R(8, C2R_CERTMAX, 4);
+            else if (need <= 8) SFW_C2R(8, C2R_CERTMAX, 8);
+            else SFW_C2R(8, C2R_CERTMAX, 16);
+            break;
     }
 #undef SFW_C2R
     return launch_check("k_c2r");
+}
+
+sfw_status launch_vox_decode(const unsigned long long* key, long long V, float* max_out,
+                             int* argk_out, cudaStream_t st) {
+    SFW_LAUNCH(st, "k_vox_decode", k_vox_decode<<<1024, 256, 0, st>>>(key, V, max_out, argk_out));
+    return launch_check("k_vox_decode");
 }
 
 }  // namespace sfw

@@ -59,6 +59,7 @@ std::atomic<bool> g_prof_on{false};
 std::vector<ProfRec> g_prof;      // event pool
 size_t g_prof_used = 0;           // records in use
 bool g_prof_dropped = false;
+std::string g_prof_only;          // record only this tag ("" = all)
 bool g_prof_collected = false;
 std::vector<ProfAcc> g_prof_acc;  // per-tag totals
 thread_local const char* t_tag = nullptr;
@@ -87,8 +88,10 @@ void prof_begin(cudaStream_t st, const char* name) {
         g_prof_dropped = true;
         return;
     }
+    const char* tag = t_tag ? t_tag : name;
+    if (!g_prof_only.empty() && g_prof_only != tag) return;
     ProfRec& r = g_prof[g_prof_used++];
-    r.tag = t_tag ? t_tag : name;
+    r.tag = tag;
     cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
     t_open = &r;
 }
@@ -222,6 +225,7 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         p.lspec = ls(0, 1, nl, nl);
         p.spec_stride = 0;
         p.nspec = 1;
+        p.ktotal = 1;
         p.spec_kind = spec_kind;
         p.conj_spec = 0;
         p.out = bufA;
@@ -331,6 +335,7 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
         p.lspec = ls(0, 1, nl, nl);
         p.spec_stride = 0;
         p.nspec = 1;
+        p.ktotal = 1;
         p.spec_kind = spec_kind;
         p.conj_spec = 1;
         p.out = bufA;
@@ -491,6 +496,8 @@ struct sfw_plan {
     float2* cB;
     float2* cC;
     unsigned long long* best_key;
+    unsigned long long* vox_key;  // V per-voxel certificate keys
+    int num_sms;
     unsigned long long* red_scratch;
     long long red_scratch_len;
     size_t ws_bytes;
@@ -659,7 +666,7 @@ extern "C" {
 
 const char* sfw_last_error(void) { return g_err; }
 
-sfw_status sfw_profile_start(int max_launches) {
+sfw_status sfw_profile_start(int max_launches, const char* only_tag) {
     clear_error();
     if (max_launches < 1 || max_launches > (1 << 20)) return fail(SFW_ERR_ARG, "max_launches outside [1, 2^20]");
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -679,6 +686,7 @@ sfw_status sfw_profile_start(int max_launches) {
     g_prof_dropped = false;
     g_prof_collected = false;
     g_prof_acc.clear();
+    g_prof_only = only_tag ? only_tag : "";
     g_prof_on = true;
     return SFW_OK;
 }
@@ -806,6 +814,14 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         p->grad_parts_atoms = 4096;
         if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;
         if ((s = plan_alloc_t(p, &p->best_key, 2))) break;
+        if ((s = plan_alloc_t(p, &p->vox_key, (size_t)p->V))) break;
+        {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            p->num_sms = 0;
+            cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+            if (p->num_sms <= 0) p->num_sms = 1;
+        }
         p->red_scratch_len = 1 << 20;
         if ((s = plan_alloc_t(p, &p->red_scratch, (size_t)p->red_scratch_len))) break;
         if (K > 0) {
@@ -962,7 +978,14 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         q.spec = p->table;
         q.lspec = ls(0, 1, nl, nl);
         q.spec_stride = (long long)P0 * nl;
-        q.nspec = K;
+        q.ktotal = K;
+        {   // split the kernels so that the launch holds about 8 CTAs per SM
+            const long long tiles = (nl + 15) / 16;
+            long long groups = (8LL * p->num_sms + tiles - 1) / tiles;
+            if (groups < 1) groups = 1;
+            if (groups > K) groups = K;
+            q.nspec = (int)((K + groups - 1) / groups);
+        }
         q.spec_kind = p->table_kind;
         q.conj_spec = 0;
         q.out = p->cC;
@@ -996,8 +1019,13 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
             SFW_TRY(launch_c2c(q, st));
         }
     }
+    const bool want_vox = max_out || argk_out;
     if (best_val || best_idx) {
         cudaError_t e = cudaMemsetAsync(p->best_key, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    if (want_vox) {
+        cudaError_t e = cudaMemsetAsync(p->vox_key, 0, sizeof(unsigned long long) * (size_t)p->V, st);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
     }
     C2RPass q;
@@ -1006,7 +1034,7 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     q.lin = ls((long long)n1 * H2, H2, 1, n1);
     q.nlines = (long long)n0 * n1;
     q.in_spec_stride = (long long)n0 * n1 * H2;
-    q.nspec = K;
+    q.ktotal = K;
     q.L = P2;
     q.fac = p->facc[2];
     q.tw = p->twc[2];
@@ -1017,13 +1045,22 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     q.mode = C2R_CERTMAX;
     q.eta_out = eta_out;
     q.V = p->V;
-    q.max_out = max_out;
-    q.argk_out = argk_out;
+    q.vox_key = want_vox ? p->vox_key : nullptr;
     q.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+    // split the kernels into groups so that the launch fills the GPU (about 3 CTAs per SM)
+    q.nspec = K;
+    {
+        const int tiles = c2r_blocks(q);
+        int groups = (8 * p->num_sms + tiles - 1) / tiles;
+        if (groups < 1) groups = 1;
+        if (groups > K) groups = K;
+        q.nspec = (K + groups - 1) / groups;
+    }
     {
         LaunchTag lt__(kCertTags.c2r);
         SFW_TRY(launch_c2r(q, st, nullptr));
     }
+    if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
     if (best_val || best_idx) SFW_TRY(launch_key_decode(p->best_key, best_val, best_idx, st));
     return SFW_OK;
 }

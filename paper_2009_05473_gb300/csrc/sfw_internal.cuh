@@ -121,7 +121,8 @@ struct MulPass {
     const void* spec;
     LineSet lspec;
     long long spec_stride;  // elements between consecutive spectra
-    int nspec;
+    int nspec;              // spectra per CTA (group size; grid.y = groups)
+    int ktotal;             // number of spectra
     int spec_kind;
     int conj_spec;
     float2* out;
@@ -152,7 +153,7 @@ struct C2RPass {
     LineSet lin;          // half-spectrum lines, Sj = 1
     long long nlines;     // real output lines
     long long in_spec_stride;
-    int nspec;
+    int nspec;            // CERTMAX: spectra per CTA (group size); otherwise 1
     int L;
     Factors fac;
     const float2* tw;
@@ -166,8 +167,10 @@ struct C2RPass {
     float* eta_out;       // CERTMAX: K x V or NULL
     long long V;
     float* max_out;       // CERTMAX: V or NULL
-    int* argk_out;        // CERTMAX: V or NULL
+    int* argk_out;        // unused by the kernel (decoded from vox_key)
     unsigned long long* best_key;  // CERTMAX: one key or NULL
+    unsigned long long* vox_key;   // CERTMAX: V per-voxel keys (atomicMax) or NULL
+    int ktotal;           // CERTMAX: number of spectra; grid.y groups them by nspec
 };
 
 // launchers (fft_kernels.cu)
@@ -177,6 +180,8 @@ sfw_status launch_r2c(const R2CPass& p, cudaStream_t st);
 // returns the number of blocks used (for the residual partials) via *blocks
 sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks);
 int c2r_blocks(const C2RPass& p);
+sfw_status launch_vox_decode(const unsigned long long* key, long long V, float* max_out,
+                             int* argk_out, cudaStream_t st);
 
 // ------------------------------------------------------------------ atoms (atoms.cu)
 struct AtomsDev {
