@@ -5,14 +5,16 @@
 // made in Fourier domain").
 //
 // A CTA owns a tile of W lines (W a multiple of 8).  Shared memory holds the
-// tile line-major with an odd pitch L + 1 (no bank conflicts along a line or
-// across lines).  The CTA loads and stores the tile cooperatively (rows of W
-// lines for strided axes, whole lines for the contiguous axis); in between,
-// each warp owns W / 8 lines and runs the butterfly stages on them alone, with
-// __syncwarp between stages.  Radix-R stages read R points L/R apart and write
-// them Ns apart (Stockham), so no bit reversal is needed.  The first stage
-// reads its inputs through a functor, which fuses the spectrum multiply of a
-// convolution or the Hermitian rebuild of a real inverse transform into it.
+// tile line-major with one padding slot every 16 points and an odd line pitch
+// (see phy / pitch), so strided stage writes and cross-line row accesses avoid
+// bank conflicts.  Tiles arrive by cp.async (no register round trip).  The CTA
+// loads and stores the tile cooperatively (rows of W lines for strided axes,
+// whole lines for the contiguous axis); in between, each warp owns W / 8 lines
+// and runs the butterfly stages on them alone, with __syncwarp between stages.
+// Radix-R stages read R points L/R apart and write them Ns apart (Stockham), so
+// no bit reversal is needed.  The first stage reads its inputs through a
+// functor, which fuses the spectrum multiply of a convolution or the Hermitian
+// rebuild of a real inverse transform into it.
 #include <math.h>
 #include <stdio.h>
 
@@ -219,6 +221,17 @@ __device__ __forceinline__ void dft(float2* v) {
     else dft16<DIR>(v);
 }
 
+// ------------------------------------------------------------------ tile layout
+
+// Point j of a line sits at phy(j) = j + j / 16: one padding slot every 16 points
+// makes the strided writes of early Stockham stages (stride R up to 16)
+// bank-conflict free.  Lines are pitch(L) apart (odd, so rows of a tile are too).
+__host__ __device__ __forceinline__ int phy(int j) { return j + (j >> 4); }
+__host__ __device__ __forceinline__ int pitch(int L) {
+    const int q = L + (L >> 4) + 1;
+    return q | 1;
+}
+
 // ------------------------------------------------------------------ warp-level stages
 
 // Radix-R Stockham stage over lines [li0, li0 + nl) of a line-major tile (pitch LS).
@@ -238,7 +251,7 @@ __device__ __forceinline__ void wstage(const float2* __restrict__ src, float2* _
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if constexpr (FIRST) v[r] = load(li, jj + r * LR);
-            else v[r] = src[li * LS + jj + r * LR];
+            else v[r] = src[li * LS + phy(jj + r * LR)];
         }
         if (Ns > 1) {
 #pragma unroll
@@ -251,7 +264,7 @@ __device__ __forceinline__ void wstage(const float2* __restrict__ src, float2* _
         dft<R, DIR>(v);
         const int base = (jj - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[li * LS + base + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) dst[li * LS + phy(base + r * Ns)] = v[r];
     }
     __syncwarp();
 }
@@ -292,7 +305,7 @@ __device__ float2* warp_fft(float2* a, float2* b, int L, int LS, int li0, int nl
 struct SmemLoad {
     const float2* a;
     int LS;
-    __device__ __forceinline__ float2 operator()(int li, int j) const { return a[li * LS + j]; }
+    __device__ __forceinline__ float2 operator()(int li, int j) const { return a[li * LS + phy(j)]; }
 };
 
 __device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* tw, int L) {
@@ -310,15 +323,31 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // ------------------------------------------------------------------ kernels
 
 constexpr int kThreads = 256;
 
+// Rows [in_off, in_off + in_len) of W strided lines -> tile (padded layout), by
+// cp.async (no register round trip); other rows and missing lines are zeroed.
+template <int W>
+__device__ __forceinline__ void load_tile(const float2* in, long long Sj, const long long* off_in,
+                                          long long l0, long long nlines, int in_off, int in_len,
+                                          int L, float2* A, int LS) {
+    for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
+        const int i = e % W, j = e / W;
+        const int jj = j - in_off;
+        float2* dst = A + i * LS + phy(j);
+        if (l0 + i < nlines && jj >= 0 && jj < in_len) cp_async(dst, in + off_in[i] + jj * Sj, 8);
+        else *dst = make_float2(0.f, 0.f);
+    }
+}
+
 template <int W, int DIR>
 __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
     constexpr int NL = W / 8;
-    const int LS = p.L + 1;
+    const int LS = pitch(p.L);
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
@@ -334,13 +363,9 @@ __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
     }
     load_twiddles(s_tw, p.tw, p.L);
     __syncthreads();
-    for (int e = threadIdx.x; e < p.L * W; e += blockDim.x) {
-        const int i = e % W, j = e / W;
-        const int jj = j - p.in_off;
-        float2 v = make_float2(0.f, 0.f);
-        if (l0 + i < p.nlines && jj >= 0 && jj < p.in_len) v = p.in[off_in[i] + jj * p.lin.Sj];
-        A[i * LS + j] = v;
-    }
+    load_tile<W>(p.in, p.lin.Sj, off_in, l0, p.nlines, p.in_off, p.in_len, p.L, A, LS);
+    cp_async_commit();
+    cp_async_wait0();
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     float2* res = warp_fft<DIR>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
@@ -348,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
     for (int e = threadIdx.x; e < p.out_len * W; e += blockDim.x) {
         const int i = e % W, j = e / W;
         if (l0 + i < p.nlines)
-            p.out[off_out[i] + j * p.lout.Sj] = cscale(res[i * LS + j + p.out_off], p.scale);
+            p.out[off_out[i] + j * p.lout.Sj] = cscale(res[i * LS + phy(j + p.out_off)], p.scale);
     }
 }
 
@@ -383,7 +408,7 @@ struct MulLoad {
     __device__ __forceinline__ float2 operator()(int li, int j) const {
         float2 h = spec_value<KIND>(S, j * SW + li);
         if (conj) h.y = -h.y;
-        return cmul(X[li * LS + j], h);
+        return cmul(X[li * LS + phy(j)], h);
     }
 };
 
@@ -441,7 +466,7 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
     constexpr int NL = W / 8;
     constexpr int ES = SpecInfo<KIND>::bytes;
     constexpr int SW = SpecPitch<W, ES>::value;
-    const int LS = p.L + 1;
+    const int LS = pitch(p.L);
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
@@ -468,13 +493,9 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
     // the first spectrum travels while the forward transform runs
     stage_spec<W, KIND>(p, k0, off_spec, l0, SP0);
     cp_async_commit();
-    for (int e = threadIdx.x; e < p.L * W; e += blockDim.x) {
-        const int i = e % W, j = e / W;
-        const int jj = j - p.in_off;
-        float2 v = make_float2(0.f, 0.f);
-        if (l0 + i < p.nlines && jj >= 0 && jj < p.in_len) v = p.in[off_in[i] + jj * p.lin.Sj];
-        A[i * LS + j] = v;
-    }
+    load_tile<W>(p.in, p.lin.Sj, off_in, l0, p.nlines, p.in_off, p.in_len, p.L, A, LS);
+    cp_async_commit();
+    cp_async_wait0();
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     float2* X = warp_fft<-1>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
@@ -492,7 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
         float2* outp = p.out + (long long)(k0 + s) * p.out_stride;
         for (int e = threadIdx.x; e < p.out_len * W; e += blockDim.x) {
             const int i = e % W, j = e / W;
-            if (l0 + i < p.nlines) outp[off_out[i] + j * p.lout.Sj] = res[i * LS + j + p.out_off];
+            if (l0 + i < p.nlines) outp[off_out[i] + j * p.lout.Sj] = res[i * LS + phy(j + p.out_off)];
         }
     }
 }
@@ -500,7 +521,7 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
     constexpr int NL = W / 8;
-    const int LS = p.L + 1;
+    const int LS = pitch(p.L);
     extern __shared__ float4 smem_raw[];
     float2* s_tw = reinterpret_cast<float2*>(smem_raw);
     float2* A = s_tw + p.L;
@@ -520,10 +541,12 @@ __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
     for (int e = threadIdx.x; e < 2 * W * p.L; e += blockDim.x) {
         const int q = e / p.L, j = e - (e / p.L) * p.L;
         const int jj = j - p.in_off;
-        float v = 0.f;
-        if (l0 + q < p.nlines && jj >= 0 && jj < p.in_len) v = p.in[off_in[q] + jj];
-        Af[((q >> 1) * LS + j) * 2 + (q & 1)] = v;
+        float* dst = Af + ((q >> 1) * LS + phy(j)) * 2 + (q & 1);
+        if (l0 + q < p.nlines && jj >= 0 && jj < p.in_len) cp_async(dst, p.in + off_in[q] + jj, 4);
+        else *dst = 0.f;
     }
+    cp_async_commit();
+    cp_async_wait0();
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     float2* Z = warp_fft<-1>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
@@ -531,8 +554,8 @@ __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
     const int H = p.L / 2 + 1;
     for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
         const int i = e / H, k = e - (e / H) * H;
-        const float2 z = Z[i * LS + k];
-        const float2 zm = Z[i * LS + ((p.L - k) % p.L)];
+        const float2 z = Z[i * LS + phy(k)];
+        const float2 zm = Z[i * LS + phy((p.L - k) % p.L)];
         // a = FFT of line 2i, b = FFT of line 2i+1 (two real lines in one complex FFT)
         const float2 a = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
         const float2 b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
@@ -572,7 +595,7 @@ __device__ __forceinline__ void stage_half(const C2RPass& p, int s, const long l
 template <int W, int MODE, int SLOTS>
 __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
     constexpr int NL = W / 8;
-    const int LS = p.L + 1;
+    const int LS = pitch(p.L);
     const int H = p.L / 2 + 1;
     const int HS = H + 1;
     extern __shared__ float4 smem_raw[];
@@ -623,7 +646,7 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
                 const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
                 const int q = q0 + qq;
                 if (l0 + q >= p.nlines) continue;
-                const float2 zz = z[(q >> 1) * LS + j + p.out_off];
+                const float2 zz = z[(q >> 1) * LS + phy(j + p.out_off)];
                 const float v = ((q & 1) ? zz.y : zz.x) * p.scale;
                 const long long o = off_out[q] + j;
                 if constexpr (MODE == C2R_STORE) {
@@ -643,7 +666,7 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
                     const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
                     const int q = q0 + qq;
                     if (l0 + q < p.nlines) {
-                        const float2 zz = z[(q >> 1) * LS + j + p.out_off];
+                        const float2 zz = z[(q >> 1) * LS + phy(j + p.out_off)];
                         const float v = ((q & 1) ? zz.y : zz.x) * p.scale;
                         if (p.eta_out) p.eta_out[(long long)kk * p.V + off_out[q] + j] = v;
                         if (v != v) saw_nan = true;
@@ -741,7 +764,7 @@ static sfw_status prepare(KernelT kernel, size_t smem) {
 }
 
 static size_t tile_bytes(int L, int W, int nbuf) {
-    return sizeof(float2) * ((size_t)L + (size_t)nbuf * W * (L + 1));
+    return sizeof(float2) * ((size_t)L + (size_t)nbuf * W * pitch(L));
 }
 
 static int spec_bytes(int kind) {
