@@ -142,6 +142,24 @@ sfw_status sfw_certificate_grid(sfw_plan* plan, const float* residual, double la
                                 float* eta_out, float* max_out, int32_t* argk_out,
                                 float* best_val, int64_t* best_idx, void* stream);
 
+/* Grid certificate with FP32 re-scoring of the best candidates: the seed of
+ * the local ascent of step 1 (Algorithms 1 and 2) when the grid correlation
+ * runs on a reduced-precision table (SFW_PREC_BF16 plans).
+ * Runs sfw_certificate_grid (per-voxel max over k), takes the topk voxels by
+ * that value (ties -> lower voxel index), forms their parameter rows
+ * (m = voxel position, sigma_k, d_k of the voxel's best k) and re-scores them
+ * in FP32 by the direct sums of sfw_eta_points.
+ *   residual   device n0*n1*n2 floats; lambda > 0; topk in [1, 64]
+ *   cand_theta device topk x 5 floats or NULL: the candidate rows
+ *   cand_grid  device topk floats or NULL: their grid values (table precision)
+ *   cand_eta   device topk doubles or NULL: their re-scored certificates
+ *   best_theta device 5 floats or NULL, best_eta device 1 double or NULL:
+ *              the candidate with the largest re-scored value (ties -> first).
+ * A NaN in the certificate makes the rows NaN.  Asynchronous. */
+sfw_status sfw_certificate_topk(sfw_plan* plan, const float* residual, double lambda, int topk,
+                                float* cand_theta, float* cand_grid, double* cand_eta,
+                                float* best_theta, double* best_eta, void* stream);
+
 /* Certificate of Eq. 5 at arbitrary (off-grid) parameters, with its
  * gradient: the objective of the local ascent of step 1 ("local ascent using
  * e.g. BFGS, starting from a maximum attained on a grid") and the FP32
@@ -191,7 +209,8 @@ sfw_status sfw_argmax_noalloc(const float* values, int64_t count, int topk, floa
  *   atoms     device atom set, N >= 1
  *   lambda    >= 0
  *   loss_out  device 1 double: C = 1/2 sum (y - Phi mu)^2 + lambda sum w
- *   grad_out  device 6N doubles: [dC/dm (N x 3, row-major) | dC/dsigma (N) |
+ *   grad_out  device 6N doubles or NULL (loss only: no back-projection and
+ *             no adjoint): [dC/dm (N x 3, row-major) | dC/dsigma (N) |
  *             dC/dd (N) | dC/dw (N)], with b = Phi^T r on E,
  *               dC/dw_n = lambda - sum_t g_n(t) b(t),
  *               dC/dtheta_n = -w_n sum_t (d g_n / d theta)(t) b(t)

@@ -12,7 +12,7 @@ with ctypes.  This file adds, in numpy, float64:
     back-projection -> per-atom sums);
   * Fourier-domain variants of the blur, back-projection and grid certificate
     (Section 2 states that convolutions are made in the Fourier domain).  A
-    library FFT is one step; the result equals the direct definition up to
+    library FFT (scipy.fft, all host threads) is one step; the result equals the direct definition up to
     rounding.  They are pinned against the direct sums in the tests and only
     make the larger cases affordable;
   * the certificate on the grid (positions x sigma-list x d-list) and its
@@ -37,6 +37,7 @@ import subprocess
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
+import scipy.fft as sfft
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sfw_oracle.c")
@@ -175,6 +176,18 @@ def _fft_shape(shape) -> Tuple[int, ...]:
     return tuple(int(s) for s in shape)
 
 
+_WORKERS = os.cpu_count() or 1
+_AX = (0, 1, 2)
+
+
+def _rfftn(a, shape):
+    return sfft.rfftn(a, shape, axes=_AX, workers=_WORKERS)
+
+
+def _irfftn(a, shape):
+    return sfft.irfftn(a, shape, axes=_AX, workers=_WORKERS)
+
+
 def _wrapped_psf(psf, R, P) -> np.ndarray:
     """H(u), u in [-R, R], stored at u mod P (circular layout of the kernel)."""
     Hp = np.zeros(P)
@@ -187,7 +200,7 @@ def forward_fft(n, R, psf, f) -> np.ndarray:
     E = ext_shape(n, R)
     P = _fft_shape(E)
     Hp = _wrapped_psf(psf, R, P)
-    out = np.fft.irfftn(np.fft.rfftn(f, P, axes=(0, 1, 2)) * np.fft.rfftn(Hp, P, axes=(0, 1, 2)), P, axes=(0, 1, 2))
+    out = _irfftn(_rfftn(f, P) * _rfftn(Hp, P), P)
     return out[R[0]:R[0] + n[0], R[1]:R[1] + n[1], R[2]:R[2] + n[2]].copy()
 
 
@@ -198,7 +211,7 @@ def backproject_fft(n, R, psf, r) -> np.ndarray:
     Hp = _wrapped_psf(psf, R, P)
     rE = np.zeros(P)
     rE[R[0]:R[0] + n[0], R[1]:R[1] + n[1], R[2]:R[2] + n[2]] = r
-    return np.fft.irfftn(np.fft.rfftn(rE, P, axes=(0, 1, 2)) * np.conj(np.fft.rfftn(Hp, P, axes=(0, 1, 2))), P, axes=(0, 1, 2))
+    return _irfftn(_rfftn(rE, P) * np.conj(_rfftn(Hp, P)), P)
 
 
 def forward(n, R, psf, m, sigma, d, w, fft=False) -> np.ndarray:
@@ -261,11 +274,11 @@ def eta_grid_fft(n, R, psf, r, lam, kernels, b=None) -> np.ndarray:
         b = backproject_fft(n, R, psf, r)
     half = tuple(int(a) + int(rr) - 1 for a, rr in zip(n, R))      # |t - R - m| <= n + R - 1
     Q = tuple(2 * h + 1 for h in half)
-    Bh = np.fft.rfftn(b, Q, axes=(0, 1, 2))
+    Bh = _rfftn(b, Q)
     out = np.empty((len(kernels),) + tuple(n))
     for k, (s, dd) in enumerate(kernels):
         g = atom_profile_window(half, s, dd)                      # g is even: correlation == conv
-        c = np.fft.irfftn(Bh * np.fft.rfftn(g, Q, axes=(0, 1, 2)), Q, axes=(0, 1, 2))             # c[z + half] = sum_t b(t) g(z - t)
+        c = _irfftn(Bh * _rfftn(g, Q), Q)                         # c[z + half] = sum_t b(t) g(z - t)
         out[k] = c[R[0] + half[0]:R[0] + half[0] + n[0], R[1] + half[1]:R[1] + half[1] + n[1],
                    R[2] + half[2]:R[2] + half[2] + n[2]] / lam
     return out

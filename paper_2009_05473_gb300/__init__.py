@@ -15,7 +15,8 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 
 from . import _abi
-from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_eta_points, sfw_forward,  # noqa: F401
+from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_topk,  # noqa: F401
+                   sfw_eta_points, sfw_forward,
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
                    sfw_slide_loss_grad, sfw_version)
 
@@ -164,6 +165,19 @@ class Plan:
         return {"eta": eta if want_eta else None, "max": mx if want_max else None,
                 "argk": ak if want_max else None, "best_val": bv, "best_idx": bi}
 
+    def certificate_topk(self, residual, lam: float, topk: int = 64, stream=None):
+        """Grid certificate, its topk voxels and their FP32 re-scores: dict with theta
+        (topk, 5), grid (topk), eta (topk, FP64 output of FP32 sums), best_theta (5), best_eta."""
+        torch = _torch()
+        th = torch.empty((topk, 5), dtype=torch.float32, device="cuda")
+        gv = torch.empty(topk, dtype=torch.float32, device="cuda")
+        ev = torch.empty(topk, dtype=torch.float64, device="cuda")
+        bt = torch.empty(5, dtype=torch.float32, device="cuda")
+        be = torch.empty(1, dtype=torch.float64, device="cuda")
+        sfw_certificate_topk(self.handle, _ptr(residual), lam, topk, _ptr(th), _ptr(gv), _ptr(ev),
+                             _ptr(bt), _ptr(be), _stream_ptr(stream))
+        return {"theta": th, "grid": gv, "eta": ev, "best_theta": bt, "best_eta": be}
+
     def eta_points(self, residual, lam: float, theta, with_grad: bool = True, stream=None):
         """eta (and d eta / d theta) at rows theta = (m0, m1, m2, sigma, d), FP32 sums."""
         torch = _torch()
@@ -176,15 +190,15 @@ class Plan:
         return (eta, grad) if with_grad else eta
 
     def slide_loss_grad(self, y, atoms: AtomSet, lam: float, want_residual: bool = False,
-                        stream=None, out=None):
-        """(loss (1 double), grad (6N doubles), residual or None) of the sliding step."""
+                        stream=None, out=None, want_grad: bool = True):
+        """(loss (1 double), grad (6N doubles) or None, residual or None) of the sliding step."""
         torch = _torch()
         out = out or {}
         loss = out.get("loss")
         if loss is None:
             loss = torch.empty(1, dtype=torch.float64, device="cuda")
-        grad = out.get("grad")
-        if grad is None or grad.numel() != 6 * atoms.N:
+        grad = out.get("grad") if want_grad else None
+        if want_grad and (grad is None or grad.numel() != 6 * atoms.N):
             grad = torch.empty(6 * atoms.N, dtype=torch.float64, device="cuda")
         r = out.get("residual")
         if want_residual and r is None:

@@ -21,7 +21,7 @@ SFW_PREC_BF16 = 1
 
 # every symbol declared in include/sfw.h
 EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
-           "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
+           "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
            "sfw_slide_loss_grad", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
            "sfw_launch_count",
            "sfw_version")
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_forward.argtypes = [vp, ctypes.POINTER(Atoms), vp, vp]
     L.sfw_certificate_grid.argtypes = [vp, vp, dbl, vp, vp, vp, vp, vp, vp]
     L.sfw_eta_points.argtypes = [vp, vp, dbl, i32, vp, vp, vp, vp]
+    L.sfw_certificate_topk.argtypes = [vp, vp, dbl, i32, vp, vp, vp, vp, vp, vp]
     L.sfw_argmax.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_argmax_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
@@ -77,7 +78,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
-                 "sfw_certificate_grid", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
+                 "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
                  "sfw_slide_loss_grad", "sfw_profile_start", "sfw_profile_collect",
                  "sfw_profile_stop"):
         getattr(L, name).restype = ctypes.c_int
@@ -122,6 +123,13 @@ def sfw_certificate_grid(plan: int, residual: int, lam: float, eta_out: int, max
                          argk_out: int, best_val: int, best_idx: int, stream: int) -> None:
     check(lib().sfw_certificate_grid(plan, residual, float(lam), eta_out, max_out, argk_out,
                                      best_val, best_idx, stream), "sfw_certificate_grid")
+
+
+def sfw_certificate_topk(plan: int, residual: int, lam: float, topk: int, cand_theta: int,
+                         cand_grid: int, cand_eta: int, best_theta: int, best_eta: int,
+                         stream: int) -> None:
+    check(lib().sfw_certificate_topk(plan, residual, float(lam), int(topk), cand_theta, cand_grid,
+                                     cand_eta, best_theta, best_eta, stream), "sfw_certificate_topk")
 
 
 def sfw_eta_points(plan: int, residual: int, lam: float, P: int, theta: int, eta_out: int,

@@ -251,6 +251,58 @@ sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3]
     return launch_check("k_eta_finalize");
 }
 
+// ------------------------------------------------------------------ top-k re-scoring
+
+__global__ void k_candidate_theta(const int64_t* vox, const int* argk, const float* grid_sd,
+                                  int topk, int n0, int n1, int n2, float* theta) {
+    const int i = threadIdx.x;
+    if (i >= topk) return;
+    const int64_t v = vox[i];
+    if (v < 0) {  // NaN in the certificate: no candidate
+        for (int q = 0; q < 5; ++q) theta[5 * i + q] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int k = argk[v];
+    theta[5 * i + 0] = (float)(v / ((int64_t)n1 * n2));
+    theta[5 * i + 1] = (float)((v / n2) % n1);
+    theta[5 * i + 2] = (float)(v % n2);
+    theta[5 * i + 3] = grid_sd[2 * k];
+    theta[5 * i + 4] = grid_sd[2 * k + 1];
+}
+
+sfw_status launch_candidate_theta(const int64_t* vox, const int* argk, const float* grid_sd,
+                                  int topk, const int n[3], float* theta, cudaStream_t st) {
+    SFW_LAUNCH(st, "k_candidate_theta", k_candidate_theta<<<1, 64, 0, st>>>(vox, argk, grid_sd, topk, n[0], n[1], n[2], theta));
+    return launch_check("k_candidate_theta");
+}
+
+__global__ void k_candidate_select(const float* theta, const float* grid_val, const double* eta,
+                                   int topk, float* theta_out, float* grid_out, double* eta_out,
+                                   float* best_theta, double* best_eta) {
+    const int i = threadIdx.x;
+    if (i < topk) {
+        if (theta_out)
+            for (int q = 0; q < 5; ++q) theta_out[5 * i + q] = theta[5 * i + q];
+        if (grid_out) grid_out[i] = grid_val[i];
+        if (eta_out) eta_out[i] = eta[i];
+    }
+    if (i == 0) {
+        int b = 0;
+        for (int j = 1; j < topk; ++j)
+            if (eta[j] > eta[b]) b = j;
+        if (best_theta)
+            for (int q = 0; q < 5; ++q) best_theta[q] = theta[5 * b + q];
+        if (best_eta) *best_eta = eta[b];
+    }
+}
+
+sfw_status launch_candidate_select(const float* theta, const float* grid_val, const double* eta,
+                                   int topk, float* theta_out, float* grid_out, double* eta_out,
+                                   float* best_theta, double* best_eta, cudaStream_t st) {
+    SFW_LAUNCH(st, "k_candidate_select", k_candidate_select<<<1, 64, 0, st>>>(theta, grid_val, eta, topk, theta_out, grid_out, eta_out, best_theta, best_eta));
+    return launch_check("k_candidate_select");
+}
+
 // ------------------------------------------------------------------ loss
 
 __global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, double lambda,

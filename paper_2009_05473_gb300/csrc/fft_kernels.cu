@@ -18,11 +18,7 @@
 #include <math.h>
 #include <stdio.h>
 
-#include <map>
-#include <mutex>
-#include <utility>
-
-#include "sfw_internal.cuh"
+#include "fft_core.cuh"
 
 namespace sfw {
 
@@ -83,639 +79,54 @@ void TwiddleCache::release() {
     tables.clear();
 }
 
-// ------------------------------------------------------------------ device arithmetic
+// ------------------------------------------------------------------ length dispatch
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-// a * (DIR * i)
-template <int DIR>
-__device__ __forceinline__ float2 mul_i(float2 a) {
-    return DIR > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-}
+// Lengths with compile-time specialisations (fft_len_*.cu); others run generic code.
+#define SFW_FFT_LENGTHS(X) X(64) X(80) X(96) X(128) X(160) X(256)
+SFW_FFT_DECLARE(0)
+#define SFW_DECL(LL) SFW_FFT_DECLARE(LL)
+SFW_FFT_LENGTHS(SFW_DECL)
+#undef SFW_DECL
 
-// Small DFTs: X[q] = sum_r v[r] exp(DIR 2 pi i r q / R).
-template <int DIR>
-__device__ __forceinline__ void dft2(float2* v) {
-    float2 a = v[0];
-    v[0] = cadd(a, v[1]);
-    v[1] = csub(a, v[1]);
-}
-
-template <int DIR>
-__device__ __forceinline__ void dft4v(float2& v0, float2& v1, float2& v2, float2& v3) {
-    float2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), t3 = mul_i<DIR>(csub(v1, v3));
-    v0 = cadd(t0, t2);
-    v2 = csub(t0, t2);
-    v1 = cadd(t1, t3);
-    v3 = csub(t1, t3);
-}
-
-template <int DIR>
-__device__ __forceinline__ void dft4(float2* v) { dft4v<DIR>(v[0], v[1], v[2], v[3]); }
-
-template <int DIR>
-__device__ __forceinline__ void dft8(float2* v) {
-    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
-    dft4v<DIR>(e0, e1, e2, e3);
-    dft4v<DIR>(o0, o1, o2, o3);
-    const float c = 0.70710678118654752440f;
-    // w = exp(DIR 2 pi i / 8): w^1 = c (1, DIR), w^2 = DIR i, w^3 = c (-1, DIR)
-    float2 p1 = make_float2(c * (o1.x - DIR * o1.y), c * (o1.y + DIR * o1.x));
-    float2 p2 = mul_i<DIR>(o2);
-    float2 p3 = make_float2(c * (-o3.x - DIR * o3.y), c * (DIR * o3.x - o3.y));
-    v[0] = cadd(e0, o0);
-    v[4] = csub(e0, o0);
-    v[1] = cadd(e1, p1);
-    v[5] = csub(e1, p1);
-    v[2] = cadd(e2, p2);
-    v[6] = csub(e2, p2);
-    v[3] = cadd(e3, p3);
-    v[7] = csub(e3, p3);
-}
-
-template <int DIR>
-__device__ __forceinline__ void dft3(float2* v) {
-    const float s3 = 0.86602540378443864676f;  // sin(2 pi / 3)
-    float2 t = cadd(v[1], v[2]);
-    float2 u = csub(v[1], v[2]);
-    float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
-    float2 s = mul_i<DIR>(cscale(u, s3));
-    v[0] = cadd(v[0], t);
-    v[1] = cadd(m, s);
-    v[2] = csub(m, s);
-}
-
-template <int DIR>
-__device__ __forceinline__ void dft5(float2* v) {
-    const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
-    const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
-    const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
-    const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
-    float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-    float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-    float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
-    float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
-    float2 b1 = mul_i<DIR>(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
-    float2 b2 = mul_i<DIR>(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
-    v[0] = cadd(v[0], cadd(t1, t2));
-    v[1] = cadd(a1, b1);
-    v[4] = csub(a1, b1);
-    v[2] = cadd(a2, b2);
-    v[3] = csub(a2, b2);
-}
-
-// a * (c + DIR i s)
-template <int DIR>
-__device__ __forceinline__ float2 cmulc(float2 a, float c, float s) {
-    return make_float2(a.x * c - DIR * a.y * s, a.y * c + DIR * a.x * s);
-}
-
-// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2.
-template <int DIR>
-__device__ __forceinline__ void dft16(float2* v) {
-    float2 a[4][4];
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-        float2 x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
-        dft4v<DIR>(x0, x1, x2, x3);
-        a[n2][0] = x0;
-        a[n2][1] = x1;
-        a[n2][2] = x2;
-        a[n2][3] = x3;
-    }
-    const float c1 = 0.92387953251128675613f;  // cos(pi / 8)
-    const float s1 = 0.38268343236508977173f;  // sin(pi / 8)
-    const float h = 0.70710678118654752440f;
-    a[1][1] = cmulc<DIR>(a[1][1], c1, s1);    // W16^1
-    a[1][2] = cmulc<DIR>(a[1][2], h, h);      // W16^2
-    a[1][3] = cmulc<DIR>(a[1][3], s1, c1);    // W16^3
-    a[2][1] = cmulc<DIR>(a[2][1], h, h);      // W16^2
-    a[2][2] = mul_i<DIR>(a[2][2]);            // W16^4
-    a[2][3] = cmulc<DIR>(a[2][3], -h, h);     // W16^6
-    a[3][1] = cmulc<DIR>(a[3][1], s1, c1);    // W16^3
-    a[3][2] = cmulc<DIR>(a[3][2], -h, h);     // W16^6
-    a[3][3] = cmulc<DIR>(a[3][3], -c1, -s1);  // W16^9
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-        float2 y0 = a[0][k1], y1 = a[1][k1], y2 = a[2][k1], y3 = a[3][k1];
-        dft4v<DIR>(y0, y1, y2, y3);
-        v[k1] = y0;
-        v[k1 + 4] = y1;
-        v[k1 + 8] = y2;
-        v[k1 + 12] = y3;
+sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
+    switch (p.L) {
+#define SFW_CASE(LL) case LL: return run_c2c<LL>(p, st);
+        SFW_FFT_LENGTHS(SFW_CASE)
+#undef SFW_CASE
+        default: return run_c2c<0>(p, st);
     }
 }
 
-template <int R, int DIR>
-__device__ __forceinline__ void dft(float2* v) {
-    if constexpr (R == 2) dft2<DIR>(v);
-    else if constexpr (R == 3) dft3<DIR>(v);
-    else if constexpr (R == 4) dft4<DIR>(v);
-    else if constexpr (R == 5) dft5<DIR>(v);
-    else if constexpr (R == 8) dft8<DIR>(v);
-    else dft16<DIR>(v);
-}
-
-// ------------------------------------------------------------------ tile layout
-
-// Point j of a line sits at phy(j) = j + j / 16: one padding slot every 16 points
-// makes the strided writes of early Stockham stages (stride R up to 16)
-// bank-conflict free.  Lines are pitch(L) apart (odd, so rows of a tile are too).
-__host__ __device__ __forceinline__ int phy(int j) { return j + (j >> 4); }
-__host__ __device__ __forceinline__ int pitch(int L) {
-    const int q = L + (L >> 4) + 1;
-    return q | 1;
-}
-
-// ------------------------------------------------------------------ warp-level stages
-
-// Radix-R Stockham stage over lines [li0, li0 + nl) of a line-major tile (pitch LS).
-template <int R, int DIR, bool FIRST, class Load>
-__device__ __forceinline__ void wstage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                       int L, int LS, int li0, int nl, int Ns,
-                                       const float2* __restrict__ tw, const Load& load) {
-    const int LR = L / R;
-    const int tstep = L / (Ns * R);
-    const int total = LR * nl;
-    for (int t = (int)(threadIdx.x & 31); t < total; t += 32) {
-        const int lq = t / LR;
-        const int jj = t - lq * LR;
-        const int li = li0 + lq;
-        const int k = jj % Ns;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if constexpr (FIRST) v[r] = load(li, jj + r * LR);
-            else v[r] = src[li * LS + phy(jj + r * LR)];
-        }
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = tw[k * r * tstep];
-                if (DIR > 0) w.y = -w.y;
-                v[r] = cmul(v[r], w);
-            }
-        }
-        dft<R, DIR>(v);
-        const int base = (jj - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[li * LS + phy(base + r * Ns)] = v[r];
-    }
-    __syncwarp();
-}
-
-template <int DIR, bool FIRST, class Load>
-__device__ __forceinline__ void wstage_any(int R, const float2* src, float2* dst, int L, int LS,
-                                           int li0, int nl, int Ns, const float2* tw, const Load& load) {
-    switch (R) {
-        case 16: wstage<16, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
-        case 8: wstage<8, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
-        case 4: wstage<4, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
-        case 2: wstage<2, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
-        case 3: wstage<3, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
-        default: wstage<5, DIR, FIRST>(src, dst, L, LS, li0, nl, Ns, tw, load); break;
+sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
+    switch (p.L) {
+#define SFW_CASE(LL) case LL: return run_mul<LL>(p, st);
+        SFW_FFT_LENGTHS(SFW_CASE)
+#undef SFW_CASE
+        default: return run_mul<0>(p, st);
     }
 }
 
-// Transform of this warp's lines.  Stage 0 reads through `load` and writes b;
-// later stages alternate a <- b <- a ...  Returns the buffer with the result.
-template <int DIR, class Load>
-__device__ float2* warp_fft(float2* a, float2* b, int L, int LS, int li0, int nl,
-                            const Factors& fac, const float2* tw, const Load& load) {
-    int Ns = 1;
-    wstage_any<DIR, true>(fac.r[0], nullptr, b, L, LS, li0, nl, Ns, tw, load);
-    Ns *= fac.r[0];
-    float2* src = b;
-    float2* dst = a;
-    for (int s = 1; s < fac.n; ++s) {
-        wstage_any<DIR, false>(fac.r[s], src, dst, L, LS, li0, nl, Ns, tw, load);
-        Ns *= fac.r[s];
-        float2* t = src;
-        src = dst;
-        dst = t;
-    }
-    return src;
-}
-
-struct SmemLoad {
-    const float2* a;
-    int LS;
-    __device__ __forceinline__ float2 operator()(int li, int j) const { return a[li * LS + phy(j)]; }
-};
-
-__device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* tw, int L) {
-    for (int j = threadIdx.x; j < L; j += blockDim.x) s_tw[j] = tw[j];
-}
-
-// ------------------------------------------------------------------ cp.async helpers
-
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-// ------------------------------------------------------------------ kernels
-
-constexpr int kThreads = 256;
-
-// Rows [in_off, in_off + in_len) of W strided lines -> tile (padded layout), by
-// cp.async (no register round trip); other rows and missing lines are zeroed.
-template <int W>
-__device__ __forceinline__ void load_tile(const float2* in, long long Sj, const long long* off_in,
-                                          long long l0, long long nlines, int in_off, int in_len,
-                                          int L, float2* A, int LS) {
-    for (int e = threadIdx.x; e < L * W; e += blockDim.x) {
-        const int i = e % W, j = e / W;
-        const int jj = j - in_off;
-        float2* dst = A + i * LS + phy(j);
-        if (l0 + i < nlines && jj >= 0 && jj < in_len) cp_async(dst, in + off_in[i] + jj * Sj, 8);
-        else *dst = make_float2(0.f, 0.f);
+sfw_status launch_r2c(const R2CPass& p, cudaStream_t st) {
+    switch (p.L) {
+#define SFW_CASE(LL) case LL: return run_r2c<LL>(p, st);
+        SFW_FFT_LENGTHS(SFW_CASE)
+#undef SFW_CASE
+        default: return run_r2c<0>(p, st);
     }
 }
 
-template <int W, int DIR>
-__global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
-    constexpr int NL = W / 8;
-    const int LS = pitch(p.L);
-    extern __shared__ float4 smem_raw[];
-    float2* s_tw = reinterpret_cast<float2*>(smem_raw);
-    float2* A = s_tw + p.L;
-    float2* B = A + W * LS;
-    __shared__ long long off_in[W], off_out[W];
-    const long long l0 = (long long)blockIdx.x * W;
-    if (threadIdx.x < W) {
-        long long l = l0 + threadIdx.x;
-        if (l < p.nlines) {
-            off_in[threadIdx.x] = line_offset(p.lin, l);
-            off_out[threadIdx.x] = line_offset(p.lout, l);
-        }
-    }
-    load_twiddles(s_tw, p.tw, p.L);
-    __syncthreads();
-    load_tile<W>(p.in, p.lin.Sj, off_in, l0, p.nlines, p.in_off, p.in_len, p.L, A, LS);
-    cp_async_commit();
-    cp_async_wait0();
-    __syncthreads();
-    const int warp = threadIdx.x >> 5;
-    float2* res = warp_fft<DIR>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
-    __syncthreads();
-    for (int e = threadIdx.x; e < p.out_len * W; e += blockDim.x) {
-        const int i = e % W, j = e / W;
-        if (l0 + i < p.nlines)
-            p.out[off_out[i] + j * p.lout.Sj] = cscale(res[i * LS + phy(j + p.out_off)], p.scale);
+sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
+    switch (p.L) {
+#define SFW_CASE(LL) case LL: return run_c2r<LL>(p, st, blocks_out);
+        SFW_FFT_LENGTHS(SFW_CASE)
+#undef SFW_CASE
+        default: return run_c2r<0>(p, st, blocks_out);
     }
 }
 
-template <int KIND>
-struct SpecInfo;
-template <> struct SpecInfo<SPEC_C64> { static constexpr int bytes = 8; };
-template <> struct SpecInfo<SPEC_R32> { static constexpr int bytes = 4; };
-template <> struct SpecInfo<SPEC_CBF16> { static constexpr int bytes = 4; };
-template <> struct SpecInfo<SPEC_RBF16> { static constexpr int bytes = 2; };
-
-template <int KIND>
-__device__ __forceinline__ float2 spec_value(const unsigned char* base, int idx) {
-    if constexpr (KIND == SPEC_C64) {
-        return reinterpret_cast<const float2*>(base)[idx];
-    } else if constexpr (KIND == SPEC_R32) {
-        return make_float2(reinterpret_cast<const float*>(base)[idx], 0.f);
-    } else if constexpr (KIND == SPEC_CBF16) {
-        return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[idx]);
-    } else {
-        return make_float2(__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[idx]), 0.f);
-    }
-}
-
-// X[li][j] times the staged spectrum tile S[j][li] (row pitch SW), optionally conjugated.
-template <int KIND>
-struct MulLoad {
-    const float2* X;
-    int LS;
-    const unsigned char* S;
-    int SW;
-    int conj;
-    __device__ __forceinline__ float2 operator()(int li, int j) const {
-        float2 h = spec_value<KIND>(S, j * SW + li);
-        if (conj) h.y = -h.y;
-        return cmul(X[li * LS + phy(j)], h);
-    }
-};
-
-// Row pitch (elements) of a staged spectrum tile: W lines padded to a multiple of 16 bytes
-// plus 16 bytes, so rows can be filled with 16-byte copies and read without bank conflicts.
-template <int W, int ES>
-struct SpecPitch {
-    static constexpr int value = W + 16 / ES;
-};
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-
-// Stage spectrum s of the tile (rows j < L of W lines) into shared memory S[j][i].
-// A row whose W values are all present and 16-byte aligned travels as 16-byte
-// cp.async chunks; other rows are copied element by element.
-template <int W, int KIND>
-__device__ __forceinline__ void stage_spec(const MulPass& p, int s, const long long* off_spec,
-                                           long long l0, unsigned char* S) {
-    constexpr int ES = SpecInfo<KIND>::bytes;
-    constexpr int SW = SpecPitch<W, ES>::value;
-    constexpr int CH = W * ES / 16;   // 16-byte chunks per full row
-    const unsigned char* base = reinterpret_cast<const unsigned char*>(p.spec);
-    const long long sbase = (long long)s * p.spec_stride;
-    const bool full = l0 + W <= p.nlines && off_spec[W - 1] == off_spec[0] + (W - 1);
-    for (int e = threadIdx.x; e < p.L * CH; e += blockDim.x) {
-        const int j = e / CH, c = e - (e / CH) * CH;
-        unsigned char* drow = S + (size_t)j * SW * ES;
-        const unsigned char* srow = base + (size_t)(sbase + off_spec[0] + j * p.lspec.Sj) * ES;
-        if (full && ((reinterpret_cast<uintptr_t>(srow) & 15) == 0)) {
-            cp_async16(drow + 16 * c, srow + 16 * c);
-        } else {
-            // element-wise: chunk c covers lines [c * 16 / ES, (c + 1) * 16 / ES)
-            for (int i = c * (16 / ES); i < (c + 1) * (16 / ES); ++i) {
-                unsigned char* dst = drow + (size_t)i * ES;
-                if (l0 + i < p.nlines) {
-                    const unsigned char* src = base + (size_t)(sbase + off_spec[i] + j * p.lspec.Sj) * ES;
-                    if constexpr (ES == 8) *reinterpret_cast<float2*>(dst) = *reinterpret_cast<const float2*>(src);
-                    else if constexpr (ES == 4) *reinterpret_cast<float*>(dst) = *reinterpret_cast<const float*>(src);
-                    else *reinterpret_cast<unsigned short*>(dst) = *reinterpret_cast<const unsigned short*>(src);
-                } else {
-                    if constexpr (ES == 8) *reinterpret_cast<float2*>(dst) = make_float2(0.f, 0.f);
-                    else if constexpr (ES == 4) *reinterpret_cast<float*>(dst) = 0.f;
-                    else *reinterpret_cast<unsigned short*>(dst) = 0;
-                }
-            }
-        }
-    }
-}
-
-template <int W, int KIND>
-__global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
-    constexpr int NL = W / 8;
-    constexpr int ES = SpecInfo<KIND>::bytes;
-    constexpr int SW = SpecPitch<W, ES>::value;
-    const int LS = pitch(p.L);
-    extern __shared__ float4 smem_raw[];
-    float2* s_tw = reinterpret_cast<float2*>(smem_raw);
-    float2* A = s_tw + p.L;
-    float2* B = A + W * LS;
-    float2* C = B + W * LS;
-    const size_t sp_bytes = (((size_t)p.L * SW * ES) + 15) & ~(size_t)15;
-    unsigned char* SP0 = reinterpret_cast<unsigned char*>(C + W * LS);
-    unsigned char* SP1 = SP0 + sp_bytes;
-    __shared__ long long off_in[W], off_out[W], off_spec[W];
-    const long long l0 = (long long)blockIdx.x * W;
-    if (threadIdx.x < W) {
-        long long l = l0 + threadIdx.x;
-        if (l < p.nlines) {
-            off_in[threadIdx.x] = line_offset(p.lin, l);
-            off_out[threadIdx.x] = line_offset(p.lout, l);
-            off_spec[threadIdx.x] = line_offset(p.lspec, l);
-        }
-    }
-    load_twiddles(s_tw, p.tw, p.L);
-    __syncthreads();
-    // grid.y splits the spectra into groups of p.nspec
-    const int k0 = (int)blockIdx.y * p.nspec;
-    const int nspec = min(p.nspec, p.ktotal - k0);
-    // the first spectrum travels while the forward transform runs
-    stage_spec<W, KIND>(p, k0, off_spec, l0, SP0);
-    cp_async_commit();
-    load_tile<W>(p.in, p.lin.Sj, off_in, l0, p.nlines, p.in_off, p.in_len, p.L, A, LS);
-    cp_async_commit();
-    cp_async_wait0();
-    __syncthreads();
-    const int warp = threadIdx.x >> 5;
-    float2* X = warp_fft<-1>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
-    float2* U = (X == A) ? B : A;
-    float2* V = C;
-    for (int s = 0; s < nspec; ++s) {
-        if (s + 1 < nspec) stage_spec<W, KIND>(p, k0 + s + 1, off_spec, l0, (s & 1) ? SP0 : SP1);
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const unsigned char* S = (s & 1) ? SP1 : SP0;
-        float2* res = warp_fft<1>(V, U, p.L, LS, warp * NL, NL, p.fac, s_tw,
-                                  MulLoad<KIND>{X, LS, S, SW, p.conj_spec});
-        __syncthreads();
-        float2* outp = p.out + (long long)(k0 + s) * p.out_stride;
-        for (int e = threadIdx.x; e < p.out_len * W; e += blockDim.x) {
-            const int i = e % W, j = e / W;
-            if (l0 + i < p.nlines) outp[off_out[i] + j * p.lout.Sj] = res[i * LS + phy(j + p.out_off)];
-        }
-    }
-}
-
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
-    constexpr int NL = W / 8;
-    const int LS = pitch(p.L);
-    extern __shared__ float4 smem_raw[];
-    float2* s_tw = reinterpret_cast<float2*>(smem_raw);
-    float2* A = s_tw + p.L;
-    float2* B = A + W * LS;
-    __shared__ long long off_in[2 * W], off_out[2 * W];
-    const long long l0 = (long long)blockIdx.x * (2 * W);
-    if (threadIdx.x < 2 * W) {
-        long long l = l0 + threadIdx.x;
-        if (l < p.nlines) {
-            off_in[threadIdx.x] = line_offset(p.lin, l);
-            off_out[threadIdx.x] = line_offset(p.lout, l);
-        }
-    }
-    load_twiddles(s_tw, p.tw, p.L);
-    __syncthreads();
-    float* Af = reinterpret_cast<float*>(A);
-    for (int e = threadIdx.x; e < 2 * W * p.L; e += blockDim.x) {
-        const int q = e / p.L, j = e - (e / p.L) * p.L;
-        const int jj = j - p.in_off;
-        float* dst = Af + ((q >> 1) * LS + phy(j)) * 2 + (q & 1);
-        if (l0 + q < p.nlines && jj >= 0 && jj < p.in_len) cp_async(dst, p.in + off_in[q] + jj, 4);
-        else *dst = 0.f;
-    }
-    cp_async_commit();
-    cp_async_wait0();
-    __syncthreads();
-    const int warp = threadIdx.x >> 5;
-    float2* Z = warp_fft<-1>(A, B, p.L, LS, warp * NL, NL, p.fac, s_tw, SmemLoad{A, LS});
-    __syncthreads();
-    const int H = p.L / 2 + 1;
-    for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
-        const int i = e / H, k = e - (e / H) * H;
-        const float2 z = Z[i * LS + phy(k)];
-        const float2 zm = Z[i * LS + phy((p.L - k) % p.L)];
-        // a = FFT of line 2i, b = FFT of line 2i+1 (two real lines in one complex FFT)
-        const float2 a = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-        const float2 b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-        if (l0 + 2 * i < p.nlines) p.out[off_out[2 * i] + k] = a;
-        if (l0 + 2 * i + 1 < p.nlines) p.out[off_out[2 * i + 1] + k] = b;
-    }
-}
-
-// Z = A + i B for complex line li from the staged half spectra of real lines
-// 2 li (A) and 2 li + 1 (B), with the Hermitian extension on (L/2, L).
-struct HermLoad {
-    const float2* R;   // raw half spectra, real line q at q * HS
-    int HS, L;
-    __device__ __forceinline__ float2 operator()(int li, int j) const {
-        const bool lo = 2 * j <= L;
-        const int k = lo ? j : L - j;
-        const float2 a = R[(2 * li) * HS + k];
-        const float2 b = R[(2 * li + 1) * HS + k];
-        return lo ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
-    }
-};
-
-constexpr int kC2RMaxSlots = 16;  // max outputs per lane in the certificate epilogue
-
-template <int W>
-__device__ __forceinline__ void stage_half(const C2RPass& p, int s, const long long* off_in,
-                                           long long l0, float2* R, int HS) {
-    const int H = p.L / 2 + 1;
-    const float2* in = p.in + (long long)s * p.in_spec_stride;
-    for (int e = threadIdx.x; e < 2 * W * H; e += blockDim.x) {
-        const int q = e / H, k = e - (e / H) * H;
-        if (l0 + q < p.nlines) cp_async(R + q * HS + k, in + off_in[q] + k, 8);
-        else R[q * HS + k] = make_float2(0.f, 0.f);
-    }
-}
-
-template <int W, int MODE, int SLOTS>
-__global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
-    constexpr int NL = W / 8;
-    const int LS = pitch(p.L);
-    const int H = p.L / 2 + 1;
-    const int HS = H + 1;
-    extern __shared__ float4 smem_raw[];
-    float2* s_tw = reinterpret_cast<float2*>(smem_raw);
-    float2* A = s_tw + p.L;
-    float2* B = A + W * LS;
-    float2* R0 = B + W * LS;
-    float2* R1 = R0 + 2 * W * HS;
-    __shared__ long long off_in[2 * W], off_out[2 * W];
-    __shared__ double s_red[kThreads / 32];
-    const long long l0 = (long long)blockIdx.x * (2 * W);
-    if (threadIdx.x < 2 * W) {
-        long long l = l0 + threadIdx.x;
-        if (l < p.nlines) {
-            off_in[threadIdx.x] = line_offset(p.lin, l);
-            off_out[threadIdx.x] = line_offset(p.lout, l);
-        }
-    }
-    load_twiddles(s_tw, p.tw, p.L);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q0 = 2 * NL * warp;                // first real output line of this warp
-    const int nout = 2 * NL * p.out_len;         // outputs of this warp
-
-    float mx[SLOTS];
-    int ak[SLOTS];
-    bool saw_nan = false;
-    double acc = 0.0;
-#pragma unroll
-    for (int it = 0; it < SLOTS; ++it) {
-        mx[it] = -INFINITY;
-        ak[it] = 0;
-    }
-    // certificate: grid.y splits the kernels into groups of p.nspec
-    const int k0 = (MODE == C2R_CERTMAX) ? (int)blockIdx.y * p.nspec : 0;
-    const int nspec = (MODE == C2R_CERTMAX) ? min(p.nspec, p.ktotal - k0) : 1;
-    stage_half<W>(p, k0, off_in, l0, R0, HS);
-    cp_async_commit();
-    for (int s = 0; s < nspec; ++s) {
-        if (s + 1 < nspec) stage_half<W>(p, k0 + s + 1, off_in, l0, (s & 1) ? R0 : R1, HS);
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const float2* Rs = (s & 1) ? R1 : R0;
-        float2* z = warp_fft<1>(B, A, p.L, LS, warp * NL, NL, p.fac, s_tw, HermLoad{Rs, HS, p.L});
-        if constexpr (MODE != C2R_CERTMAX) {
-            for (int e = lane; e < nout; e += 32) {
-                const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
-                const int q = q0 + qq;
-                if (l0 + q >= p.nlines) continue;
-                const float2 zz = z[(q >> 1) * LS + phy(j + p.out_off)];
-                const float v = ((q & 1) ? zz.y : zz.x) * p.scale;
-                const long long o = off_out[q] + j;
-                if constexpr (MODE == C2R_STORE) {
-                    p.out[o] = v;
-                } else {
-                    const float r = p.y[o] - v;
-                    if (p.out) p.out[o] = r;
-                    acc += (double)r * (double)r;
-                }
-            }
-        } else {
-            const int kk = k0 + s;
-#pragma unroll
-            for (int it = 0; it < SLOTS; ++it) {
-                const int e = lane + 32 * it;
-                if (e < nout) {
-                    const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
-                    const int q = q0 + qq;
-                    if (l0 + q < p.nlines) {
-                        const float2 zz = z[(q >> 1) * LS + phy(j + p.out_off)];
-                        const float v = ((q & 1) ? zz.y : zz.x) * p.scale;
-                        if (p.eta_out) p.eta_out[(long long)kk * p.V + off_out[q] + j] = v;
-                        if (v != v) saw_nan = true;
-                        if (v > mx[it]) {
-                            mx[it] = v;
-                            ak[it] = kk;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();   // the staged buffer of spectrum s is refilled at s + 2
-    }
-    if constexpr (MODE == C2R_RESIDUAL) {
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-        if (lane == 0) s_red[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
-            p.partials[blockIdx.x] = t;
-        }
-    }
-    if constexpr (MODE == C2R_CERTMAX) {
-        unsigned long long best = 0ull;
-#pragma unroll
-        for (int it = 0; it < SLOTS; ++it) {
-            const int e = lane + 32 * it;
-            if (e < nout) {
-                const int qq = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
-                const int q = q0 + qq;
-                if (l0 + q < p.nlines) {
-                    const long long o = off_out[q] + j;
-                    const unsigned long long key =
-                        candidate_key(mx[it], (unsigned long long)ak[it] * p.V + o);
-                    if (p.vox_key) atomicMax(p.vox_key + o, key);
-                    if (key > best) best = key;
-                }
-            }
-        }
-        if (saw_nan) best = ~0ull;
-        if (p.best_key) {
-            for (int off = 16; off > 0; off >>= 1) {
-                unsigned long long o2 = __shfl_down_sync(0xffffffffu, best, off);
-                if (o2 > best) best = o2;
-            }
-            if (lane == 0 && best) atomicMax(p.best_key, best);
-        }
-    }
+int c2r_blocks(const C2RPass& p) {
+    const int W = c2r_width(p);
+    return (int)((p.nlines + 2 * W - 1) / (2 * W));
 }
 
 // Per-voxel keys -> max over k and its k.
@@ -737,137 +148,6 @@ __global__ void k_vox_decode(const unsigned long long* key, long long V, float* 
         if (max_out) max_out[i] = v;
         if (argk_out) argk_out[i] = a;
     }
-}
-
-// ------------------------------------------------------------------ launchers
-
-// Lines per CTA: 16 up to length 256, else 8 (shared memory).
-static int tile_width(int L) { return L <= 256 ? 16 : 8; }
-
-// Raise a kernel's dynamic shared-memory limit once per (device, kernel, size):
-// the attribute call is kept out of stream captures after the first use.
-template <typename KernelT>
-static sfw_status prepare(KernelT kernel, size_t smem) {
-    if (smem <= 48 * 1024) return SFW_OK;
-    static std::mutex mu;
-    static std::map<std::pair<int, const void*>, size_t> done;
-    int dev = 0;
-    SFW_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
-    auto it = done.find(key);
-    if (it != done.end() && it->second >= smem) return SFW_OK;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-    done[key] = smem;
-    return SFW_OK;
-}
-
-static size_t tile_bytes(int L, int W, int nbuf) {
-    return sizeof(float2) * ((size_t)L + (size_t)nbuf * W * pitch(L));
-}
-
-static int spec_bytes(int kind) {
-    return kind == SPEC_C64 ? 8 : kind == SPEC_RBF16 ? 2 : 4;
-}
-
-sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
-    if (p.nlines <= 0) return SFW_OK;
-    const int W = tile_width(p.L);
-    const size_t smem = tile_bytes(p.L, W, 2);
-    const unsigned blocks = (unsigned)((p.nlines + W - 1) / W);
-#define SFW_C2C(WW, DD)                                              \
-    do {                                                             \
-        SFW_TRY(prepare(k_c2c<WW, DD>, smem));                       \
-        SFW_LAUNCH(st, "k_c2c", k_c2c<WW, DD><<<blocks, kThreads, smem, st>>>(p)); \
-    } while (0)
-    if (W == 16) {
-        if (p.dir < 0) SFW_C2C(16, -1); else SFW_C2C(16, 1);
-    } else {
-        if (p.dir < 0) SFW_C2C(8, -1); else SFW_C2C(8, 1);
-    }
-#undef SFW_C2C
-    return launch_check("k_c2c");
-}
-
-sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
-    if (p.nlines <= 0) return SFW_OK;
-    const int W = tile_width(p.L);
-    const int es = spec_bytes(p.spec_kind);
-    const size_t sp = ((size_t)p.L * (W + 16 / es) * es + 15) & ~(size_t)15;
-    const size_t smem = tile_bytes(p.L, W, 3) + 2 * sp;
-    const unsigned blocks = (unsigned)((p.nlines + W - 1) / W);
-    const dim3 grid(blocks, (unsigned)((p.ktotal + p.nspec - 1) / p.nspec));
-#define SFW_MUL(WW, KK)                                              \
-    do {                                                             \
-        SFW_TRY(prepare(k_mul<WW, KK>, smem));                       \
-        SFW_LAUNCH(st, "k_mul", k_mul<WW, KK><<<grid, kThreads, smem, st>>>(p)); \
-    } while (0)
-    switch (p.spec_kind) {
-        case SPEC_C64: if (W == 16) SFW_MUL(16, SPEC_C64); else SFW_MUL(8, SPEC_C64); break;
-        case SPEC_R32: if (W == 16) SFW_MUL(16, SPEC_R32); else SFW_MUL(8, SPEC_R32); break;
-        case SPEC_CBF16: if (W == 16) SFW_MUL(16, SPEC_CBF16); else SFW_MUL(8, SPEC_CBF16); break;
-        default: if (W == 16) SFW_MUL(16, SPEC_RBF16); else SFW_MUL(8, SPEC_RBF16); break;
-    }
-#undef SFW_MUL
-    return launch_check("k_mul");
-}
-
-sfw_status launch_r2c(const R2CPass& p, cudaStream_t st) {
-    if (p.nlines <= 0) return SFW_OK;
-    const int W = tile_width(p.L);
-    const size_t smem = tile_bytes(p.L, W, 2);
-    const unsigned blocks = (unsigned)((p.nlines + 2 * W - 1) / (2 * W));
-    if (W == 16) {
-        SFW_TRY(prepare(k_r2c<16>, smem));
-        SFW_LAUNCH(st, "k_r2c", k_r2c<16><<<blocks, kThreads, smem, st>>>(p));
-    } else {
-        SFW_TRY(prepare(k_r2c<8>, smem));
-        SFW_LAUNCH(st, "k_r2c", k_r2c<8><<<blocks, kThreads, smem, st>>>(p));
-    }
-    return launch_check("k_r2c");
-}
-
-// The certificate epilogue keeps 2 (W / 8) * out_len running maxima per warp in
-// registers: SLOTS per lane (4, 8 or 16).  Its tiles are 8 lines wide (more CTAs,
-// fewer registers); the other modes use tile_width.
-static int c2r_width(const C2RPass& p) {
-    return p.mode == C2R_CERTMAX ? 8 : tile_width(p.L);
-}
-
-int c2r_blocks(const C2RPass& p) {
-    const int W = c2r_width(p);
-    return (int)((p.nlines + 2 * W - 1) / (2 * W));
-}
-
-sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
-    const int W = c2r_width(p);
-    const int blocks = c2r_blocks(p);
-    if (blocks_out) *blocks_out = blocks;
-    if (p.nlines <= 0) return SFW_OK;
-    const int need = (2 * (W / 8) * p.out_len + 31) / 32;
-    if (p.mode == C2R_CERTMAX && need > kC2RMaxSlots)
-        return fail(SFW_ERR_SHAPE, "c2r: %d outputs per line exceed the epilogue tile", p.out_len);
-    const int H = p.L / 2 + 1;
-    const size_t smem = tile_bytes(p.L, W, 2) + sizeof(float2) * 2 * 2 * (size_t)W * (H + 1);
-    const int groups = p.mode == C2R_CERTMAX ? (p.ktotal + p.nspec - 1) / p.nspec : 1;
-    const dim3 grid((unsigned)blocks, (unsigned)groups);
-#define SFW_C2R(WW, MM, SS)                                          \
-    do {                                                             \
-        SFW_TRY(prepare(k_c2r<WW, MM, SS>, smem));                   \
-        SFW_LAUNCH(st, "k_c2r", k_c2r<WW, MM, SS><<<grid, kThreads, smem, st>>>(p)); \
-    } while (0)
-    switch (p.mode) {
-        case C2R_STORE: if (W == 16) SFW_C2R(16, C2R_STORE, 1); else SFW_C2R(8, C2R_STORE, 1); break;
-        case C2R_RESIDUAL: if (W == 16) SFW_C2R(16, C2R_RESIDUAL, 1); else SFW_C2R(8, C2R_RESIDUAL, 1); break;
-        default:
-            if (need <= 4) SFW_C2R(8, C2R_CERTMAX, 4);
-            else if (need <= 8) SFW_C2R(8, C2R_CERTMAX, 8);
-            else SFW_C2R(8, C2R_CERTMAX, 16);
-            break;
-    }
-#undef SFW_C2R
-    return launch_check("k_c2r");
 }
 
 sfw_status launch_vox_decode(const unsigned long long* key, long long V, float* max_out,

@@ -497,6 +497,13 @@ struct sfw_plan {
     float2* cC;
     unsigned long long* best_key;
     unsigned long long* vox_key;  // V per-voxel certificate keys
+    float* grid_sd;               // 2K floats on the device: sigma_k, d_k
+    float* vmax;                  // V: per-voxel max over k (top-k path)
+    int* vargk;                   // V: its k
+    float* cand_val;              // 64 grid values of the top-k voxels
+    int64_t* cand_idx;            // their voxel indices
+    float* cand_theta;            // 64 x 5 parameter rows
+    double* cand_eta;             // 64 FP32-summed certificates
     int num_sms;
     unsigned long long* red_scratch;
     long long red_scratch_len;
@@ -815,6 +822,25 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;
         if ((s = plan_alloc_t(p, &p->best_key, 2))) break;
         if ((s = plan_alloc_t(p, &p->vox_key, (size_t)p->V))) break;
+        if (K > 0) {
+            if ((s = plan_alloc_t(p, &p->grid_sd, 2 * (size_t)K))) break;
+            std::vector<float> sd(2 * (size_t)K);
+            for (int k = 0; k < K; ++k) {
+                sd[2 * k] = p->sigmas[k];
+                sd[2 * k + 1] = p->ds[k];
+            }
+            e = cudaMemcpy(p->grid_sd, sd.data(), sizeof(float) * sd.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                s = cuda_fail(e, "grid upload");
+                break;
+            }
+            if ((s = plan_alloc_t(p, &p->vmax, (size_t)p->V))) break;
+            if ((s = plan_alloc_t(p, &p->vargk, (size_t)p->V))) break;
+            if ((s = plan_alloc_t(p, &p->cand_val, 64))) break;
+            if ((s = plan_alloc_t(p, &p->cand_idx, 64))) break;
+            if ((s = plan_alloc_t(p, &p->cand_theta, 64 * 5))) break;
+            if ((s = plan_alloc_t(p, &p->cand_eta, 64))) break;
+        }
         {
             int dev = 0;
             cudaGetDevice(&dev);
@@ -892,7 +918,7 @@ sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* ato
                                double* loss_out, double* grad_out, float* residual_out,
                                void* stream) {
     clear_error();
-    if (!p || !y || !loss_out || !grad_out) return fail(SFW_ERR_ARG, "plan, y, loss_out, grad_out must be non-NULL");
+    if (!p || !y || !loss_out) return fail(SFW_ERR_ARG, "plan, y, loss_out must be non-NULL");
     SFW_TRY(check_atoms(atoms, true));
     if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and >= 0");
     if (atoms->N > p->grad_parts_atoms) return fail(SFW_ERR_ARG, "too many atoms");
@@ -911,6 +937,7 @@ sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* ato
     SFW_TRY(blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, &blocks));
     if (blocks > p->loss_parts_len) return fail(SFW_ERR_SHAPE, "loss partial buffer too small");
     SFW_TRY(launch_loss_finalize(p->loss_parts, blocks, a, lambda, loss_out, st));
+    if (!grad_out) return SFW_OK;  // loss only
     SFW_TRY(blur_transpose(p->blur, r, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
     return launch_atom_grad(a, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, grad_out, st);
 }
@@ -1063,6 +1090,38 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
     if (best_val || best_idx) SFW_TRY(launch_key_decode(p->best_key, best_val, best_idx, st));
     return SFW_OK;
+}
+
+sfw_status sfw_certificate_topk(sfw_plan* p, const float* residual, double lambda, int topk,
+                                float* cand_theta, float* cand_grid, double* cand_eta,
+                                float* best_theta, double* best_eta, void* stream) {
+    clear_error();
+    if (!p || !residual) return fail(SFW_ERR_ARG, "plan and residual must be non-NULL");
+    if (p->K == 0) return fail(SFW_ERR_ARG, "plan has no certificate grid");
+    if (topk < 1 || topk > 64 || topk > p->V) return fail(SFW_ERR_ARG, "topk must be in [1, min(64, V)]");
+    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // 1. grid certificate -> per-voxel max over k and its k
+    SFW_TRY(sfw_certificate_grid(p, residual, lambda, nullptr, p->vmax, p->vargk, nullptr, nullptr, stream));
+    // 2. the topk voxels by their grid maximum
+    SFW_TRY(launch_topk(p->vmax, p->V, topk, p->red_scratch, p->red_scratch_len, p->cand_val,
+                        p->cand_idx, st));
+    // 3. parameter rows (voxel position, sigma_k, d_k) and their FP32 re-score
+    SFW_TRY(launch_candidate_theta(p->cand_idx, p->vargk, p->grid_sd, topk, p->n, p->cand_theta, st));
+    SFW_TRY(blur_transpose(p->blur, residual, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
+    AtomsDev pts;
+    pts.N = topk;
+    pts.m = p->cand_theta;
+    pts.sigma = p->cand_theta + 3;
+    pts.d = p->cand_theta + 4;
+    pts.w = p->cand_theta + 3;
+    pts.ms = 5;
+    pts.ps = 5;
+    SFW_TRY(launch_eta_points(pts, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, p->cand_eta,
+                              nullptr, st));
+    // 4. the best re-scored candidate and the requested copies
+    return launch_candidate_select(p->cand_theta, p->cand_val, p->cand_eta, topk, cand_theta,
+                                   cand_grid, cand_eta, best_theta, best_eta, st);
 }
 
 sfw_status sfw_eta_points(sfw_plan* p, const float* residual, double lambda, int P,

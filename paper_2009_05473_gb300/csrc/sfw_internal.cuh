@@ -206,6 +206,13 @@ sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], f
 sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3], float eps,
                              const float* b, double lambda, double* partials, double* eta,
                              double* grad, cudaStream_t st);
+// Top-k voxels -> parameter rows (m0, m1, m2, sigma_k, d_k), k = argk of the voxel.
+sfw_status launch_candidate_theta(const int64_t* vox, const int* argk, const float* grid_sd,
+                                  int topk, const int n[3], float* theta, cudaStream_t st);
+// Best of the FP32-summed candidates (ties -> first) and optional copies out.
+sfw_status launch_candidate_select(const float* theta, const float* grid_val, const double* eta,
+                                   int topk, float* theta_out, float* grid_out, double* eta_out,
+                                   float* best_theta, double* best_eta, cudaStream_t st);
 // sum_n w_n added to the loss: loss = 0.5 * sum(partials) + lambda * sum w
 sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
                                 double lambda, double* loss, cudaStream_t st);
