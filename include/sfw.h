@@ -236,6 +236,19 @@ sfw_status sfw_profile_start(int max_launches, const char* only_tag);
 sfw_status sfw_profile_collect(void);
 sfw_status sfw_profile_stop(char* json, size_t len);
 
+/* Gram system of the non-negative LASSO of step 3 (Algorithm 1; step 3 of
+ * Algorithm 2): with a_i = Phi G(theta_i, 1) the blurred unit atoms,
+ *   G[i][j] = <a_i, a_j>,  c[i] = <a_i, y>   (sums in FP64 over the grid),
+ * so that C(y, mu_{w,theta}, lambda) = 1/2 w^T G w - (c - lambda)^T w + |y|^2/2.
+ *   atoms   device atom set, 1 <= N <= 256 (weights ignored)
+ *   y       device n0*n1*n2 floats
+ *   G_out   device N x N doubles (row-major), c_out device N doubles
+ * The first call with N atoms allocates N*V floats in the plan (kept for
+ * later calls; synchronises the stream when it grows).  Asynchronous
+ * otherwise. */
+sfw_status sfw_gram(sfw_plan* plan, const sfw_atoms* atoms, const float* y, double* G_out,
+                    double* c_out, void* stream);
+
 /* Thread-local text of the last error of this thread ("" if none). */
 const char* sfw_last_error(void);
 

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _abi
 from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_topk,  # noqa: F401
-                   sfw_eta_points, sfw_forward,
+                   sfw_eta_points, sfw_forward, sfw_gram,
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
                    sfw_slide_loss_grad, sfw_version)
 
@@ -177,6 +177,14 @@ class Plan:
         sfw_certificate_topk(self.handle, _ptr(residual), lam, topk, _ptr(th), _ptr(gv), _ptr(ev),
                              _ptr(bt), _ptr(be), _stream_ptr(stream))
         return {"theta": th, "grid": gv, "eta": ev, "best_theta": bt, "best_eta": be}
+
+    def gram(self, atoms: AtomSet, y, stream=None):
+        """(G, c): G[i][j] = <Phi G(theta_i,1), Phi G(theta_j,1)>, c[i] = <Phi G(theta_i,1), y>."""
+        torch = _torch()
+        G = torch.empty((atoms.N, atoms.N), dtype=torch.float64, device="cuda")
+        c = torch.empty(atoms.N, dtype=torch.float64, device="cuda")
+        sfw_gram(self.handle, atoms.abi(), _ptr(y), _ptr(G), _ptr(c), _stream_ptr(stream))
+        return G, c
 
     def eta_points(self, residual, lam: float, theta, with_grad: bool = True, stream=None):
         """eta (and d eta / d theta) at rows theta = (m0, m1, m2, sigma, d), FP32 sums."""

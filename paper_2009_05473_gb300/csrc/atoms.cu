@@ -303,6 +303,62 @@ sfw_status launch_candidate_select(const float* theta, const float* grid_val, co
     return launch_check("k_candidate_select");
 }
 
+// ------------------------------------------------------------------ Gram matrix (LASSO of step 3)
+
+// Copy atom i of a set into a one-atom slot with unit weight: (m0, m1, m2, sigma, d, 1).
+__global__ void k_unit_atom(AtomsDev a, int i, float* slot) {
+    if (threadIdx.x == 0) {
+        slot[0] = a.m[a.ms * i + 0];
+        slot[1] = a.m[a.ms * i + 1];
+        slot[2] = a.m[a.ms * i + 2];
+        slot[3] = a.sigma[a.ps * i];
+        slot[4] = a.d[a.ps * i];
+        slot[5] = 1.0f;
+    }
+}
+
+sfw_status launch_unit_atom(const AtomsDev& a, int i, float* slot, cudaStream_t st) {
+    SFW_LAUNCH(st, "k_unit_atom", k_unit_atom<<<1, 32, 0, st>>>(a, i, slot));
+    return launch_check("k_unit_atom");
+}
+
+// One block per pair (i, j >= i) and per row (i, N) for <a_i, y>: FP64 sums over V.
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, const float* __restrict__ y,
+                                              int N, long long V, double* G, double* c) {
+    __shared__ double s_red[8];
+    // block b -> pair index in the upper triangle (with the y column as j = N)
+    int b = blockIdx.x, i = 0;
+    while (b >= N + 1 - i) {
+        b -= N + 1 - i;
+        ++i;
+    }
+    const int j = i + b;
+    const float* ai = A + (long long)i * V;
+    const float* aj = j < N ? A + (long long)j * V : y;
+    double acc = 0.0;
+    for (long long v = threadIdx.x; v < V; v += 256) acc += (double)ai[v] * (double)aj[v];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += s_red[q];
+        if (j < N) {
+            G[(long long)i * N + j] = t;
+            G[(long long)j * N + i] = t;
+        } else {
+            c[i] = t;
+        }
+    }
+}
+
+sfw_status launch_gram(const float* A, const float* y, int N, long long V, double* G, double* c,
+                       cudaStream_t st) {
+    const int pairs = N * (N + 1) / 2 + N;
+    SFW_LAUNCH(st, "k_gram", k_gram<<<pairs, 256, 0, st>>>(A, y, N, V, G, c));
+    return launch_check("k_gram");
+}
+
 // ------------------------------------------------------------------ loss
 
 __global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, double lambda,

@@ -504,6 +504,9 @@ struct sfw_plan {
     int64_t* cand_idx;            // their voxel indices
     float* cand_theta;            // 64 x 5 parameter rows
     double* cand_eta;             // 64 FP32-summed certificates
+    float* gram_cols;             // N x V blurred unit atoms (grown on demand, sfw_gram)
+    int gram_cap;                 // atoms gram_cols can hold
+    float* unit_slot;             // one atom (m0, m1, m2, sigma, d, w = 1)
     int num_sms;
     unsigned long long* red_scratch;
     long long red_scratch_len;
@@ -534,6 +537,8 @@ static sfw_status plan_alloc_t(sfw_plan* p, T** ptr, size_t count) {
 
 static void plan_free(sfw_plan* p) {
     if (!p) return;
+    if (p->gram_cols) cudaFree(p->gram_cols);
+    p->gram_cols = nullptr;
     for (void* q : p->allocations) cudaFree(q);
     p->allocations.clear();
     p->tw.release();
@@ -822,6 +827,7 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;
         if ((s = plan_alloc_t(p, &p->best_key, 2))) break;
         if ((s = plan_alloc_t(p, &p->vox_key, (size_t)p->V))) break;
+        if ((s = plan_alloc_t(p, &p->unit_slot, 8))) break;
         if (K > 0) {
             if ((s = plan_alloc_t(p, &p->grid_sd, 2 * (size_t)K))) break;
             std::vector<float> sd(2 * (size_t)K);
@@ -1090,6 +1096,48 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
     if (best_val || best_idx) SFW_TRY(launch_key_decode(p->best_key, best_val, best_idx, st));
     return SFW_OK;
+}
+
+sfw_status sfw_gram(sfw_plan* p, const sfw_atoms* atoms, const float* y, double* G_out,
+                    double* c_out, void* stream) {
+    clear_error();
+    if (!p || !y || !G_out || !c_out) return fail(SFW_ERR_ARG, "plan, y, G_out, c_out must be non-NULL");
+    SFW_TRY(check_atoms(atoms, true));
+    if (atoms->N > 256) return fail(SFW_ERR_ARG, "sfw_gram takes at most 256 atoms");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int N = atoms->N;
+    if (p->gram_cap < N) {
+        // the only allocation of the hot path's API: the N blurred atoms, kept for reuse
+        SFW_CUDA(cudaStreamSynchronize(st));
+        if (p->gram_cols) cudaFree(p->gram_cols);
+        p->gram_cols = nullptr;
+        p->gram_cap = 0;
+        const int cap = N < 16 ? 16 : N;
+        cudaError_t e = cudaMalloc(&p->gram_cols, sizeof(float) * (size_t)cap * (size_t)p->V);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SFW_ERR_ALLOC, "sfw_gram: %d blurred atoms do not fit", cap);
+        }
+        p->gram_cap = cap;
+    }
+    AtomsDev a = to_dev(atoms);
+    AtomsDev unit;
+    unit.N = 1;
+    unit.m = p->unit_slot;
+    unit.sigma = p->unit_slot + 3;
+    unit.d = p->unit_slot + 4;
+    unit.w = p->unit_slot + 5;
+    for (int i = 0; i < N; ++i) {
+        SFW_TRY(launch_unit_atom(a, i, p->unit_slot, st));
+        SFW_TRY(launch_render(unit, p->E, p->R, p->eps, p->fE, st));
+        C2RPass ep;
+        memset(&ep, 0, sizeof(ep));
+        ep.mode = C2R_STORE;
+        ep.scale = 1.f;
+        ep.out = p->gram_cols + (size_t)i * (size_t)p->V;
+        SFW_TRY(blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, nullptr));
+    }
+    return launch_gram(p->gram_cols, y, N, p->V, G_out, c_out, st);
 }
 
 sfw_status sfw_certificate_topk(sfw_plan* p, const float* residual, double lambda, int topk,

@@ -213,6 +213,10 @@ sfw_status launch_candidate_theta(const int64_t* vox, const int* argk, const flo
 sfw_status launch_candidate_select(const float* theta, const float* grid_val, const double* eta,
                                    int topk, float* theta_out, float* grid_out, double* eta_out,
                                    float* best_theta, double* best_eta, cudaStream_t st);
+// Atom i with unit weight into a 6-float slot; Gram matrix and projections.
+sfw_status launch_unit_atom(const AtomsDev& a, int i, float* slot, cudaStream_t st);
+sfw_status launch_gram(const float* A, const float* y, int N, long long V, double* G, double* c,
+                       cudaStream_t st);
 // sum_n w_n added to the loss: loss = 0.5 * sum(partials) + lambda * sum w
 sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
                                 double lambda, double* loss, cudaStream_t st);
