@@ -249,6 +249,47 @@ sfw_status sfw_profile_stop(char* json, size_t len);
 sfw_status sfw_gram(sfw_plan* plan, const sfw_atoms* atoms, const float* y, double* G_out,
                     double* c_out, void* stream);
 
+/* ---- Batches: many independent volumes (uneven shapes, PSFs, atom counts)
+ * through one step of grouped launches.
+ * At creation the batch records the launches of one SFW iteration's hot path
+ * for every volume -- sfw_slide_loss_grad (loss, gradient, residual), then
+ * sfw_certificate_grid of that residual (grid argmax only) -- and merges the
+ * launches of each stage that use the same kernel variant into one
+ * persistent launch whose CTAs stride over a device work list of (volume,
+ * tile) items.  sfw_batch_step issues those launches only (no host
+ * synchronisation, no allocation): capture it into a CUDA graph to run the
+ * whole batch as one graph launch.  The first step computes the launch grids
+ * (occupancy queries): run it once before any capture.
+ *   plans     host array of count distinct plans with a certificate grid; they
+ *             must outlive the batch and not be used concurrently with a step
+ *   vols      host array of count volume descriptions: device buffers owned by
+ *             the caller, fixed for the batch's lifetime (the step reads y and
+ *             the atoms and writes the outputs in place)
+ *   lambdas   host array of count regularisation weights (> 0) */
+typedef struct sfw_batch sfw_batch;
+
+typedef struct {
+    int N;               /* atoms of the volume, 1..4096 */
+    const float* y;      /* device n0*n1*n2 (plan's grid): observation */
+    const float* m;      /* device N x 3 atom positions; sigma, d, w: device N */
+    const float* sigma;
+    const float* d;
+    const float* w;
+    float* residual;     /* device n0*n1*n2: y - Phi mu (output) */
+    double* grad;        /* device 6N: gradient of C (output, sfw_slide_loss_grad layout) */
+    double* loss;        /* device 1: C (output) */
+    float* best_val;     /* device 1: grid maximum of eta (output) */
+    int64_t* best_idx;   /* device 1: its flat index k*V + lin(m) (output) */
+} sfw_batch_volume;
+
+sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_volume* vols,
+                            const double* lambdas, sfw_batch** out);
+sfw_status sfw_batch_destroy(sfw_batch* batch);
+/* Number of grouped launches one sfw_batch_step issues. */
+sfw_status sfw_batch_query(const sfw_batch* batch, int* launches_per_step);
+/* One hot-path step for every volume of the batch, asynchronous on stream. */
+sfw_status sfw_batch_step(sfw_batch* batch, void* stream);
+
 /* Thread-local text of the last error of this thread ("" if none). */
 const char* sfw_last_error(void);
 

@@ -20,7 +20,7 @@ from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_t
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
                    sfw_slide_loss_grad, sfw_version)
 
-__all__ = ["Plan", "AtomSet", "argmax", "launch_count", "SfwError", "build_library"]
+__all__ = ["Plan", "AtomSet", "Batch", "argmax", "launch_count", "SfwError", "build_library"]
 
 
 def build_library(force: bool = False) -> str:
@@ -214,6 +214,52 @@ class Plan:
         sfw_slide_loss_grad(self.handle, _ptr(y), atoms.abi(), lam, _ptr(loss), _ptr(grad),
                             _ptr(r) if want_residual else 0, _stream_ptr(stream))
         return loss, grad, (r if want_residual else None)
+
+
+class Batch:
+    """Independent volumes (each with its own Plan) stepped together: one SFW iteration's hot
+    path per volume (loss, gradient, residual, grid argmax) through grouped persistent launches
+    (libsfw ``sfw_batch``).  The input tensors (y and the atoms) are read in place at every
+    step: update them with in-place copies.  Outputs: loss (count), best_val, best_idx (count),
+    residual[v], grad[v]."""
+
+    def __init__(self, plans: Sequence[Plan], ys, atoms: Sequence[AtomSet], lambdas: Sequence[float]):
+        torch = _torch()
+        self.plans = list(plans)
+        self.ys = list(ys)
+        self.atoms = list(atoms)
+        count = len(self.plans)
+        self.loss = torch.empty(count, dtype=torch.float64, device="cuda")
+        self.best_val = torch.empty(count, dtype=torch.float32, device="cuda")
+        self.best_idx = torch.empty(count, dtype=torch.int64, device="cuda")
+        self.residual = [torch.empty(p.n, dtype=torch.float32, device="cuda") for p in self.plans]
+        self.grad = [torch.empty(6 * a.N, dtype=torch.float64, device="cuda") for a in self.atoms]
+        vols = []
+        for v in range(count):
+            a = self.atoms[v]
+            a.abi()  # validates the atom tensors
+            if not (self.ys[v].is_cuda and self.ys[v].dtype == torch.float32 and self.ys[v].is_contiguous()):
+                raise ValueError("y must be a contiguous float32 CUDA tensor")
+            vols.append(_abi.BatchVolume(a.N, _ptr(self.ys[v]), _ptr(a.m), _ptr(a.sigma), _ptr(a.d),
+                                         _ptr(a.w), _ptr(self.residual[v]), _ptr(self.grad[v]),
+                                         _ptr(self.loss[v:v + 1]), _ptr(self.best_val[v:v + 1]),
+                                         _ptr(self.best_idx[v:v + 1])))
+        self.handle = _abi.sfw_batch_create([p.handle for p in self.plans], vols, lambdas)
+        self.launches_per_step = _abi.sfw_batch_query(self.handle)
+
+    def step(self, stream=None):
+        _abi.sfw_batch_step(self.handle, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _abi.sfw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def argmax(values, topk: int = 1, stream=None) -> Tuple["torch.Tensor", "torch.Tensor"]:

@@ -22,7 +22,8 @@ SFW_PREC_BF16 = 1
 # every symbol declared in include/sfw.h
 EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
            "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
-           "sfw_slide_loss_grad", "sfw_gram", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
+           "sfw_slide_loss_grad", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
+           "sfw_batch_query", "sfw_batch_step", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
            "sfw_launch_count",
            "sfw_version")
 
@@ -52,6 +53,13 @@ class Atoms(ctypes.Structure):
                 ("d", ctypes.c_void_p), ("w", ctypes.c_void_p)]
 
 
+class BatchVolume(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("y", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("d", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("residual", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("loss", ctypes.c_void_p),
+                ("best_val", ctypes.c_void_p), ("best_idx", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -76,11 +84,17 @@ def lib() -> ctypes.CDLL:
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
     L.sfw_profile_start.argtypes = [i32, ctypes.c_char_p]
     L.sfw_gram.argtypes = [vp, ctypes.POINTER(Atoms), vp, vp, vp, vp]
+    L.sfw_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(BatchVolume),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp)]
+    L.sfw_batch_destroy.argtypes = [vp]
+    L.sfw_batch_query.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.sfw_batch_step.argtypes = [vp, vp]
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
                  "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
-                 "sfw_slide_loss_grad", "sfw_gram", "sfw_profile_start", "sfw_profile_collect",
+                 "sfw_slide_loss_grad", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
+           "sfw_batch_query", "sfw_batch_step", "sfw_profile_start", "sfw_profile_collect",
                  "sfw_profile_stop"):
         getattr(L, name).restype = ctypes.c_int
     L.sfw_last_error.restype = ctypes.c_char_p
@@ -160,6 +174,30 @@ def sfw_slide_loss_grad(plan: int, y: int, atoms: Atoms, lam: float, loss_out: i
 
 def sfw_gram(plan: int, atoms: Atoms, y: int, G_out: int, c_out: int, stream: int) -> None:
     check(lib().sfw_gram(plan, ctypes.byref(atoms), y, G_out, c_out, stream), "sfw_gram")
+
+
+def sfw_batch_create(plans, vols, lambdas) -> int:
+    n = len(plans)
+    arr = (ctypes.c_void_p * n)(*plans)
+    va = (BatchVolume * n)(*vols)
+    la = (ctypes.c_double * n)(*[float(x) for x in lambdas])
+    h = ctypes.c_void_p()
+    check(lib().sfw_batch_create(n, arr, va, la, ctypes.byref(h)), "sfw_batch_create")
+    return h.value
+
+
+def sfw_batch_destroy(batch: int) -> None:
+    check(lib().sfw_batch_destroy(batch), "sfw_batch_destroy")
+
+
+def sfw_batch_query(batch: int) -> int:
+    n = ctypes.c_int()
+    check(lib().sfw_batch_query(batch, ctypes.byref(n)), "sfw_batch_query")
+    return n.value
+
+
+def sfw_batch_step(batch: int, stream: int) -> None:
+    check(lib().sfw_batch_step(batch, stream), "sfw_batch_step")
 
 
 def sfw_profile_start(max_launches: int, only_tag: str = None) -> None:

@@ -27,8 +27,9 @@ __device__ __forceinline__ float atom_cut2(float sigma, float d, float log_inv_e
 constexpr int kRX = 32, kRY = 4, kRZ = 2;  // tile: axis 2 x axis 1 x axis 0
 constexpr int kRenderThreads = kRX * kRY * kRZ;
 
-__global__ void __launch_bounds__(kRenderThreads)
-k_render(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2, float* f) {
+__device__ __forceinline__ void render_body(const AtomsDev& a, int E0, int E1, int E2, int R0, int R1,
+                                            int R2, float log_inv_eps2, float* f, int bx, int by,
+                                            int bz) {
     __shared__ float s_m0[kRenderThreads], s_m1[kRenderThreads], s_m2[kRenderThreads];
     __shared__ float s_is2[kRenderThreads], s_hd[kRenderThreads], s_w[kRenderThreads];
     __shared__ float s_c2[kRenderThreads];
@@ -38,14 +39,14 @@ k_render(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_i
     const int tx = threadIdx.x % kRX;
     const int ty = (threadIdx.x / kRX) % kRY;
     const int tz = threadIdx.x / (kRX * kRY);
-    const int t2 = (int)blockIdx.x * kRX + tx;
-    const int t1 = (int)blockIdx.y * kRY + ty;
-    const int t0 = (int)blockIdx.z * kRZ + tz;
+    const int t2 = bx * kRX + tx;
+    const int t1 = by * kRY + ty;
+    const int t0 = bz * kRZ + tz;
     // grid coordinates of this voxel and of the tile's bounding box
     const float x0 = (float)(t0 - R0), x1 = (float)(t1 - R1), x2 = (float)(t2 - R2);
-    const float b0lo = (float)((int)blockIdx.z * kRZ - R0), b0hi = b0lo + (kRZ - 1);
-    const float b1lo = (float)((int)blockIdx.y * kRY - R1), b1hi = b1lo + (kRY - 1);
-    const float b2lo = (float)((int)blockIdx.x * kRX - R2), b2hi = b2lo + (kRX - 1);
+    const float b0lo = (float)(bz * kRZ - R0), b0hi = b0lo + (kRZ - 1);
+    const float b1lo = (float)(by * kRY - R1), b1hi = b1lo + (kRY - 1);
+    const float b2lo = (float)(bx * kRX - R2), b2hi = b2lo + (kRX - 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     float acc = 0.f;
@@ -105,8 +106,54 @@ k_render(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_i
     if (t0 < E0 && t1 < E1 && t2 < E2) f[((long long)t0 * E1 + t1) * E2 + t2] = acc;
 }
 
+__global__ void __launch_bounds__(kRenderThreads)
+k_render(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2, float* f) {
+    render_body(a, E0, E1, E2, R0, R1, R2, log_inv_eps2, f, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+int render_tiles(const RenderOp& op, int* nbx) {
+    *nbx = (op.E[2] + kRX - 1) / kRX;
+    return *nbx * ((op.E[1] + kRY - 1) / kRY) * ((op.E[0] + kRZ - 1) / kRZ);
+}
+
+// Persistent render over the tiles of n volumes.
+__global__ void __launch_bounds__(kRenderThreads)
+k_render_g(const RenderOp* __restrict__ ops, const int* __restrict__ start, const int* __restrict__ nbx,
+           int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const RenderOp& o = ops[q];
+        const int local = t - start[q];
+        const int ny = (o.E[1] + kRY - 1) / kRY;
+        const int bx = local % nbx[q], r = local / nbx[q];
+        const float lie2 = log2f(2.0f * logf(1.0f / o.eps));
+        render_body(o.a, o.E[0], o.E[1], o.E[2], o.R[0], o.R[1], o.R[2], lie2, o.f, bx, r % ny, r / ny);
+        __syncthreads();
+    }
+}
+
+sfw_status launch_render_group(const RenderOp* ops, const int* start, const int* nbx, int n,
+                               int total, int grid, cudaStream_t st) {
+    if (total <= 0) return SFW_OK;
+    SFW_LAUNCH(st, "k_render", k_render_g<<<grid, kRenderThreads, 0, st>>>(ops, start, nbx, n));
+    return launch_check("k_render_g");
+}
+
 sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], float eps, float* f,
                          cudaStream_t st) {
+    if (g_recorder) {
+        RenderOp op;
+        op.a = a;
+        for (int q = 0; q < 3; ++q) {
+            op.E[q] = E[q];
+            op.R[q] = R[q];
+        }
+        op.eps = eps;
+        op.f = f;
+        return g_recorder->add(op);
+    }
     dim3 grid((E[2] + kRX - 1) / kRX, (E[1] + kRY - 1) / kRY, (E[0] + kRZ - 1) / kRZ);
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
     SFW_LAUNCH(st, "k_render", k_render<<<grid, kRenderThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, f));
@@ -129,12 +176,11 @@ __device__ __forceinline__ double block_sum(double v, double* s_red) {
 }
 
 // grid = (N, kGradChunks): chunk c of atom n strides over the atom's box.
-__global__ void __launch_bounds__(kGradThreads)
-k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2,
-            const float* __restrict__ b, double* partials) {
+__device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1, int E2, int R0,
+                                               int R1, int R2, float log_inv_eps2,
+                                               const float* __restrict__ b, double* partials, int n,
+                                               int c, int nchunks) {
     __shared__ double s_red[kGradThreads / 32];
-    const int n = blockIdx.x;
-    const int c = blockIdx.y;
     const float m0 = a.m[a.ms * n + 0], m1 = a.m[a.ms * n + 1], m2 = a.m[a.ms * n + 2];
     const float sg = a.sigma[a.ps * n], dd = a.d[a.ps * n];
     const float c2 = atom_cut2(sg, dd, log_inv_eps2);
@@ -150,7 +196,7 @@ k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float lo
 
     float sg_b = 0.f, sm0 = 0.f, sm1 = 0.f, sm2 = 0.f, ss = 0.f, sd = 0.f;
     for (long long v = (long long)c * kGradThreads + threadIdx.x; v < nb;
-         v += (long long)gridDim.y * kGradThreads) {
+         v += (long long)nchunks * kGradThreads) {
         const int i2 = (int)(v % n2);
         const long long r = v / n2;
         const int i1 = (int)(r % n1);
@@ -178,8 +224,43 @@ k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float lo
     double out[6] = {sm0, sm1, sm2, ss, sd, sg_b};
     for (int q = 0; q < 6; ++q) {
         const double t = block_sum(out[q], s_red);
-        if (threadIdx.x == 0) partials[((long long)n * gridDim.y + c) * 6 + q] = t;
+        if (threadIdx.x == 0) partials[((long long)n * nchunks + c) * 6 + q] = t;
     }
+}
+
+__global__ void __launch_bounds__(kGradThreads)
+k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2,
+            const float* __restrict__ b, double* partials) {
+    atom_grad_body(a, E0, E1, E2, R0, R1, R2, log_inv_eps2, b, partials, blockIdx.x, blockIdx.y,
+                   gridDim.y);
+}
+
+int grad_tiles(const GradOp& op, int* nbx) {
+    *nbx = kGradChunks;
+    return op.a.N * kGradChunks;
+}
+
+__global__ void __launch_bounds__(kGradThreads)
+k_atom_grad_g(const GradOp* __restrict__ ops, const int* __restrict__ start, const int* __restrict__ nbx,
+              int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const GradOp& o = ops[q];
+        const int local = t - start[q];
+        const float lie2 = log2f(2.0f * logf(1.0f / o.eps));
+        atom_grad_body(o.a, o.E[0], o.E[1], o.E[2], o.R[0], o.R[1], o.R[2], lie2, o.b, o.partials,
+                       local / kGradChunks, local % kGradChunks, kGradChunks);
+        __syncthreads();
+    }
+}
+
+sfw_status launch_grad_group(const GradOp* ops, const int* start, const int* nbx, int n, int total,
+                             int grid, cudaStream_t st) {
+    if (total <= 0) return SFW_OK;
+    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad_g<<<grid, kGradThreads, 0, st>>>(ops, start, nbx, n));
+    return launch_check("k_atom_grad_g");
 }
 
 // One warp per atom: lane c sums chunk c (c < 32 = kGradChunks), then a fixed-order
@@ -211,10 +292,58 @@ __global__ void k_grad_finalize(AtomsDev a, int chunks, const double* partials, 
     grad[5 * N + n] = lambda - s[5];
 }
 
+int grad_finalize_tiles(const GradOp& op, int* nbx) {
+    *nbx = (op.a.N + 3) / 4;
+    return *nbx;
+}
+
+// Finalize over the atoms of n ops: block t of op q handles its atoms 4 t .. 4 t + 3.
+__global__ void k_grad_finalize_g(const GradOp* __restrict__ ops, const int* __restrict__ start, int n) {
+    const int t = blockIdx.x;
+    int q = 0;
+    while (start[q + 1] <= t) ++q;
+    const GradOp& o = ops[q];
+    const int nat = (t - start[q]) * 4 + (threadIdx.x >> 5);
+    if (nat >= o.a.N) return;
+    double sums[6];
+    warp_chunk_sums(nat, kGradChunks, o.partials, sums);
+    if ((threadIdx.x & 31) != 0) return;
+    const double w = o.a.w[o.a.ps * nat];
+    const int N = o.a.N;
+    o.grad[3 * nat + 0] = -w * sums[0];
+    o.grad[3 * nat + 1] = -w * sums[1];
+    o.grad[3 * nat + 2] = -w * sums[2];
+    o.grad[3 * N + nat] = -w * sums[3];
+    o.grad[4 * N + nat] = -w * sums[4];
+    o.grad[5 * N + nat] = o.lambda - sums[5];
+}
+
+sfw_status launch_grad_finalize_group(const GradOp* ops, const int* start, const int* nbx, int n,
+                                      int total, cudaStream_t st) {
+    (void)nbx;
+    if (total <= 0) return SFW_OK;
+    SFW_LAUNCH(st, "k_grad_finalize", k_grad_finalize_g<<<total, 128, 0, st>>>(ops, start, n));
+    return launch_check("k_grad_finalize_g");
+}
+
 sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
                             const float* b, double lambda, double* partials, double* grad,
                             cudaStream_t st) {
     if (a.N <= 0) return SFW_OK;
+    if (g_recorder) {
+        GradOp op;
+        op.a = a;
+        for (int q = 0; q < 3; ++q) {
+            op.E[q] = E[q];
+            op.R[q] = R[q];
+        }
+        op.eps = eps;
+        op.b = b;
+        op.lambda = lambda;
+        op.partials = partials;
+        op.grad = grad;
+        return g_recorder->add(op);
+    }
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
     dim3 grid(a.N, kGradChunks);
     SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2,
@@ -361,8 +490,8 @@ sfw_status launch_gram(const float* A, const float* y, int N, long long V, doubl
 
 // ------------------------------------------------------------------ loss
 
-__global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, double lambda,
-                                double* loss) {
+__device__ __forceinline__ void k_loss_finalize_body(const double* partials, int nparts,
+                                                     const AtomsDev& a, double lambda, double* loss) {
     __shared__ double s_red[8];
     double acc = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
@@ -379,8 +508,33 @@ __global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, 
     }
 }
 
+__global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, double lambda,
+                                double* loss) {
+    k_loss_finalize_body(partials, nparts, a, lambda, loss);
+}
+
+__global__ void k_loss_finalize_g(const LossFinOp* __restrict__ ops) {
+    const LossFinOp& o = ops[blockIdx.x];
+    k_loss_finalize_body(o.partials, o.nparts, o.a, o.lambda, o.loss);
+}
+
+sfw_status launch_lossfin_group(const LossFinOp* ops, int n, cudaStream_t st) {
+    if (n <= 0) return SFW_OK;
+    SFW_LAUNCH(st, "k_loss_finalize", k_loss_finalize_g<<<n, 256, 0, st>>>(ops));
+    return launch_check("k_loss_finalize_g");
+}
+
 sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
                                 double lambda, double* loss, cudaStream_t st) {
+    if (g_recorder) {
+        LossFinOp op;
+        op.partials = partials;
+        op.nparts = nparts;
+        op.a = a;
+        op.lambda = lambda;
+        op.loss = loss;
+        return g_recorder->add(op);
+    }
     SFW_LAUNCH(st, "k_loss_finalize", k_loss_finalize<<<1, 256, 0, st>>>(partials, nparts, a, lambda, loss));
     return launch_check("k_loss_finalize");
 }

@@ -359,7 +359,7 @@ __device__ __forceinline__ void load_tile(const float2* in, long long Sj, const 
 }
 
 template <int W, int DIR, int LL>
-__global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
+__device__ __forceinline__ void c2c_body(const C2CPass& p, int bx, int by) {
     constexpr int NL = W / 8;
     const int L = LL > 0 ? LL : p.L;
     const int LS = pitch(L);
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
     float2* A = s_tw + L;
     float2* B = A + W * LS;
     __shared__ long long off_in[W], off_out[W];
-    const long long l0 = (long long)blockIdx.x * W;
+    const long long l0 = (long long)bx * W;
     if (threadIdx.x < W) {
         long long l = l0 + threadIdx.x;
         if (l < p.nlines) {
@@ -391,6 +391,26 @@ __global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
             p.out[off_out[i] + j * p.lout.Sj] = cscale(res[i * LS + phy(j + p.out_off)], p.scale);
     }
 }
+
+template <int W, int DIR, int LL>
+__global__ void __launch_bounds__(kThreads) k_c2c(C2CPass p) {
+    c2c_body<W, DIR, LL>(p, blockIdx.x, blockIdx.y);
+}
+
+// Persistent variant: the CTAs stride over the tiles of n passes (device array).
+template <int W, int DIR, int LL>
+__global__ void __launch_bounds__(kThreads) k_c2c_g(const C2CPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        c2c_body<W, DIR, LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
+
 
 template <int KIND>
 struct SpecInfo;
@@ -477,7 +497,7 @@ __device__ __forceinline__ void stage_spec(const MulPass& p, int L, int s, const
 }
 
 template <int W, int KIND, int LL>
-__global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
+__device__ __forceinline__ void mul_body(const MulPass& p, int bx, int by) {
     constexpr int NL = W / 8;
     constexpr int ES = SpecInfo<KIND>::bytes;
     constexpr int SW = SpecPitch<W, ES>::value;
@@ -492,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
     unsigned char* SP0 = reinterpret_cast<unsigned char*>(C + W * LS);
     unsigned char* SP1 = SP0 + sp_bytes;
     __shared__ long long off_in[W], off_out[W], off_spec[W];
-    const long long l0 = (long long)blockIdx.x * W;
+    const long long l0 = (long long)bx * W;
     if (threadIdx.x < W) {
         long long l = l0 + threadIdx.x;
         if (l < p.nlines) {
@@ -504,7 +524,7 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
     load_twiddles(s_tw, p.tw, L);
     __syncthreads();
     // grid.y splits the spectra into groups of p.nspec
-    const int k0 = (int)blockIdx.y * p.nspec;
+    const int k0 = (int)by * p.nspec;
     const int nspec = min(p.nspec, p.ktotal - k0);
     // the first spectrum travels while the forward transform runs
     stage_spec<W, KIND>(p, L, k0, off_spec, l0, SP0);
@@ -534,8 +554,28 @@ __global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
     }
 }
 
+template <int W, int KIND, int LL>
+__global__ void __launch_bounds__(kThreads) k_mul(MulPass p) {
+    mul_body<W, KIND, LL>(p, blockIdx.x, blockIdx.y);
+}
+
+// Persistent variant: the CTAs stride over the tiles of n passes (device array).
+template <int W, int KIND, int LL>
+__global__ void __launch_bounds__(kThreads) k_mul_g(const MulPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        mul_body<W, KIND, LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
+
+
 template <int W, int LL>
-__global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
+__device__ __forceinline__ void r2c_body(const R2CPass& p, int bx, int by) {
     constexpr int NL = W / 8;
     const int L = LL > 0 ? LL : p.L;
     const int LS = pitch(L);
@@ -544,7 +584,7 @@ __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
     float2* A = s_tw + L;
     float2* B = A + W * LS;
     __shared__ long long off_in[2 * W], off_out[2 * W];
-    const long long l0 = (long long)blockIdx.x * (2 * W);
+    const long long l0 = (long long)bx * (2 * W);
     if (threadIdx.x < 2 * W) {
         long long l = l0 + threadIdx.x;
         if (l < p.nlines) {
@@ -581,6 +621,26 @@ __global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
     }
 }
 
+template <int W, int LL>
+__global__ void __launch_bounds__(kThreads) k_r2c(R2CPass p) {
+    r2c_body<W, LL>(p, blockIdx.x, blockIdx.y);
+}
+
+// Persistent variant: the CTAs stride over the tiles of n passes (device array).
+template <int W, int LL>
+__global__ void __launch_bounds__(kThreads) k_r2c_g(const R2CPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        r2c_body<W, LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
+
+
 // Z = A + i B for complex line li from the staged half spectra of real lines
 // 2 li (A) and 2 li + 1 (B), with the Hermitian extension on (L/2, L).
 struct HermLoad {
@@ -610,7 +670,7 @@ __device__ __forceinline__ void stage_half(const C2RPass& p, int L, int s, const
 }
 
 template <int W, int MODE, int SLOTS, int LL>
-__global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
+__device__ __forceinline__ void c2r_body(const C2RPass& p, int bx, int by) {
     constexpr int NL = W / 8;
     const int L = LL > 0 ? LL : p.L;
     const int LS = pitch(L);
@@ -624,7 +684,7 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
     float2* R1 = R0 + 2 * W * HS;
     __shared__ long long off_in[2 * W], off_out[2 * W];
     __shared__ double s_red[kThreads / 32];
-    const long long l0 = (long long)blockIdx.x * (2 * W);
+    const long long l0 = (long long)bx * (2 * W);
     if (threadIdx.x < 2 * W) {
         long long l = l0 + threadIdx.x;
         if (l < p.nlines) {
@@ -648,7 +708,7 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
         ak[it] = 0;
     }
     // certificate: grid.y splits the kernels into groups of p.nspec
-    const int k0 = (MODE == C2R_CERTMAX) ? (int)blockIdx.y * p.nspec : 0;
+    const int k0 = (MODE == C2R_CERTMAX) ? (int)by * p.nspec : 0;
     const int nspec = (MODE == C2R_CERTMAX) ? min(p.nspec, p.ktotal - k0) : 1;
     stage_half<W>(p, L, k0, off_in, l0, R0, HS);
     cp_async_commit();
@@ -705,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
-            p.partials[blockIdx.x] = t;
+            p.partials[bx] = t;
         }
     }
     if constexpr (MODE == C2R_CERTMAX) {
@@ -736,10 +796,27 @@ __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
     }
 }
 
-// ------------------------------------------------------------------ launchers
+template <int W, int MODE, int SLOTS, int LL>
+__global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
+    c2r_body<W, MODE, SLOTS, LL>(p, blockIdx.x, blockIdx.y);
+}
 
-// Lines per CTA: 16 up to length 256, else 8 (shared memory).
-inline int tile_width(int L) { return L <= 256 ? 16 : 8; }
+// Persistent variant: the CTAs stride over the tiles of n passes (device array).
+template <int W, int MODE, int SLOTS, int LL>
+__global__ void __launch_bounds__(kThreads) k_c2r_g(const C2RPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        c2r_body<W, MODE, SLOTS, LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
+
+
+// ------------------------------------------------------------------ launchers
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel, size):
 // the attribute call is kept out of stream captures after the first use.
@@ -768,116 +845,111 @@ inline int spec_bytes(int kind) {
     return kind == SPEC_C64 ? 8 : kind == SPEC_RBF16 ? 2 : 4;
 }
 
-template <int LL>
-sfw_status run_c2c(const C2CPass& p, cudaStream_t st) {
-    if (p.nlines <= 0) return SFW_OK;
-    const int W = tile_width(p.L);
-    const size_t smem = tile_bytes(p.L, W, 2);
-    const unsigned blocks = (unsigned)((p.nlines + W - 1) / W);
-#define SFW_C2C(WW, DD)                                              \
-    do {                                                             \
-        SFW_TRY(prepare(k_c2c<WW, DD, LL>, smem));                       \
-        SFW_LAUNCH(st, "k_c2c", k_c2c<WW, DD, LL><<<blocks, kThreads, smem, st>>>(p)); \
-    } while (0)
-    if (W == 16) {
-        if (p.dir < 0) SFW_C2C(16, -1); else SFW_C2C(16, 1);
+// Single launch (g == NULL: one pass, kernel parameter by value) or persistent
+// grouped launch (g: n passes of the same template variant in device memory).
+template <class Single, class Grouped, class PassT>
+inline sfw_status run_either(Single ks, Grouped kg, const char* name, const PassT& p, dim3 grid1,
+                             size_t smem, cudaStream_t st, GroupArgs* g) {
+    if (!g) {
+        SFW_TRY(prepare(ks, smem));
+        SFW_LAUNCH(st, name, ks<<<grid1, kThreads, smem, st>>>(p));
     } else {
-        if (p.dir < 0) SFW_C2C(8, -1); else SFW_C2C(8, 1);
+        SFW_TRY(prepare(kg, smem));
+        if (g->grid <= 0) {  // resident CTAs, computed once (before any capture)
+            int dev = 0, sms = 1, per = 1;
+            SFW_CUDA(cudaGetDevice(&dev));
+            SFW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kg, kThreads, smem));
+            if (per < 1) per = 1;
+            g->grid = g->total < per * sms ? g->total : per * sms;
+        }
+        if (g->total <= 0) return SFW_OK;
+        SFW_LAUNCH(st, name, kg<<<g->grid, kThreads, smem, st>>>(
+            reinterpret_cast<const PassT*>(g->passes), g->start, g->nbx, g->n));
     }
-#undef SFW_C2C
-    return launch_check("k_c2c");
+    return launch_check(name);
 }
 
 template <int LL>
-sfw_status run_mul(const MulPass& p, cudaStream_t st) {
-    if (p.nlines <= 0) return SFW_OK;
-    const int W = tile_width(p.L);
+sfw_status run_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g) {
+    if (!g && p.nlines <= 0) return SFW_OK;
+    int W, nbx, nby;
+    pass_tiles(p, &W, &nbx, &nby);
+    const size_t smem = tile_bytes(p.L, W, 2);
+    const dim3 grid1((unsigned)nbx);
+    if (W == 16) {
+        if (p.dir < 0) return run_either(k_c2c<16, -1, LL>, k_c2c_g<16, -1, LL>, "k_c2c", p, grid1, smem, st, g);
+        return run_either(k_c2c<16, 1, LL>, k_c2c_g<16, 1, LL>, "k_c2c", p, grid1, smem, st, g);
+    }
+    if (p.dir < 0) return run_either(k_c2c<8, -1, LL>, k_c2c_g<8, -1, LL>, "k_c2c", p, grid1, smem, st, g);
+    return run_either(k_c2c<8, 1, LL>, k_c2c_g<8, 1, LL>, "k_c2c", p, grid1, smem, st, g);
+}
+
+template <int LL>
+sfw_status run_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
+    if (!g && p.nlines <= 0) return SFW_OK;
+    int W, nbx, nby;
+    pass_tiles(p, &W, &nbx, &nby);
     const int es = spec_bytes(p.spec_kind);
     const size_t sp = ((size_t)p.L * (W + 16 / es) * es + 15) & ~(size_t)15;
     const size_t smem = tile_bytes(p.L, W, 3) + 2 * sp;
-    const unsigned blocks = (unsigned)((p.nlines + W - 1) / W);
-    const dim3 grid(blocks, (unsigned)((p.ktotal + p.nspec - 1) / p.nspec));
-#define SFW_MUL(WW, KK)                                              \
-    do {                                                             \
-        SFW_TRY(prepare(k_mul<WW, KK, LL>, smem));                       \
-        SFW_LAUNCH(st, "k_mul", k_mul<WW, KK, LL><<<grid, kThreads, smem, st>>>(p)); \
-    } while (0)
+    const dim3 grid1((unsigned)nbx, (unsigned)nby);
+#define SFW_MUL(WW, KK) return run_either(k_mul<WW, KK, LL>, k_mul_g<WW, KK, LL>, "k_mul", p, grid1, smem, st, g)
     switch (p.spec_kind) {
-        case SPEC_C64: if (W == 16) SFW_MUL(16, SPEC_C64); else SFW_MUL(8, SPEC_C64); break;
-        case SPEC_R32: if (W == 16) SFW_MUL(16, SPEC_R32); else SFW_MUL(8, SPEC_R32); break;
-        case SPEC_CBF16: if (W == 16) SFW_MUL(16, SPEC_CBF16); else SFW_MUL(8, SPEC_CBF16); break;
-        default: if (W == 16) SFW_MUL(16, SPEC_RBF16); else SFW_MUL(8, SPEC_RBF16); break;
+        case SPEC_C64: if (W == 16) SFW_MUL(16, SPEC_C64); else SFW_MUL(8, SPEC_C64);
+        case SPEC_R32: if (W == 16) SFW_MUL(16, SPEC_R32); else SFW_MUL(8, SPEC_R32);
+        case SPEC_CBF16: if (W == 16) SFW_MUL(16, SPEC_CBF16); else SFW_MUL(8, SPEC_CBF16);
+        default: if (W == 16) SFW_MUL(16, SPEC_RBF16); else SFW_MUL(8, SPEC_RBF16);
     }
 #undef SFW_MUL
-    return launch_check("k_mul");
 }
 
 template <int LL>
-sfw_status run_r2c(const R2CPass& p, cudaStream_t st) {
-    if (p.nlines <= 0) return SFW_OK;
-    const int W = tile_width(p.L);
+sfw_status run_r2c(const R2CPass& p, cudaStream_t st, GroupArgs* g) {
+    if (!g && p.nlines <= 0) return SFW_OK;
+    int W, nbx, nby;
+    pass_tiles(p, &W, &nbx, &nby);
     const size_t smem = tile_bytes(p.L, W, 2);
-    const unsigned blocks = (unsigned)((p.nlines + 2 * W - 1) / (2 * W));
-    if (W == 16) {
-        SFW_TRY(prepare(k_r2c<16, LL>, smem));
-        SFW_LAUNCH(st, "k_r2c", k_r2c<16, LL><<<blocks, kThreads, smem, st>>>(p));
-    } else {
-        SFW_TRY(prepare(k_r2c<8, LL>, smem));
-        SFW_LAUNCH(st, "k_r2c", k_r2c<8, LL><<<blocks, kThreads, smem, st>>>(p));
-    }
-    return launch_check("k_r2c");
-}
-
-// The certificate epilogue keeps 2 (W / 8) * out_len running maxima per warp in
-// registers: SLOTS per lane (4, 8 or 16).  Its tiles are 8 lines wide (more CTAs,
-// fewer registers); the other modes use tile_width.
-inline int c2r_width(const C2RPass& p) {
-    return p.mode == C2R_CERTMAX ? 8 : tile_width(p.L);
+    const dim3 grid1((unsigned)nbx);
+    if (W == 16) return run_either(k_r2c<16, LL>, k_r2c_g<16, LL>, "k_r2c", p, grid1, smem, st, g);
+    return run_either(k_r2c<8, LL>, k_r2c_g<8, LL>, "k_r2c", p, grid1, smem, st, g);
 }
 
 template <int LL>
-sfw_status run_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
-    const int W = c2r_width(p);
-    const int blocks = (int)((p.nlines + 2 * W - 1) / (2 * W));
-    if (blocks_out) *blocks_out = blocks;
-    if (p.nlines <= 0) return SFW_OK;
+sfw_status run_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out, GroupArgs* g) {
+    int W, nbx, nby;
+    pass_tiles(p, &W, &nbx, &nby);
+    if (blocks_out) *blocks_out = nbx;
+    if (!g && p.nlines <= 0) return SFW_OK;
     const int need = (2 * (W / 8) * p.out_len + 31) / 32;
     if (p.mode == C2R_CERTMAX && need > kC2RMaxSlots)
         return fail(SFW_ERR_SHAPE, "c2r: %d outputs per line exceed the epilogue tile", p.out_len);
     const int H = p.L / 2 + 1;
     const size_t smem = tile_bytes(p.L, W, 2) + sizeof(float2) * 2 * 2 * (size_t)W * (H + 1);
-    const int groups = p.mode == C2R_CERTMAX ? (p.ktotal + p.nspec - 1) / p.nspec : 1;
-    const dim3 grid((unsigned)blocks, (unsigned)groups);
-#define SFW_C2R(WW, MM, SS)                                          \
-    do {                                                             \
-        SFW_TRY(prepare(k_c2r<WW, MM, SS, LL>, smem));                   \
-        SFW_LAUNCH(st, "k_c2r", k_c2r<WW, MM, SS, LL><<<grid, kThreads, smem, st>>>(p)); \
-    } while (0)
+    const dim3 grid1((unsigned)nbx, (unsigned)nby);
+#define SFW_C2R(WW, MM, SS) return run_either(k_c2r<WW, MM, SS, LL>, k_c2r_g<WW, MM, SS, LL>, "k_c2r", p, grid1, smem, st, g)
     switch (p.mode) {
-        case C2R_STORE: if (W == 16) SFW_C2R(16, C2R_STORE, 1); else SFW_C2R(8, C2R_STORE, 1); break;
-        case C2R_RESIDUAL: if (W == 16) SFW_C2R(16, C2R_RESIDUAL, 1); else SFW_C2R(8, C2R_RESIDUAL, 1); break;
+        case C2R_STORE: if (W == 16) SFW_C2R(16, C2R_STORE, 1); else SFW_C2R(8, C2R_STORE, 1);
+        case C2R_RESIDUAL: if (W == 16) SFW_C2R(16, C2R_RESIDUAL, 1); else SFW_C2R(8, C2R_RESIDUAL, 1);
         default:
             if (need <= 4) SFW_C2R(8, C2R_CERTMAX, 4);
             else if (need <= 8) SFW_C2R(8, C2R_CERTMAX, 8);
             else SFW_C2R(8, C2R_CERTMAX, 16);
-            break;
     }
 #undef SFW_C2R
-    return launch_check("k_c2r");
 }
-
 
 // explicit instantiations live in fft_len_*.cu
 #define SFW_FFT_INSTANTIATE(LL)                                                       \
-    template sfw_status run_c2c<LL>(const C2CPass&, cudaStream_t);                    \
-    template sfw_status run_mul<LL>(const MulPass&, cudaStream_t);                    \
-    template sfw_status run_r2c<LL>(const R2CPass&, cudaStream_t);                    \
-    template sfw_status run_c2r<LL>(const C2RPass&, cudaStream_t, int*);
+    template sfw_status run_c2c<LL>(const C2CPass&, cudaStream_t, GroupArgs*);        \
+    template sfw_status run_mul<LL>(const MulPass&, cudaStream_t, GroupArgs*);        \
+    template sfw_status run_r2c<LL>(const R2CPass&, cudaStream_t, GroupArgs*);        \
+    template sfw_status run_c2r<LL>(const C2RPass&, cudaStream_t, int*, GroupArgs*);
 
 #define SFW_FFT_DECLARE(LL)                                                           \
-    extern template sfw_status run_c2c<LL>(const C2CPass&, cudaStream_t);             \
-    extern template sfw_status run_mul<LL>(const MulPass&, cudaStream_t);             \
-    extern template sfw_status run_r2c<LL>(const R2CPass&, cudaStream_t);             \
-    extern template sfw_status run_c2r<LL>(const C2RPass&, cudaStream_t, int*);
+    extern template sfw_status run_c2c<LL>(const C2CPass&, cudaStream_t, GroupArgs*); \
+    extern template sfw_status run_mul<LL>(const MulPass&, cudaStream_t, GroupArgs*); \
+    extern template sfw_status run_r2c<LL>(const R2CPass&, cudaStream_t, GroupArgs*); \
+    extern template sfw_status run_c2r<LL>(const C2RPass&, cudaStream_t, int*, GroupArgs*);
 
 }  // namespace sfw

@@ -88,45 +88,93 @@ SFW_FFT_DECLARE(0)
 SFW_FFT_LENGTHS(SFW_DECL)
 #undef SFW_DECL
 
-sfw_status launch_c2c(const C2CPass& p, cudaStream_t st) {
-    switch (p.L) {
-#define SFW_CASE(LL) case LL: return run_c2c<LL>(p, st);
+bool fft_specialised(int L) {
+    switch (L) {
+#define SFW_CASE(LL) case LL: return true;
         SFW_FFT_LENGTHS(SFW_CASE)
 #undef SFW_CASE
-        default: return run_c2c<0>(p, st);
+        default: return false;
     }
 }
 
-sfw_status launch_mul(const MulPass& p, cudaStream_t st) {
+// Lines per CTA: 16 up to length 256, else 8 (shared memory).
+int tile_width(int L) { return L <= 256 ? 16 : 8; }
+
+void pass_tiles(const C2CPass& p, int* W, int* nbx, int* nby) {
+    *W = tile_width(p.L);
+    *nbx = (int)((p.nlines + *W - 1) / *W);
+    *nby = 1;
+}
+
+void pass_tiles(const MulPass& p, int* W, int* nbx, int* nby) {
+    *W = tile_width(p.L);
+    *nbx = (int)((p.nlines + *W - 1) / *W);
+    *nby = (p.ktotal + p.nspec - 1) / p.nspec;
+}
+
+void pass_tiles(const R2CPass& p, int* W, int* nbx, int* nby) {
+    *W = tile_width(p.L);
+    *nbx = (int)((p.nlines + 2 * *W - 1) / (2 * *W));
+    *nby = 1;
+}
+
+// The certificate epilogue keeps 2 (W / 8) * out_len running maxima per warp in
+// registers (SLOTS per lane): its tiles are 8 lines wide; other modes use tile_width.
+void pass_tiles(const C2RPass& p, int* W, int* nbx, int* nby) {
+    *W = p.mode == C2R_CERTMAX ? 8 : tile_width(p.L);
+    *nbx = (int)((p.nlines + 2 * *W - 1) / (2 * *W));
+    *nby = p.mode == C2R_CERTMAX ? (p.ktotal + p.nspec - 1) / p.nspec : 1;
+}
+
+sfw_status launch_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g) {
+    if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
-#define SFW_CASE(LL) case LL: return run_mul<LL>(p, st);
+#define SFW_CASE(LL) case LL: return run_c2c<LL>(p, st, g);
         SFW_FFT_LENGTHS(SFW_CASE)
 #undef SFW_CASE
-        default: return run_mul<0>(p, st);
+        default: return run_c2c<0>(p, st, g);
     }
 }
 
-sfw_status launch_r2c(const R2CPass& p, cudaStream_t st) {
+sfw_status launch_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
+    if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
-#define SFW_CASE(LL) case LL: return run_r2c<LL>(p, st);
+#define SFW_CASE(LL) case LL: return run_mul<LL>(p, st, g);
         SFW_FFT_LENGTHS(SFW_CASE)
 #undef SFW_CASE
-        default: return run_r2c<0>(p, st);
+        default: return run_mul<0>(p, st, g);
     }
 }
 
-sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out) {
+sfw_status launch_r2c(const R2CPass& p, cudaStream_t st, GroupArgs* g) {
+    if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
-#define SFW_CASE(LL) case LL: return run_c2r<LL>(p, st, blocks_out);
+#define SFW_CASE(LL) case LL: return run_r2c<LL>(p, st, g);
         SFW_FFT_LENGTHS(SFW_CASE)
 #undef SFW_CASE
-        default: return run_c2r<0>(p, st, blocks_out);
+        default: return run_r2c<0>(p, st, g);
+    }
+}
+
+sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out, GroupArgs* g) {
+    if (g_recorder && !g) {
+        int W, nbx, nby;
+        pass_tiles(p, &W, &nbx, &nby);
+        if (blocks_out) *blocks_out = nbx;
+        return g_recorder->add(p);
+    }
+    switch (p.L) {
+#define SFW_CASE(LL) case LL: return run_c2r<LL>(p, st, blocks_out, g);
+        SFW_FFT_LENGTHS(SFW_CASE)
+#undef SFW_CASE
+        default: return run_c2r<0>(p, st, blocks_out, g);
     }
 }
 
 int c2r_blocks(const C2RPass& p) {
-    const int W = c2r_width(p);
-    return (int)((p.nlines + 2 * W - 1) / (2 * W));
+    int W, nbx, nby;
+    pass_tiles(p, &W, &nbx, &nby);
+    return nbx;
 }
 
 // Per-voxel keys -> max over k and its k.

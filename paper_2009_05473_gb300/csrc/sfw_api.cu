@@ -19,6 +19,7 @@ namespace sfw {
 // ------------------------------------------------------------------ errors
 
 static thread_local char g_err[512] = "";
+thread_local Recorder* g_recorder = nullptr;
 std::atomic<int64_t> g_launches{0};
 
 sfw_status fail(sfw_status st, const char* fmt, ...) {
@@ -1054,10 +1055,18 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     }
     const bool want_vox = max_out || argk_out;
     if (best_val || best_idx) {
-        cudaError_t e = cudaMemsetAsync(p->best_key, 0, sizeof(unsigned long long), st);
-        if (e != cudaSuccess) return cuda_fail(e, "memset");
+        if (g_recorder) {
+            ZeroOp z;
+            z.ptr = p->best_key;
+            z.bytes = sizeof(unsigned long long);
+            SFW_TRY(g_recorder->add(z));
+        } else {
+            cudaError_t e = cudaMemsetAsync(p->best_key, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset");
+        }
     }
     if (want_vox) {
+        if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the argmax-only certificate");
         cudaError_t e = cudaMemsetAsync(p->vox_key, 0, sizeof(unsigned long long) * (size_t)p->V, st);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
     }
@@ -1237,6 +1246,360 @@ sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_o
         return launch_argmax_final(scratch, nb, val_out, idx_out, st);
     }
     return launch_topk(values, count, topk, scratch, scratch_len, val_out, idx_out, st);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches of volumes
+
+namespace {
+
+// One grouped launch of a batch step.
+struct BatchLaunch {
+    OpKind kind;
+    int finalize;        // OP_GRAD: 0 = adjoint sums, 1 = their finalisation
+    RecOp proto;         // prototype pass (largest length of the group) for the FFT kinds
+    GroupArgs g;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Key of the kernel variant an op launches (ops with equal keys share a launch).
+std::string variant_key(const RecOp& o) {
+    char b[128];
+    int W, nbx, nby;
+    switch (o.kind) {
+        case OP_R2C:
+            pass_tiles(o.r2c, &W, &nbx, &nby);
+            snprintf(b, sizeof(b), "r2c/%d/%d", fft_specialised(o.r2c.L) ? o.r2c.L : 0, W);
+            break;
+        case OP_C2C:
+            pass_tiles(o.c2c, &W, &nbx, &nby);
+            snprintf(b, sizeof(b), "c2c/%d/%d/%d", fft_specialised(o.c2c.L) ? o.c2c.L : 0, W, o.c2c.dir);
+            break;
+        case OP_MUL:
+            pass_tiles(o.mul, &W, &nbx, &nby);
+            snprintf(b, sizeof(b), "mul/%d/%d/%d", fft_specialised(o.mul.L) ? o.mul.L : 0, W, o.mul.spec_kind);
+            break;
+        case OP_C2R: {
+            pass_tiles(o.c2r, &W, &nbx, &nby);
+            const int need = (2 * (W / 8) * o.c2r.out_len + 31) / 32;
+            const int slots = o.c2r.mode != C2R_CERTMAX ? 1 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
+            snprintf(b, sizeof(b), "c2r/%d/%d/%d/%d", fft_specialised(o.c2r.L) ? o.c2r.L : 0, W, o.c2r.mode, slots);
+            break;
+        }
+        default:
+            snprintf(b, sizeof(b), "op/%d", (int)o.kind);
+    }
+    return b;
+}
+
+int op_length(const RecOp& o) {
+    switch (o.kind) {
+        case OP_R2C: return o.r2c.L;
+        case OP_C2C: return o.c2c.L;
+        case OP_MUL: return o.mul.L;
+        case OP_C2R: return o.c2r.L;
+        default: return 0;
+    }
+}
+
+// Tiles of an op in a grouped launch: (x tiles, total tiles).
+void op_tiles(const RecOp& o, int finalize, int* nbx, int* total) {
+    int W, nby;
+    switch (o.kind) {
+        case OP_R2C: pass_tiles(o.r2c, &W, nbx, &nby); *total = *nbx * nby; break;
+        case OP_C2C: pass_tiles(o.c2c, &W, nbx, &nby); *total = *nbx * nby; break;
+        case OP_MUL: pass_tiles(o.mul, &W, nbx, &nby); *total = *nbx * nby; break;
+        case OP_C2R: pass_tiles(o.c2r, &W, nbx, &nby); *total = *nbx * nby; break;
+        case OP_RENDER: *total = render_tiles(o.render, nbx); break;
+        case OP_GRAD: *total = finalize ? grad_finalize_tiles(o.grad, nbx) : grad_tiles(o.grad, nbx); break;
+        default: *nbx = 1; *total = 1;
+    }
+}
+
+template <class T>
+const T& op_payload(const RecOp& o);
+template <> const R2CPass& op_payload<R2CPass>(const RecOp& o) { return o.r2c; }
+template <> const C2CPass& op_payload<C2CPass>(const RecOp& o) { return o.c2c; }
+template <> const MulPass& op_payload<MulPass>(const RecOp& o) { return o.mul; }
+template <> const C2RPass& op_payload<C2RPass>(const RecOp& o) { return o.c2r; }
+template <> const RenderOp& op_payload<RenderOp>(const RecOp& o) { return o.render; }
+template <> const GradOp& op_payload<GradOp>(const RecOp& o) { return o.grad; }
+template <> const LossFinOp& op_payload<LossFinOp>(const RecOp& o) { return o.lossfin; }
+template <> const KeyDecodeOp& op_payload<KeyDecodeOp>(const RecOp& o) { return o.keydec; }
+template <> const ZeroOp& op_payload<ZeroOp>(const RecOp& o) { return o.zero; }
+
+template <class T>
+void append_payloads(const std::vector<const RecOp*>& ops, std::vector<unsigned char>& blob) {
+    for (const RecOp* o : ops) {
+        const T& t = op_payload<T>(*o);
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&t);
+        blob.insert(blob.end(), b, b + sizeof(T));
+    }
+}
+
+size_t payload_size(OpKind k) {
+    switch (k) {
+        case OP_R2C: return sizeof(R2CPass);
+        case OP_C2C: return sizeof(C2CPass);
+        case OP_MUL: return sizeof(MulPass);
+        case OP_C2R: return sizeof(C2RPass);
+        case OP_RENDER: return sizeof(RenderOp);
+        case OP_GRAD: return sizeof(GradOp);
+        case OP_LOSSFIN: return sizeof(LossFinOp);
+        case OP_KEYDECODE: return sizeof(KeyDecodeOp);
+        default: return sizeof(ZeroOp);
+    }
+}
+
+}  // namespace
+
+struct sfw_batch {
+    int count;
+    int num_sms;
+    std::vector<sfw_plan*> plans;
+    std::vector<BatchLaunch> launches;
+    void* blob;           // device descriptors of every grouped launch
+};
+
+static void batch_free(sfw_batch* b) {
+    if (b->blob) cudaFree(b->blob);
+    b->blob = nullptr;
+}
+
+extern "C" {
+
+sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_volume* vols,
+                            const double* lambdas, sfw_batch** out) {
+    clear_error();
+    if (!out || !plans || !vols || !lambdas) return fail(SFW_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (count < 1 || count > 1024) return fail(SFW_ERR_ARG, "count must be in [1, 1024]");
+    for (int v = 0; v < count; ++v) {
+        const sfw_batch_volume& bv = vols[v];
+        if (!plans[v]) return fail(SFW_ERR_ARG, "plan %d is NULL", v);
+        if (plans[v]->K == 0) return fail(SFW_ERR_ARG, "plan %d has no certificate grid", v);
+        if (bv.N < 1 || bv.N > 4096) return fail(SFW_ERR_ARG, "volume %d: atoms outside [1, 4096]", v);
+        if (!bv.y || !bv.m || !bv.sigma || !bv.d || !bv.w || !bv.residual || !bv.grad || !bv.loss ||
+            !bv.best_val || !bv.best_idx)
+            return fail(SFW_ERR_ARG, "volume %d: every buffer must be non-NULL", v);
+        if (!(lambdas[v] > 0.0) || !isfinite(lambdas[v])) return fail(SFW_ERR_ARG, "volume %d: lambda must be > 0", v);
+        for (int u = 0; u < v; ++u)
+            if (plans[u] == plans[v]) return fail(SFW_ERR_ARG, "plans %d and %d are the same plan", u, v);
+    }
+    sfw_batch* b = new (std::nothrow) sfw_batch();
+    if (!b) return fail(SFW_ERR_ALLOC, "host allocation");
+    b->count = count;
+    b->blob = nullptr;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        b->num_sms = 0;
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (b->num_sms <= 0) b->num_sms = 1;
+    }
+    sfw_status s = SFW_OK;
+    std::vector<Recorder> rec(count);
+    do {
+        // record one step per volume through the single-volume code path
+        for (int v = 0; v < count && !s; ++v) {
+            sfw_plan* p = plans[v];
+            const sfw_batch_volume& bv = vols[v];
+            b->plans.push_back(p);
+            sfw_atoms at;
+            at.N = bv.N;
+            at.m = bv.m;
+            at.sigma = bv.sigma;
+            at.d = bv.d;
+            at.w = bv.w;
+            g_recorder = &rec[v];
+            s = sfw_slide_loss_grad(p, bv.y, &at, lambdas[v], bv.loss, bv.grad, bv.residual, nullptr);
+            if (!s) s = sfw_certificate_grid(p, bv.residual, lambdas[v], nullptr, nullptr, nullptr,
+                                             bv.best_val, bv.best_idx, nullptr);
+            g_recorder = nullptr;
+        }
+        if (s) break;
+        const size_t nops = rec[0].ops.size();
+        for (int v = 1; v < count && !s; ++v) {
+            if (rec[v].ops.size() != nops) s = fail(SFW_ERR_UNSUPPORTED, "volumes record different steps");
+            for (size_t i = 0; i < nops && !s; ++i)
+                if (rec[v].ops[i].kind != rec[0].ops[i].kind) s = fail(SFW_ERR_UNSUPPORTED, "volumes record different steps");
+        }
+        if (s) break;
+        // group the ops of every stage by kernel variant; lay out their descriptors
+        std::vector<unsigned char> blob;
+        struct Pending {
+            BatchLaunch L;
+            size_t off_passes, off_start, off_nbx;
+        };
+        std::vector<Pending> pend;
+        for (size_t i = 0; i < nops; ++i) {
+            const int passes = rec[0].ops[i].kind == OP_GRAD ? 2 : 1;
+            for (int fin = 0; fin < passes; ++fin) {
+                std::vector<std::string> keys;
+                std::vector<std::vector<const RecOp*>> groups;
+                for (int v = 0; v < count; ++v) {
+                    const RecOp* o = &rec[v].ops[i];
+                    std::string k = variant_key(*o);
+                    size_t gi = 0;
+                    while (gi < keys.size() && keys[gi] != k) ++gi;
+                    if (gi == keys.size()) {
+                        keys.push_back(k);
+                        groups.emplace_back();
+                    }
+                    groups[gi].push_back(o);
+                }
+                for (auto& grp : groups) {
+                    Pending P;
+                    memset(&P.L, 0, sizeof(P.L));
+                    P.L.kind = grp[0]->kind;
+                    P.L.finalize = fin;
+                    const RecOp* proto = grp[0];
+                    for (const RecOp* o : grp)
+                        if (op_length(*o) > op_length(*proto)) proto = o;
+                    P.L.proto = *proto;
+                    P.L.g.n = (int)grp.size();
+                    std::vector<int> start(grp.size() + 1, 0), nbx(grp.size(), 1);
+                    for (size_t q = 0; q < grp.size(); ++q) {
+                        int nx, tot;
+                        op_tiles(*grp[q], fin, &nx, &tot);
+                        nbx[q] = nx;
+                        start[q + 1] = start[q] + tot;
+                    }
+                    P.L.g.total = start.back();
+                    P.L.g.grid = 0;
+                    blob.resize(align16(blob.size()));
+                    P.off_passes = blob.size();
+                    switch (P.L.kind) {
+                        case OP_R2C: append_payloads<R2CPass>(grp, blob); break;
+                        case OP_C2C: append_payloads<C2CPass>(grp, blob); break;
+                        case OP_MUL: append_payloads<MulPass>(grp, blob); break;
+                        case OP_C2R: append_payloads<C2RPass>(grp, blob); break;
+                        case OP_RENDER: append_payloads<RenderOp>(grp, blob); break;
+                        case OP_GRAD: append_payloads<GradOp>(grp, blob); break;
+                        case OP_LOSSFIN: append_payloads<LossFinOp>(grp, blob); break;
+                        case OP_KEYDECODE: append_payloads<KeyDecodeOp>(grp, blob); break;
+                        default: append_payloads<ZeroOp>(grp, blob); break;
+                    }
+                    blob.resize(align16(blob.size()));
+                    P.off_start = blob.size();
+                    blob.insert(blob.end(), reinterpret_cast<unsigned char*>(start.data()),
+                                reinterpret_cast<unsigned char*>(start.data() + start.size()));
+                    blob.resize(align16(blob.size()));
+                    P.off_nbx = blob.size();
+                    blob.insert(blob.end(), reinterpret_cast<unsigned char*>(nbx.data()),
+                                reinterpret_cast<unsigned char*>(nbx.data() + nbx.size()));
+                    pend.push_back(P);
+                }
+            }
+        }
+        cudaError_t e = cudaMalloc(&b->blob, blob.size() ? blob.size() : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(SFW_ERR_ALLOC, "batch descriptors");
+            break;
+        }
+        e = cudaMemcpy(b->blob, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            s = cuda_fail(e, "batch descriptors");
+            break;
+        }
+        unsigned char* base = static_cast<unsigned char*>(b->blob);
+        for (auto& P : pend) {
+            P.L.g.passes = base + P.off_passes;
+            P.L.g.start = reinterpret_cast<const int*>(base + P.off_start);
+            P.L.g.nbx = reinterpret_cast<const int*>(base + P.off_nbx);
+            b->launches.push_back(P.L);
+        }
+    } while (0);
+    g_recorder = nullptr;
+    if (s) {
+        batch_free(b);
+        delete b;
+        return s;
+    }
+    *out = b;
+    return SFW_OK;
+}
+
+sfw_status sfw_batch_destroy(sfw_batch* b) {
+    clear_error();
+    if (!b) return SFW_OK;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+    return SFW_OK;
+}
+
+sfw_status sfw_batch_query(const sfw_batch* b, int* launches_per_step) {
+    clear_error();
+    if (!b || !launches_per_step) return fail(SFW_ERR_ARG, "NULL argument");
+    *launches_per_step = (int)b->launches.size();
+    return SFW_OK;
+}
+
+sfw_status sfw_batch_step(sfw_batch* b, void* stream) {
+    clear_error();
+    if (!b) return fail(SFW_ERR_ARG, "batch is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (BatchLaunch& L : b->launches) {
+        GroupArgs& g = L.g;
+        switch (L.kind) {
+            case OP_R2C: {
+                LaunchTag t("batch_r2c");
+                SFW_TRY(launch_r2c(L.proto.r2c, st, &g));
+                break;
+            }
+            case OP_C2C: {
+                LaunchTag t("batch_c2c");
+                SFW_TRY(launch_c2c(L.proto.c2c, st, &g));
+                break;
+            }
+            case OP_MUL: {
+                LaunchTag t(L.proto.mul.ktotal > 1 ? "batch_cert_axis0" : "batch_axis0");
+                SFW_TRY(launch_mul(L.proto.mul, st, &g));
+                break;
+            }
+            case OP_C2R: {
+                LaunchTag t(L.proto.c2r.mode == C2R_CERTMAX ? "batch_cert_c2r_max" : "batch_c2r");
+                SFW_TRY(launch_c2r(L.proto.c2r, st, nullptr, &g));
+                break;
+            }
+            case OP_RENDER: {
+                if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
+                LaunchTag t("batch_render");
+                SFW_TRY(launch_render_group(static_cast<const RenderOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
+                break;
+            }
+            case OP_GRAD: {
+                LaunchTag t(L.finalize ? "batch_grad_finalize" : "batch_atom_grad");
+                if (L.finalize) {
+                    SFW_TRY(launch_grad_finalize_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, st));
+                } else {
+                    if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
+                    SFW_TRY(launch_grad_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
+                }
+                break;
+            }
+            case OP_LOSSFIN: {
+                LaunchTag t("batch_loss_finalize");
+                SFW_TRY(launch_lossfin_group(static_cast<const LossFinOp*>(g.passes), g.n, st));
+                break;
+            }
+            case OP_KEYDECODE: {
+                LaunchTag t("batch_key_decode");
+                SFW_TRY(launch_keydecode_group(static_cast<const KeyDecodeOp*>(g.passes), g.n, st));
+                break;
+            }
+            default: {
+                LaunchTag t("batch_zero");
+                SFW_TRY(launch_zero_group(static_cast<const ZeroOp*>(g.passes), g.n, st));
+                break;
+            }
+        }
+    }
+    return SFW_OK;
 }
 
 }  // extern "C"

@@ -173,12 +173,33 @@ struct C2RPass {
     int ktotal;           // CERTMAX: number of spectra; grid.y groups them by nspec
 };
 
-// launchers (fft_kernels.cu)
-sfw_status launch_c2c(const C2CPass& p, cudaStream_t st);
-sfw_status launch_mul(const MulPass& p, cudaStream_t st);
-sfw_status launch_r2c(const R2CPass& p, cudaStream_t st);
+// A persistent grouped launch: n passes of one kernel variant, their
+// descriptors and tile prefix sums in device memory.  Pass q owns tiles
+// [start[q], start[q+1]); tile t of it maps to (t % nbx[q], t / nbx[q]).
+struct GroupArgs {
+    const void* passes;
+    const int* start;
+    const int* nbx;
+    int n;
+    int total;
+    int grid;  // CTAs launched (0: resident CTAs of the kernel, computed on first use)
+};
+
+// Tile width W and tile grid (nbx, nby) of a pass (same rule for single and grouped launches).
+int tile_width(int L);
+void pass_tiles(const C2CPass& p, int* W, int* nbx, int* nby);
+void pass_tiles(const MulPass& p, int* W, int* nbx, int* nby);
+void pass_tiles(const R2CPass& p, int* W, int* nbx, int* nby);
+void pass_tiles(const C2RPass& p, int* W, int* nbx, int* nby);
+// Lengths with compile-time kernels (others run the generic code).
+bool fft_specialised(int L);
+
+// launchers (fft_kernels.cu); g != NULL launches the group instead of p
+sfw_status launch_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g = nullptr);
+sfw_status launch_mul(const MulPass& p, cudaStream_t st, GroupArgs* g = nullptr);
+sfw_status launch_r2c(const R2CPass& p, cudaStream_t st, GroupArgs* g = nullptr);
 // returns the number of blocks used (for the residual partials) via *blocks
-sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks);
+sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks, GroupArgs* g = nullptr);
 int c2r_blocks(const C2RPass& p);
 sfw_status launch_vox_decode(const unsigned long long* key, long long V, float* max_out,
                              int* argk_out, cudaStream_t st);
@@ -220,6 +241,88 @@ sfw_status launch_gram(const float* A, const float* y, int N, long long V, doubl
 // sum_n w_n added to the loss: loss = 0.5 * sum(partials) + lambda * sum w
 sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
                                 double lambda, double* loss, cudaStream_t st);
+
+// ------------------------------------------------------------------ non-FFT ops as descriptors
+// (one launch each, or grouped over the volumes of a batch)
+
+struct RenderOp {
+    AtomsDev a;
+    int E[3], R[3];
+    float eps;
+    float* f;
+};
+struct GradOp {
+    AtomsDev a;
+    int E[3], R[3];
+    float eps;
+    const float* b;
+    double lambda;
+    double* partials;
+    double* grad;
+};
+struct LossFinOp {
+    const double* partials;
+    int nparts;
+    AtomsDev a;
+    double lambda;
+    double* loss;
+};
+struct KeyDecodeOp {
+    const unsigned long long* key;
+    float* val;
+    int64_t* idx;
+};
+struct ZeroOp {
+    void* ptr;
+    long long bytes;  // multiple of 8
+};
+
+// Grouped launches of the non-FFT ops (device arrays of n ops).
+sfw_status launch_render_group(const RenderOp* ops, const int* start, const int* nbx, int n,
+                               int total, int grid, cudaStream_t st);
+sfw_status launch_grad_group(const GradOp* ops, const int* start, const int* nbx, int n, int total,
+                             int grid, cudaStream_t st);
+sfw_status launch_grad_finalize_group(const GradOp* ops, const int* start, const int* nbx, int n,
+                                      int total, cudaStream_t st);
+sfw_status launch_lossfin_group(const LossFinOp* ops, int n, cudaStream_t st);
+sfw_status launch_keydecode_group(const KeyDecodeOp* ops, int n, cudaStream_t st);
+sfw_status launch_zero_group(const ZeroOp* ops, int n, cudaStream_t st);
+// tiles of one render / adjoint op
+int render_tiles(const RenderOp& op, int* nbx);
+int grad_tiles(const GradOp& op, int* nbx);
+int grad_finalize_tiles(const GradOp& op, int* nbx);
+
+// ------------------------------------------------------------------ recording (batches)
+// While g_recorder is set on this thread, every launcher appends its op here
+// instead of launching; a batch replays the ops of all its volumes stage by stage.
+enum OpKind {
+    OP_R2C = 0, OP_C2C, OP_MUL, OP_C2R, OP_RENDER, OP_GRAD, OP_LOSSFIN, OP_KEYDECODE, OP_ZERO
+};
+struct RecOp {
+    OpKind kind;
+    R2CPass r2c;
+    C2CPass c2c;
+    MulPass mul;
+    C2RPass c2r;
+    RenderOp render;
+    GradOp grad;
+    LossFinOp lossfin;
+    KeyDecodeOp keydec;
+    ZeroOp zero;
+};
+struct Recorder {
+    std::vector<RecOp> ops;
+    sfw_status add(const R2CPass& p) { RecOp o{}; o.kind = OP_R2C; o.r2c = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const C2CPass& p) { RecOp o{}; o.kind = OP_C2C; o.c2c = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const MulPass& p) { RecOp o{}; o.kind = OP_MUL; o.mul = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const C2RPass& p) { RecOp o{}; o.kind = OP_C2R; o.c2r = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const RenderOp& p) { RecOp o{}; o.kind = OP_RENDER; o.render = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const GradOp& p) { RecOp o{}; o.kind = OP_GRAD; o.grad = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const LossFinOp& p) { RecOp o{}; o.kind = OP_LOSSFIN; o.lossfin = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const KeyDecodeOp& p) { RecOp o{}; o.kind = OP_KEYDECODE; o.keydec = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const ZeroOp& p) { RecOp o{}; o.kind = OP_ZERO; o.zero = p; ops.push_back(o); return SFW_OK; }
+};
+extern thread_local Recorder* g_recorder;
 
 // ------------------------------------------------------------------ misc kernels (reduce.cu)
 // dst[p] = src box value with circular placement (see definitions in reduce.cu)
