@@ -289,6 +289,13 @@ sfw_status sfw_batch_destroy(sfw_batch* batch);
 sfw_status sfw_batch_query(const sfw_batch* batch, int* launches_per_step);
 /* One hot-path step for every volume of the batch, asynchronous on stream. */
 sfw_status sfw_batch_step(sfw_batch* batch, void* stream);
+/* Autotuner: for every grouped launch, time persistent grids of {resident
+ * CTAs, 1, 2, 4, 8 x SMs, all tiles} on the batch's live buffers (after one
+ * full step) and keep the fastest.  With cache_path (host string, may be
+ * NULL) the choices are written there, keyed by the batch's launch list, and
+ * read back by later calls with the same list instead of timing again.
+ * Synchronous; not capturable (run it before capturing sfw_batch_step). */
+sfw_status sfw_batch_autotune(sfw_batch* batch, const char* cache_path, void* stream);
 
 /* Thread-local text of the last error of this thread ("" if none). */
 const char* sfw_last_error(void);

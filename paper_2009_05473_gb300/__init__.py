@@ -250,6 +250,10 @@ class Batch:
     def step(self, stream=None):
         _abi.sfw_batch_step(self.handle, _stream_ptr(stream))
 
+    def autotune(self, cache_path: Optional[str] = None, stream=None):
+        """Pick the persistent grid of every grouped launch by timing (cached in cache_path)."""
+        _abi.sfw_batch_autotune(self.handle, cache_path, _stream_ptr(stream))
+
     def close(self):
         if getattr(self, "handle", None):
             _abi.sfw_batch_destroy(self.handle)

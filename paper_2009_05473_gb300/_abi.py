@@ -23,7 +23,7 @@ SFW_PREC_BF16 = 1
 EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
            "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
            "sfw_slide_loss_grad", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
-           "sfw_batch_query", "sfw_batch_step", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
+           "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
            "sfw_launch_count",
            "sfw_version")
 
@@ -89,12 +89,13 @@ def lib() -> ctypes.CDLL:
     L.sfw_batch_destroy.argtypes = [vp]
     L.sfw_batch_query.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.sfw_batch_step.argtypes = [vp, vp]
+    L.sfw_batch_autotune.argtypes = [vp, ctypes.c_char_p, vp]
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
                  "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
                  "sfw_slide_loss_grad", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
-           "sfw_batch_query", "sfw_batch_step", "sfw_profile_start", "sfw_profile_collect",
+           "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect",
                  "sfw_profile_stop"):
         getattr(L, name).restype = ctypes.c_int
     L.sfw_last_error.restype = ctypes.c_char_p
@@ -198,6 +199,11 @@ def sfw_batch_query(batch: int) -> int:
 
 def sfw_batch_step(batch: int, stream: int) -> None:
     check(lib().sfw_batch_step(batch, stream), "sfw_batch_step")
+
+
+def sfw_batch_autotune(batch: int, cache_path, stream: int) -> None:
+    check(lib().sfw_batch_autotune(batch, cache_path.encode() if cache_path else None, stream),
+          "sfw_batch_autotune")
 
 
 def sfw_profile_start(max_launches: int, only_tag: str = None) -> None:

@@ -1368,6 +1368,65 @@ static void batch_free(sfw_batch* b) {
     b->blob = nullptr;
 }
 
+// One grouped launch of a batch step (also timed alone by the autotuner).
+static sfw_status batch_launch(sfw_batch* b, BatchLaunch& L, cudaStream_t st) {
+    GroupArgs& g = L.g;
+    switch (L.kind) {
+        case OP_R2C: {
+            LaunchTag t("batch_r2c");
+            SFW_TRY(launch_r2c(L.proto.r2c, st, &g));
+            break;
+        }
+        case OP_C2C: {
+            LaunchTag t("batch_c2c");
+            SFW_TRY(launch_c2c(L.proto.c2c, st, &g));
+            break;
+        }
+        case OP_MUL: {
+            LaunchTag t(L.proto.mul.ktotal > 1 ? "batch_cert_axis0" : "batch_axis0");
+            SFW_TRY(launch_mul(L.proto.mul, st, &g));
+            break;
+        }
+        case OP_C2R: {
+            LaunchTag t(L.proto.c2r.mode == C2R_CERTMAX ? "batch_cert_c2r_max" : "batch_c2r");
+            SFW_TRY(launch_c2r(L.proto.c2r, st, nullptr, &g));
+            break;
+        }
+        case OP_RENDER: {
+            if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
+            LaunchTag t("batch_render");
+            SFW_TRY(launch_render_group(static_cast<const RenderOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
+            break;
+        }
+        case OP_GRAD: {
+            LaunchTag t(L.finalize ? "batch_grad_finalize" : "batch_atom_grad");
+            if (L.finalize) {
+                SFW_TRY(launch_grad_finalize_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, st));
+            } else {
+                if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
+                SFW_TRY(launch_grad_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
+            }
+            break;
+        }
+        case OP_LOSSFIN: {
+            LaunchTag t("batch_loss_finalize");
+            SFW_TRY(launch_lossfin_group(static_cast<const LossFinOp*>(g.passes), g.n, st));
+            break;
+        }
+        case OP_KEYDECODE: {
+            LaunchTag t("batch_key_decode");
+            SFW_TRY(launch_keydecode_group(static_cast<const KeyDecodeOp*>(g.passes), g.n, st));
+            break;
+        }
+        default: {
+            LaunchTag t("batch_zero");
+            SFW_TRY(launch_zero_group(static_cast<const ZeroOp*>(g.passes), g.n, st));
+            break;
+        }
+    }
+    return SFW_OK;
+}
+
 extern "C" {
 
 sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_volume* vols,
@@ -1543,61 +1602,99 @@ sfw_status sfw_batch_step(sfw_batch* b, void* stream) {
     clear_error();
     if (!b) return fail(SFW_ERR_ARG, "batch is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (BatchLaunch& L : b->launches) {
-        GroupArgs& g = L.g;
-        switch (L.kind) {
-            case OP_R2C: {
-                LaunchTag t("batch_r2c");
-                SFW_TRY(launch_r2c(L.proto.r2c, st, &g));
-                break;
-            }
-            case OP_C2C: {
-                LaunchTag t("batch_c2c");
-                SFW_TRY(launch_c2c(L.proto.c2c, st, &g));
-                break;
-            }
-            case OP_MUL: {
-                LaunchTag t(L.proto.mul.ktotal > 1 ? "batch_cert_axis0" : "batch_axis0");
-                SFW_TRY(launch_mul(L.proto.mul, st, &g));
-                break;
-            }
-            case OP_C2R: {
-                LaunchTag t(L.proto.c2r.mode == C2R_CERTMAX ? "batch_cert_c2r_max" : "batch_c2r");
-                SFW_TRY(launch_c2r(L.proto.c2r, st, nullptr, &g));
-                break;
-            }
-            case OP_RENDER: {
-                if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
-                LaunchTag t("batch_render");
-                SFW_TRY(launch_render_group(static_cast<const RenderOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
-                break;
-            }
-            case OP_GRAD: {
-                LaunchTag t(L.finalize ? "batch_grad_finalize" : "batch_atom_grad");
-                if (L.finalize) {
-                    SFW_TRY(launch_grad_finalize_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, st));
-                } else {
-                    if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
-                    SFW_TRY(launch_grad_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
+    for (BatchLaunch& L : b->launches) SFW_TRY(batch_launch(b, L, st));
+    return SFW_OK;
+}
+
+sfw_status sfw_batch_autotune(sfw_batch* b, const char* cache_path, void* stream) {
+    clear_error();
+    if (!b) return fail(SFW_ERR_ARG, "batch is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // signature of the launch list: kind, group size, total tiles of every launch
+    std::string sig = "sfw-batch-v1";
+    for (const BatchLaunch& L : b->launches) {
+        char t[64];
+        snprintf(t, sizeof(t), " %d.%d.%d.%d", (int)L.kind, L.finalize, L.g.n, L.g.total);
+        sig += t;
+    }
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "r");
+        if (f) {
+            std::string text;
+            char buf[4096];
+            size_t got;
+            while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+            fclose(f);
+            // {"signature": "<sig>", "grids": [g0, g1, ...]}
+            const std::string want = "\"signature\": \"" + sig + "\"";
+            const size_t at = text.find("\"grids\": [");
+            if (text.find(want) != std::string::npos && at != std::string::npos) {
+                std::vector<int> grids;
+                const char* c = text.c_str() + at + 10;
+                char* end = nullptr;
+                while (true) {
+                    while (*c == ' ' || *c == ',') ++c;
+                    long v = strtol(c, &end, 10);
+                    if (end == c) break;
+                    grids.push_back((int)v);
+                    c = end;
                 }
-                break;
-            }
-            case OP_LOSSFIN: {
-                LaunchTag t("batch_loss_finalize");
-                SFW_TRY(launch_lossfin_group(static_cast<const LossFinOp*>(g.passes), g.n, st));
-                break;
-            }
-            case OP_KEYDECODE: {
-                LaunchTag t("batch_key_decode");
-                SFW_TRY(launch_keydecode_group(static_cast<const KeyDecodeOp*>(g.passes), g.n, st));
-                break;
-            }
-            default: {
-                LaunchTag t("batch_zero");
-                SFW_TRY(launch_zero_group(static_cast<const ZeroOp*>(g.passes), g.n, st));
-                break;
+                if (grids.size() == b->launches.size()) {
+                    for (size_t i = 0; i < grids.size(); ++i) b->launches[i].g.grid = grids[i];
+                    return SFW_OK;
+                }
             }
         }
+    }
+    // a full step first: every launch then re-runs idempotently on live buffers
+    SFW_TRY(sfw_batch_step(b, stream));
+    SFW_CUDA(cudaStreamSynchronize(st));
+    cudaEvent_t e0, e1;
+    SFW_CUDA(cudaEventCreate(&e0));
+    SFW_CUDA(cudaEventCreate(&e1));
+    sfw_status s = SFW_OK;
+    for (BatchLaunch& L : b->launches) {
+        const bool tunable = L.kind == OP_R2C || L.kind == OP_C2C || L.kind == OP_MUL || L.kind == OP_C2R ||
+                             L.kind == OP_RENDER || (L.kind == OP_GRAD && !L.finalize);
+        if (!tunable || L.g.total <= 1) continue;
+        const int resident = L.g.grid;  // default chosen by the first step
+        const int cand[6] = {resident, b->num_sms, 2 * b->num_sms, 4 * b->num_sms, 8 * b->num_sms, L.g.total};
+        int best = resident;
+        float best_ms = 1e30f;
+        for (int c = 0; c < 6 && !s; ++c) {
+            int gsz = cand[c] < L.g.total ? cand[c] : L.g.total;
+            if (gsz < 1) continue;
+            L.g.grid = gsz;
+            if ((s = batch_launch(b, L, st))) break;  // warm
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && !s; ++r) s = batch_launch(b, L, st);
+            cudaEventRecord(e1, st);
+            if (s) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(e, "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = gsz;
+            }
+        }
+        L.g.grid = best;
+        if (s) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "w");
+        if (!f) return fail(SFW_ERR_ARG, "cannot write %s", cache_path);
+        fprintf(f, "{\"signature\": \"%s\", \"grids\": [", sig.c_str());
+        for (size_t i = 0; i < b->launches.size(); ++i) fprintf(f, "%s%d", i ? ", " : "", b->launches[i].g.grid);
+        fprintf(f, "]}\n");
+        fclose(f);
     }
     return SFW_OK;
 }
