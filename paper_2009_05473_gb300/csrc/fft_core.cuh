@@ -168,11 +168,19 @@ struct CFac {
     int ns[kMaxFactors];
 };
 
-__host__ __device__ constexpr CFac cfactor(int L) {
+__host__ __device__ constexpr int max_radix_c(int L, int nl) {
+    int r = 16;
+    while (r > 2 && (L / r) * nl < 32) r >>= 1;
+    return r;
+}
+
+// Same order as the host's factorize(L, maxr) (the twiddle layout depends on it).
+__host__ __device__ constexpr CFac cfactor(int L, int maxr) {
     CFac f{};
     const int rad[6] = {16, 8, 4, 2, 3, 5};
     int ns = 1;
     for (int q = 0; q < 6; ++q) {
+        if (rad[q] <= 16 && (rad[q] & (rad[q] - 1)) == 0 && rad[q] > maxr) continue;
         while (L % rad[q] == 0 && L > 1) {
             f.r[f.n] = rad[q];
             f.ns[f.n] = ns;
@@ -192,7 +200,6 @@ __device__ __forceinline__ void wstage(const float2* __restrict__ src, float2* _
                                        int L, int LS, int li0, int nl, int Ns,
                                        const float2* __restrict__ tw, const Load& load) {
     const int LR = L / R;
-    const int tstep = L / (Ns * R);
     const int total = LR * nl;
     for (int t = (int)(threadIdx.x & 31); t < total; t += 32) {
         const int lq = t / LR;
@@ -208,7 +215,7 @@ __device__ __forceinline__ void wstage(const float2* __restrict__ src, float2* _
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[k * r * tstep];
+                float2 w = tw[(Ns - 1) + (r - 1) * Ns + k];
                 if (DIR > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -260,7 +267,6 @@ template <int R, int DIR, bool FIRST, int L, int NS, int NL, class Load>
 __device__ __forceinline__ void cstage(const float2* __restrict__ src, float2* __restrict__ dst,
                                        int li0, const float2* __restrict__ tw, const Load& load) {
     constexpr int LR = L / R;
-    constexpr int TSTEP = L / (NS * R);
     constexpr int TOTAL = LR * NL;
     constexpr int LS = pitch(L);
     const int lane = (int)(threadIdx.x & 31);
@@ -281,7 +287,7 @@ __device__ __forceinline__ void cstage(const float2* __restrict__ src, float2* _
             if constexpr (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = tw[k * r * TSTEP];
+                    float2 w = tw[(NS - 1) + (r - 1) * NS + k];
                     if (DIR > 0) w.y = -w.y;
                     v[r] = cmul(v[r], w);
                 }
@@ -298,7 +304,7 @@ __device__ __forceinline__ void cstage(const float2* __restrict__ src, float2* _
 template <int DIR, int L, int NL, int S, class Load>
 __device__ __forceinline__ float2* cstages(float2* src, float2* dst, int li0, const float2* tw,
                                            const Load& load) {
-    constexpr CFac F = cfactor(L);
+    constexpr CFac F = cfactor(L, max_radix_c(L, NL));
     if constexpr (S >= F.n) {
         return src;
     } else {

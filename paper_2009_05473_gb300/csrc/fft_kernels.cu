@@ -18,18 +18,31 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "fft_core.cuh"
 
 namespace sfw {
 
 // ------------------------------------------------------------------ host helpers
 
-bool factorize(int L, Factors* f) {
+// Largest power-of-two radix that still gives every lane of a warp a butterfly
+// when a warp owns nl lines of length L: (L / R) nl >= 32.
+int max_radix(int L, int nl) {
+    int r = 16;
+    while (r > 2 && (L / r) * nl < 32) r >>= 1;
+    return r;
+}
+
+bool factorize(int L, Factors* f, int maxr) {
     f->n = 0;
     if (L < 1 || L > kMaxLen) return false;
     const int radices[6] = {16, 8, 4, 2, 3, 5};
     for (int q = 0; q < 6; ++q) {
         int r = radices[q];
+        if (r <= 16 && (r & (r - 1)) == 0 && r > maxr) continue;
         while (L % r == 0 && L > 1) {
             if (f->n >= kMaxFactors) return false;
             f->r[f->n++] = r;
@@ -50,33 +63,75 @@ int next_smooth_even(int x) {
     }
 }
 
-sfw_status TwiddleCache::get(int L, const float2** out) {
-    auto it = tables.find(L);
-    if (it != tables.end()) {
+namespace {
+std::mutex g_tw_mu;
+std::map<std::tuple<int, int, int>, float2*> g_tw;  // (device, L, max radix) -> table
+}  // namespace
+
+// Per-stage twiddles in the order of the Stockham stages of factorize(L, maxr):
+// stage s (radix R, Ns = product of the earlier radices) stores
+// exp(-2 pi i k r / (Ns R)) at (Ns - 1) + (r - 1) Ns + k, r = 1..R-1, k < Ns (the
+// stages telescope to L - 1 entries), so that the lanes of a warp read
+// consecutive entries.  Tables live until process exit.
+sfw_status twiddle_table(int L, int maxr, const float2** out) {
+    int dev = 0;
+    SFW_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto key = std::make_tuple(dev, L, maxr);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) {
         *out = it->second;
         return SFW_OK;
     }
-    std::vector<float2> h(L);
+    Factors fac;
+    if (!factorize(L, &fac, maxr)) return fail(SFW_ERR_SHAPE, "cannot factor %d", L);
+    std::vector<float2> h(L, make_float2(1.f, 0.f));
     const double two_pi = 6.283185307179586476925286766559;
-    for (int j = 0; j < L; ++j) {
-        double a = -two_pi * (double)j / (double)L;
-        h[j] = make_float2((float)cos(a), (float)sin(a));
+    int Ns = 1;
+    for (int st = 0; st < fac.n; ++st) {
+        const int R = fac.r[st];
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                const double a = -two_pi * (double)k * (double)r / ((double)Ns * (double)R);
+                h[(Ns - 1) + (r - 1) * Ns + k] = make_float2((float)cos(a), (float)sin(a));
+            }
+        Ns *= R;
     }
     float2* d = nullptr;
-    if (cudaMalloc(&d, sizeof(float2) * L) != cudaSuccess) return fail(SFW_ERR_ALLOC, "twiddle table");
+    if (cudaMalloc(&d, sizeof(float2) * L) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SFW_ERR_ALLOC, "twiddle table");
+    }
     cudaError_t e = cudaMemcpy(d, h.data(), sizeof(float2) * L, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(d);
         return cuda_fail(e, "twiddle upload");
     }
-    tables[L] = d;
+    g_tw[key] = d;
     *out = d;
     return SFW_OK;
 }
 
-void TwiddleCache::release() {
-    for (auto& kv : tables) cudaFree(kv.second);
-    tables.clear();
+// Make the tables of length L for every tile width a pass of that length can
+// use (so that launches, and stream captures, never allocate).
+sfw_status TwiddleCache::get(int L, const float2** out) {
+    const int ws[2] = {8, 16};
+    for (int q = 0; q < 2; ++q) {
+        const float2* t = nullptr;
+        SFW_TRY(twiddle_table(L, max_radix(L, ws[q] / 8), &t));
+        if (ws[q] == tile_width(L)) *out = t;
+    }
+    if (tile_width(L) != 8 && tile_width(L) != 16) return fail(SFW_ERR_SHAPE, "tile width");
+    return SFW_OK;
+}
+
+void TwiddleCache::release() { tables.clear(); }
+
+// The factors and twiddles of a pass follow the lines each warp owns (W / 8).
+static sfw_status fit_factors(int L, int W, Factors* fac, const float2** tw) {
+    const int mr = max_radix(L, W / 8);
+    if (!factorize(L, fac, mr)) return fail(SFW_ERR_SHAPE, "cannot factor %d", L);
+    return twiddle_table(L, mr, tw);
 }
 
 // ------------------------------------------------------------------ length dispatch
@@ -126,7 +181,13 @@ void pass_tiles(const C2RPass& p, int* W, int* nbx, int* nby) {
     *nby = p.mode == C2R_CERTMAX ? (p.ktotal + p.nspec - 1) / p.nspec : 1;
 }
 
-sfw_status launch_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g) {
+sfw_status launch_c2c(const C2CPass& p0, cudaStream_t st, GroupArgs* g) {
+    C2CPass p = p0;
+    if (!g) {
+        int W, nbx, nby;
+        pass_tiles(p, &W, &nbx, &nby);
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+    }
     if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
 #define SFW_CASE(LL) case LL: return run_c2c<LL>(p, st, g);
@@ -136,7 +197,13 @@ sfw_status launch_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g) {
     }
 }
 
-sfw_status launch_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
+sfw_status launch_mul(const MulPass& p0, cudaStream_t st, GroupArgs* g) {
+    MulPass p = p0;
+    if (!g) {
+        int W, nbx, nby;
+        pass_tiles(p, &W, &nbx, &nby);
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+    }
     if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
 #define SFW_CASE(LL) case LL: return run_mul<LL>(p, st, g);
@@ -146,7 +213,13 @@ sfw_status launch_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
     }
 }
 
-sfw_status launch_r2c(const R2CPass& p, cudaStream_t st, GroupArgs* g) {
+sfw_status launch_r2c(const R2CPass& p0, cudaStream_t st, GroupArgs* g) {
+    R2CPass p = p0;
+    if (!g) {
+        int W, nbx, nby;
+        pass_tiles(p, &W, &nbx, &nby);
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+    }
     if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
 #define SFW_CASE(LL) case LL: return run_r2c<LL>(p, st, g);
@@ -156,7 +229,13 @@ sfw_status launch_r2c(const R2CPass& p, cudaStream_t st, GroupArgs* g) {
     }
 }
 
-sfw_status launch_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out, GroupArgs* g) {
+sfw_status launch_c2r(const C2RPass& p0, cudaStream_t st, int* blocks_out, GroupArgs* g) {
+    C2RPass p = p0;
+    if (!g) {
+        int W, nbx, nby;
+        pass_tiles(p, &W, &nbx, &nby);
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+    }
     if (g_recorder && !g) {
         int W, nbx, nby;
         pass_tiles(p, &W, &nbx, &nby);

@@ -64,8 +64,13 @@ struct Factors {
     int r[kMaxFactors];
 };
 
-// Split L into radices 8, 4, 2, 3, 5 (false if another prime divides L).
-bool factorize(int L, Factors* f);
+// Split L into radices 16, 8, 4, 2, 3, 5 with power-of-two radices <= maxr
+// (false if another prime divides L).
+bool factorize(int L, Factors* f, int maxr = 16);
+// Largest power-of-two radix that keeps all 32 lanes busy with nl lines per warp.
+int max_radix(int L, int nl);
+// Per-stage twiddles of factorize(L, maxr) (device table, cached per device).
+sfw_status twiddle_table(int L, int maxr, const float2** out);
 // Smallest 2-3-5 smooth even integer >= x.
 int next_smooth_even(int x);
 
@@ -82,7 +87,7 @@ __host__ __device__ inline long long line_offset(const LineSet& s, long long l) 
     return a * s.Sa + b * s.Sb;
 }
 
-// Twiddle tables exp(-2 pi i j / L), j < L, one per length (device, float2).
+// Per-stage twiddle tables, one per length (device, float2; layout in fft_kernels.cu).
 struct TwiddleCache {
     std::map<int, float2*> tables;
     sfw_status get(int L, const float2** out);
