@@ -175,11 +175,25 @@ __device__ __forceinline__ double block_sum(double v, double* s_red) {
     return t;
 }
 
-// grid = (N, kGradChunks): chunk c of atom n strides over the atom's box.
+// Warp 0 sums the chunk partials of atom n in a fixed order (lane c takes chunk c).
+__device__ __forceinline__ void warp_chunk_sums(int n, int chunks, const double* partials, double s[6]) {
+    const int lane = threadIdx.x & 31;
+    for (int q = 0; q < 6; ++q) {
+        double v = 0.0;
+        for (int c = lane; c < chunks; c += 32) v += __ldcg(partials + ((long long)n * chunks + c) * 6 + q);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        s[q] = v;
+    }
+}
+
+// Chunk c (of nchunks) of atom n strides over the atom's box and writes six
+// partial sums; the last chunk-block of the atom to finish turns the atom's
+// partials into its gradient entries (mode 0) or its certificate and
+// certificate gradient (mode 1), then re-arms the atom's counter.
 __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1, int E2, int R0,
                                                int R1, int R2, float log_inv_eps2,
                                                const float* __restrict__ b, double* partials, int n,
-                                               int c, int nchunks) {
+                                               int c, int nchunks, const AdjFin& fin) {
     __shared__ double s_red[kGradThreads / 32];
     const float m0 = a.m[a.ms * n + 0], m1 = a.m[a.ms * n + 1], m2 = a.m[a.ms * n + 2];
     const float sg = a.sigma[a.ps * n], dd = a.d[a.ps * n];
@@ -226,13 +240,35 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
         const double t = block_sum(out[q], s_red);
         if (threadIdx.x == 0) partials[((long long)n * nchunks + c) * 6 + q] = t;
     }
+    if (!fin.counters || !last_block(fin.counters + n, nchunks)) return;
+    if (threadIdx.x < 32) {
+        double su[6];
+        warp_chunk_sums(n, nchunks, partials, su);
+        if (threadIdx.x == 0) {
+            if (fin.mode == 0) {
+                const double w = a.w[a.ps * n];
+                const int N = a.N;
+                fin.grad[3 * n + 0] = -w * su[0];
+                fin.grad[3 * n + 1] = -w * su[1];
+                fin.grad[3 * n + 2] = -w * su[2];
+                fin.grad[3 * N + n] = -w * su[3];
+                fin.grad[4 * N + n] = -w * su[4];
+                fin.grad[5 * N + n] = fin.lambda - su[5];
+            } else {
+                fin.eta[n] = su[5] / fin.lambda;
+                if (fin.grad)
+                    for (int q = 0; q < 5; ++q) fin.grad[5 * n + q] = su[q] / fin.lambda;
+            }
+            fin.counters[n] = 0u;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kGradThreads)
 k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2,
-            const float* __restrict__ b, double* partials) {
+            const float* __restrict__ b, double* partials, AdjFin fin) {
     atom_grad_body(a, E0, E1, E2, R0, R1, R2, log_inv_eps2, b, partials, blockIdx.x, blockIdx.y,
-                   gridDim.y);
+                   gridDim.y, fin);
 }
 
 int grad_tiles(const GradOp& op, int* nbx) {
@@ -251,7 +287,7 @@ k_atom_grad_g(const GradOp* __restrict__ ops, const int* __restrict__ start, con
         const int local = t - start[q];
         const float lie2 = log2f(2.0f * logf(1.0f / o.eps));
         atom_grad_body(o.a, o.E[0], o.E[1], o.E[2], o.R[0], o.R[1], o.R[2], lie2, o.b, o.partials,
-                       local / kGradChunks, local % kGradChunks, kGradChunks);
+                       local / kGradChunks, local % kGradChunks, kGradChunks, o.fin);
         __syncthreads();
     }
 }
@@ -263,72 +299,8 @@ sfw_status launch_grad_group(const GradOp* ops, const int* start, const int* nbx
     return launch_check("k_atom_grad_g");
 }
 
-// One warp per atom: lane c sums chunk c (c < 32 = kGradChunks), then a fixed-order
-// shuffle tree (deterministic).
-__device__ __forceinline__ void warp_chunk_sums(int n, int chunks, const double* partials, double s[6]) {
-    const int lane = threadIdx.x & 31;
-    for (int q = 0; q < 6; ++q) {
-        double v = 0.0;
-        for (int c = lane; c < chunks; c += 32) v += partials[((long long)n * chunks + c) * 6 + q];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        s[q] = v;
-    }
-}
-
-__global__ void k_grad_finalize(AtomsDev a, int chunks, const double* partials, double lambda,
-                                double* grad) {
-    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (n >= a.N) return;
-    double s[6];
-    warp_chunk_sums(n, chunks, partials, s);
-    if ((threadIdx.x & 31) != 0) return;
-    const double w = a.w[a.ps * n];
-    const int N = a.N;
-    grad[3 * n + 0] = -w * s[0];
-    grad[3 * n + 1] = -w * s[1];
-    grad[3 * n + 2] = -w * s[2];
-    grad[3 * N + n] = -w * s[3];
-    grad[4 * N + n] = -w * s[4];
-    grad[5 * N + n] = lambda - s[5];
-}
-
-int grad_finalize_tiles(const GradOp& op, int* nbx) {
-    *nbx = (op.a.N + 3) / 4;
-    return *nbx;
-}
-
-// Finalize over the atoms of n ops: block t of op q handles its atoms 4 t .. 4 t + 3.
-__global__ void k_grad_finalize_g(const GradOp* __restrict__ ops, const int* __restrict__ start, int n) {
-    const int t = blockIdx.x;
-    int q = 0;
-    while (start[q + 1] <= t) ++q;
-    const GradOp& o = ops[q];
-    const int nat = (t - start[q]) * 4 + (threadIdx.x >> 5);
-    if (nat >= o.a.N) return;
-    double sums[6];
-    warp_chunk_sums(nat, kGradChunks, o.partials, sums);
-    if ((threadIdx.x & 31) != 0) return;
-    const double w = o.a.w[o.a.ps * nat];
-    const int N = o.a.N;
-    o.grad[3 * nat + 0] = -w * sums[0];
-    o.grad[3 * nat + 1] = -w * sums[1];
-    o.grad[3 * nat + 2] = -w * sums[2];
-    o.grad[3 * N + nat] = -w * sums[3];
-    o.grad[4 * N + nat] = -w * sums[4];
-    o.grad[5 * N + nat] = o.lambda - sums[5];
-}
-
-sfw_status launch_grad_finalize_group(const GradOp* ops, const int* start, const int* nbx, int n,
-                                      int total, cudaStream_t st) {
-    (void)nbx;
-    if (total <= 0) return SFW_OK;
-    SFW_LAUNCH(st, "k_grad_finalize", k_grad_finalize_g<<<total, 128, 0, st>>>(ops, start, n));
-    return launch_check("k_grad_finalize_g");
-}
-
-sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
-                            const float* b, double lambda, double* partials, double* grad,
-                            cudaStream_t st) {
+static sfw_status adjoint(const AtomsDev& a, const int E[3], const int R[3], float eps,
+                          const float* b, double* partials, const AdjFin& fin, cudaStream_t st) {
     if (a.N <= 0) return SFW_OK;
     if (g_recorder) {
         GradOp op;
@@ -339,45 +311,38 @@ sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], f
         }
         op.eps = eps;
         op.b = b;
-        op.lambda = lambda;
         op.partials = partials;
-        op.grad = grad;
+        op.fin = fin;
         return g_recorder->add(op);
     }
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
     dim3 grid(a.N, kGradChunks);
-    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2,
-                                                b, partials));
-    SFW_TRY(launch_check("k_atom_grad"));
-    SFW_LAUNCH(st, "k_grad_finalize", k_grad_finalize<<<(a.N + 3) / 4, 128, 0, st>>>(a, kGradChunks, partials, lambda, grad));
-    return launch_check("k_grad_finalize");
+    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, b, partials, fin));
+    return launch_check("k_atom_grad");
 }
 
-// eta and its gradient at parameter rows: the same per-atom sums, scaled by 1/lambda.
-__global__ void k_eta_finalize(int P, int chunks, const double* partials, double lambda,
-                               double* eta, double* grad) {
-    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (n >= P) return;
-    double s[6];
-    warp_chunk_sums(n, chunks, partials, s);
-    if ((threadIdx.x & 31) != 0) return;
-    eta[n] = s[5] / lambda;
-    if (grad)
-        for (int q = 0; q < 5; ++q) grad[5 * n + q] = s[q] / lambda;
+sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
+                            const float* b, double lambda, double* partials, double* grad,
+                            unsigned int* counters, cudaStream_t st) {
+    AdjFin fin;
+    fin.mode = 0;
+    fin.lambda = lambda;
+    fin.grad = grad;
+    fin.eta = nullptr;
+    fin.counters = counters;
+    return adjoint(a, E, R, eps, b, partials, fin, st);
 }
 
 sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3], float eps,
                              const float* b, double lambda, double* partials, double* eta,
-                             double* grad, cudaStream_t st) {
-    if (pts.N <= 0) return SFW_OK;
-    const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
-    dim3 grid(pts.N, kGradChunks);
-    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(pts, E[0], E[1], E[2], R[0], R[1], R[2],
-                                                log_inv_eps2, b, partials));
-    SFW_TRY(launch_check("k_atom_grad"));
-    SFW_LAUNCH(st, "k_eta_finalize", k_eta_finalize<<<(pts.N + 3) / 4, 128, 0, st>>>(pts.N, kGradChunks, partials, lambda, eta,
-                                                        grad));
-    return launch_check("k_eta_finalize");
+                             double* grad, unsigned int* counters, cudaStream_t st) {
+    AdjFin fin;
+    fin.mode = 1;
+    fin.lambda = lambda;
+    fin.grad = grad;
+    fin.eta = eta;
+    fin.counters = counters;
+    return adjoint(pts, E, R, eps, b, partials, fin, st);
 }
 
 // ------------------------------------------------------------------ top-k re-scoring
@@ -486,57 +451,6 @@ sfw_status launch_gram(const float* A, const float* y, int N, long long V, doubl
     const int pairs = N * (N + 1) / 2 + N;
     SFW_LAUNCH(st, "k_gram", k_gram<<<pairs, 256, 0, st>>>(A, y, N, V, G, c));
     return launch_check("k_gram");
-}
-
-// ------------------------------------------------------------------ loss
-
-__device__ __forceinline__ void k_loss_finalize_body(const double* partials, int nparts,
-                                                     const AtomsDev& a, double lambda, double* loss) {
-    __shared__ double s_red[8];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partials[i];
-    double wsum = 0.0;
-    for (int i = threadIdx.x; i < a.N; i += blockDim.x) wsum += (double)a.w[a.ps * i];
-    double v = 0.5 * acc + lambda * wsum;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += s_red[q];
-        *loss = t;
-    }
-}
-
-__global__ void k_loss_finalize(const double* partials, int nparts, AtomsDev a, double lambda,
-                                double* loss) {
-    k_loss_finalize_body(partials, nparts, a, lambda, loss);
-}
-
-__global__ void k_loss_finalize_g(const LossFinOp* __restrict__ ops) {
-    const LossFinOp& o = ops[blockIdx.x];
-    k_loss_finalize_body(o.partials, o.nparts, o.a, o.lambda, o.loss);
-}
-
-sfw_status launch_lossfin_group(const LossFinOp* ops, int n, cudaStream_t st) {
-    if (n <= 0) return SFW_OK;
-    SFW_LAUNCH(st, "k_loss_finalize", k_loss_finalize_g<<<n, 256, 0, st>>>(ops));
-    return launch_check("k_loss_finalize_g");
-}
-
-sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
-                                double lambda, double* loss, cudaStream_t st) {
-    if (g_recorder) {
-        LossFinOp op;
-        op.partials = partials;
-        op.nparts = nparts;
-        op.a = a;
-        op.lambda = lambda;
-        op.loss = loss;
-        return g_recorder->add(op);
-    }
-    SFW_LAUNCH(st, "k_loss_finalize", k_loss_finalize<<<1, 256, 0, st>>>(partials, nparts, a, lambda, loss));
-    return launch_check("k_loss_finalize");
 }
 
 }  // namespace sfw

@@ -347,6 +347,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// ------------------------------------------------------------------ last-tile reductions
+
+// Fixed-order block sum of one double per thread (result in thread 0).
+__device__ __forceinline__ double block_sum_d(double v, double* s_red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kThreads / 32; ++q) t += s_red[q];
+    return t;
+}
+
 // ------------------------------------------------------------------ kernels
 
 // Rows [in_off, in_off + in_len) of W strided lines -> tile (padded layout), by
@@ -773,6 +787,18 @@ __device__ __forceinline__ void c2r_body(const C2RPass& p, int bx, int by) {
             for (int w = 0; w < kThreads / 32; ++w) t += s_red[w];
             p.partials[bx] = t;
         }
+        // the last tile to finish forms C = 1/2 sum r^2 + lambda sum w (fixed order)
+        if (p.loss_out && last_block(p.counter, p.ntiles)) {
+            double a = 0.0;
+            for (int i = threadIdx.x; i < p.ntiles; i += kThreads) a += __ldcg(p.partials + i);
+            double wsum = 0.0;
+            for (int i = threadIdx.x; i < p.nw; i += kThreads) wsum += (double)__ldg(p.w + (long long)i * p.w_stride);
+            const double t = block_sum_d(0.5 * a + p.lambda * wsum, s_red);
+            if (threadIdx.x == 0) {
+                *p.loss_out = t;
+                *p.counter = 0u;
+            }
+        }
     }
     if constexpr (MODE == C2R_CERTMAX) {
         unsigned long long best = 0ull;
@@ -798,6 +824,19 @@ __device__ __forceinline__ void c2r_body(const C2RPass& p, int bx, int by) {
                 if (o2 > best) best = o2;
             }
             if (lane == 0 && best) atomicMax(p.best_key, best);
+            // the last tile decodes the key and re-arms it (0) for the next call
+            __syncthreads();
+            if (last_block(p.counter, p.ntiles) && threadIdx.x == 0) {
+                const unsigned long long k = atomicExch(p.best_key, 0ull);
+                if (k == ~0ull || k == 0ull) {
+                    if (p.best_val) *p.best_val = __int_as_float(0x7fc00000);
+                    if (p.best_idx) *p.best_idx = -1;
+                } else {
+                    if (p.best_val) *p.best_val = float_from_order_key((unsigned int)(k >> 32));
+                    if (p.best_idx) *p.best_idx = (int64_t)(0xffffffffu - (unsigned int)(k & 0xffffffffu));
+                }
+                *p.counter = 0u;
+            }
         }
     }
 }

@@ -235,6 +235,7 @@ sfw_status launch_c2r(const C2RPass& p0, cudaStream_t st, int* blocks_out, Group
         int W, nbx, nby;
         pass_tiles(p, &W, &nbx, &nby);
         SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+        p.ntiles = nbx * nby;
     }
     if (g_recorder && !g) {
         int W, nbx, nby;

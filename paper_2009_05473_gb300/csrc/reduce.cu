@@ -130,63 +130,6 @@ sfw_status launch_argmax_final(const unsigned long long* partial, int n, float* 
     return launch_check("k_argmax_final");
 }
 
-__global__ void k_key_decode(const unsigned long long* key, float* val, int64_t* idx) {
-    const unsigned long long best = *key;
-    if (best == ~0ull || best == 0ull) {
-        if (val) *val = __int_as_float(0x7fc00000);
-        if (idx) *idx = -1;
-    } else {
-        if (val) *val = float_from_order_key((unsigned int)(best >> 32));
-        if (idx) *idx = (int64_t)(0xffffffffu - (unsigned int)(best & 0xffffffffu));
-    }
-}
-
-__global__ void k_key_decode_g(const KeyDecodeOp* __restrict__ ops, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const KeyDecodeOp& o = ops[i];
-    const unsigned long long best = *o.key;
-    if (best == ~0ull || best == 0ull) {
-        if (o.val) *o.val = __int_as_float(0x7fc00000);
-        if (o.idx) *o.idx = -1;
-    } else {
-        if (o.val) *o.val = float_from_order_key((unsigned int)(best >> 32));
-        if (o.idx) *o.idx = (int64_t)(0xffffffffu - (unsigned int)(best & 0xffffffffu));
-    }
-}
-
-sfw_status launch_keydecode_group(const KeyDecodeOp* ops, int n, cudaStream_t st) {
-    if (n <= 0) return SFW_OK;
-    SFW_LAUNCH(st, "k_key_decode", k_key_decode_g<<<(n + 63) / 64, 64, 0, st>>>(ops, n));
-    return launch_check("k_key_decode_g");
-}
-
-// Zero n buffers (bytes a multiple of 8): one block per buffer.
-__global__ void k_zero_g(const ZeroOp* __restrict__ ops) {
-    const ZeroOp& o = ops[blockIdx.x];
-    unsigned long long* p = reinterpret_cast<unsigned long long*>(o.ptr);
-    for (long long i = threadIdx.x; i < o.bytes / 8; i += blockDim.x) p[i] = 0ull;
-}
-
-sfw_status launch_zero_group(const ZeroOp* ops, int n, cudaStream_t st) {
-    if (n <= 0) return SFW_OK;
-    SFW_LAUNCH(st, "k_zero", k_zero_g<<<n, 256, 0, st>>>(ops));
-    return launch_check("k_zero_g");
-}
-
-sfw_status launch_key_decode(const unsigned long long* key, float* val, int64_t* idx,
-                             cudaStream_t st) {
-    if (g_recorder) {
-        KeyDecodeOp op;
-        op.key = key;
-        op.val = val;
-        op.idx = idx;
-        return g_recorder->add(op);
-    }
-    SFW_LAUNCH(st, "k_key_decode", k_key_decode<<<1, 1, 0, st>>>(key, val, idx));
-    return launch_check("k_key_decode");
-}
-
 // ------------------------------------------------------------------ top-k (k <= 64)
 
 constexpr int kSortN = 4096;  // keys sorted per block

@@ -497,6 +497,8 @@ struct sfw_plan {
     float2* cB;
     float2* cC;
     unsigned long long* best_key;
+    unsigned int* ctr;            // last-block counters of the fused loss / argmax finalisers
+    unsigned int* adj_ctr;        // one last-block counter per atom of the adjoint
     unsigned long long* vox_key;  // V per-voxel certificate keys
     float* grid_sd;               // 2K floats on the device: sigma_k, d_k
     float* vmax;                  // V: per-voxel max over k (top-k path)
@@ -827,6 +829,15 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         p->grad_parts_atoms = 4096;
         if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;
         if ((s = plan_alloc_t(p, &p->best_key, 2))) break;
+        if ((s = plan_alloc_t(p, &p->ctr, 16))) break;
+        if ((s = plan_alloc_t(p, &p->adj_ctr, (size_t)p->grad_parts_atoms))) break;
+        // the fused finalisers re-arm these themselves after every use
+        if (cudaMemset(p->best_key, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(p->ctr, 0, 16 * sizeof(unsigned int)) != cudaSuccess ||
+            cudaMemset(p->adj_ctr, 0, (size_t)p->grad_parts_atoms * sizeof(unsigned int)) != cudaSuccess) {
+            s = cuda_fail(cudaGetLastError(), "counter reset");
+            break;
+        }
         if ((s = plan_alloc_t(p, &p->vox_key, (size_t)p->V))) break;
         if ((s = plan_alloc_t(p, &p->unit_slot, 8))) break;
         if (K > 0) {
@@ -940,13 +951,19 @@ sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* ato
     ep.out = r;
     ep.y = y;
     ep.partials = p->loss_parts;
+    ep.loss_out = loss_out;
+    ep.counter = p->ctr + 0;
+    ep.w = atoms->w;
+    ep.nw = atoms->N;
+    ep.w_stride = 1;
+    ep.lambda = lambda;
     int blocks = 0;
     SFW_TRY(blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, &blocks));
     if (blocks > p->loss_parts_len) return fail(SFW_ERR_SHAPE, "loss partial buffer too small");
-    SFW_TRY(launch_loss_finalize(p->loss_parts, blocks, a, lambda, loss_out, st));
     if (!grad_out) return SFW_OK;  // loss only
     SFW_TRY(blur_transpose(p->blur, r, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
-    return launch_atom_grad(a, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, grad_out, st);
+    return launch_atom_grad(a, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, grad_out,
+                            p->adj_ctr, st);
 }
 
 sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambda, float* eta_out,
@@ -1054,17 +1071,6 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         }
     }
     const bool want_vox = max_out || argk_out;
-    if (best_val || best_idx) {
-        if (g_recorder) {
-            ZeroOp z;
-            z.ptr = p->best_key;
-            z.bytes = sizeof(unsigned long long);
-            SFW_TRY(g_recorder->add(z));
-        } else {
-            cudaError_t e = cudaMemsetAsync(p->best_key, 0, sizeof(unsigned long long), st);
-            if (e != cudaSuccess) return cuda_fail(e, "memset");
-        }
-    }
     if (want_vox) {
         if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the argmax-only certificate");
         cudaError_t e = cudaMemsetAsync(p->vox_key, 0, sizeof(unsigned long long) * (size_t)p->V, st);
@@ -1089,6 +1095,9 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
     q.V = p->V;
     q.vox_key = want_vox ? p->vox_key : nullptr;
     q.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+    q.best_val = best_val;
+    q.best_idx = best_idx;
+    q.counter = p->ctr + 1;
     // split the kernels into groups so that the launch fills the GPU (about 3 CTAs per SM)
     q.nspec = K;
     {
@@ -1103,7 +1112,6 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         SFW_TRY(launch_c2r(q, st, nullptr));
     }
     if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
-    if (best_val || best_idx) SFW_TRY(launch_key_decode(p->best_key, best_val, best_idx, st));
     return SFW_OK;
 }
 
@@ -1175,7 +1183,7 @@ sfw_status sfw_certificate_topk(sfw_plan* p, const float* residual, double lambd
     pts.ms = 5;
     pts.ps = 5;
     SFW_TRY(launch_eta_points(pts, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, p->cand_eta,
-                              nullptr, st));
+                              nullptr, p->adj_ctr, st));
     // 4. the best re-scored candidate and the requested copies
     return launch_candidate_select(p->cand_theta, p->cand_val, p->cand_eta, topk, cand_theta,
                                    cand_grid, cand_eta, best_theta, best_eta, st);
@@ -1198,7 +1206,7 @@ sfw_status sfw_eta_points(sfw_plan* p, const float* residual, double lambda, int
     pts.ms = 5;
     pts.ps = 5;
     return launch_eta_points(pts, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, eta_out,
-                             grad_out, st);
+                             grad_out, p->adj_ctr, st);
 }
 
 // Test hook (not part of the public header): copy an internal plan buffer to
@@ -1257,7 +1265,6 @@ namespace {
 // One grouped launch of a batch step.
 struct BatchLaunch {
     OpKind kind;
-    int finalize;        // OP_GRAD: 0 = adjoint sums, 1 = their finalisation
     RecOp proto;         // prototype pass (largest length of the group) for the FFT kinds
     GroupArgs g;
 };
@@ -1305,7 +1312,7 @@ int op_length(const RecOp& o) {
 }
 
 // Tiles of an op in a grouped launch: (x tiles, total tiles).
-void op_tiles(const RecOp& o, int finalize, int* nbx, int* total) {
+void op_tiles(const RecOp& o, int* nbx, int* total) {
     int W, nby;
     switch (o.kind) {
         case OP_R2C: pass_tiles(o.r2c, &W, nbx, &nby); *total = *nbx * nby; break;
@@ -1313,7 +1320,7 @@ void op_tiles(const RecOp& o, int finalize, int* nbx, int* total) {
         case OP_MUL: pass_tiles(o.mul, &W, nbx, &nby); *total = *nbx * nby; break;
         case OP_C2R: pass_tiles(o.c2r, &W, nbx, &nby); *total = *nbx * nby; break;
         case OP_RENDER: *total = render_tiles(o.render, nbx); break;
-        case OP_GRAD: *total = finalize ? grad_finalize_tiles(o.grad, nbx) : grad_tiles(o.grad, nbx); break;
+        case OP_GRAD: *total = grad_tiles(o.grad, nbx); break;
         default: *nbx = 1; *total = 1;
     }
 }
@@ -1326,9 +1333,6 @@ template <> const MulPass& op_payload<MulPass>(const RecOp& o) { return o.mul; }
 template <> const C2RPass& op_payload<C2RPass>(const RecOp& o) { return o.c2r; }
 template <> const RenderOp& op_payload<RenderOp>(const RecOp& o) { return o.render; }
 template <> const GradOp& op_payload<GradOp>(const RecOp& o) { return o.grad; }
-template <> const LossFinOp& op_payload<LossFinOp>(const RecOp& o) { return o.lossfin; }
-template <> const KeyDecodeOp& op_payload<KeyDecodeOp>(const RecOp& o) { return o.keydec; }
-template <> const ZeroOp& op_payload<ZeroOp>(const RecOp& o) { return o.zero; }
 
 template <class T>
 void append_payloads(const std::vector<const RecOp*>& ops, std::vector<unsigned char>& blob) {
@@ -1347,9 +1351,7 @@ size_t payload_size(OpKind k) {
         case OP_C2R: return sizeof(C2RPass);
         case OP_RENDER: return sizeof(RenderOp);
         case OP_GRAD: return sizeof(GradOp);
-        case OP_LOSSFIN: return sizeof(LossFinOp);
-        case OP_KEYDECODE: return sizeof(KeyDecodeOp);
-        default: return sizeof(ZeroOp);
+        default: return 0;
     }
 }
 
@@ -1399,30 +1401,13 @@ static sfw_status batch_launch(sfw_batch* b, BatchLaunch& L, cudaStream_t st) {
             break;
         }
         case OP_GRAD: {
-            LaunchTag t(L.finalize ? "batch_grad_finalize" : "batch_atom_grad");
-            if (L.finalize) {
-                SFW_TRY(launch_grad_finalize_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, st));
-            } else {
-                if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
-                SFW_TRY(launch_grad_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
-            }
+            if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
+            LaunchTag t("batch_atom_grad");
+            SFW_TRY(launch_grad_group(static_cast<const GradOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
             break;
         }
-        case OP_LOSSFIN: {
-            LaunchTag t("batch_loss_finalize");
-            SFW_TRY(launch_lossfin_group(static_cast<const LossFinOp*>(g.passes), g.n, st));
-            break;
-        }
-        case OP_KEYDECODE: {
-            LaunchTag t("batch_key_decode");
-            SFW_TRY(launch_keydecode_group(static_cast<const KeyDecodeOp*>(g.passes), g.n, st));
-            break;
-        }
-        default: {
-            LaunchTag t("batch_zero");
-            SFW_TRY(launch_zero_group(static_cast<const ZeroOp*>(g.passes), g.n, st));
-            break;
-        }
+        default:
+            return fail(SFW_ERR_UNSUPPORTED, "unknown batch op");
     }
     return SFW_OK;
 }
@@ -1494,63 +1479,57 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
         };
         std::vector<Pending> pend;
         for (size_t i = 0; i < nops; ++i) {
-            const int passes = rec[0].ops[i].kind == OP_GRAD ? 2 : 1;
-            for (int fin = 0; fin < passes; ++fin) {
-                std::vector<std::string> keys;
-                std::vector<std::vector<const RecOp*>> groups;
-                for (int v = 0; v < count; ++v) {
-                    const RecOp* o = &rec[v].ops[i];
-                    std::string k = variant_key(*o);
-                    size_t gi = 0;
-                    while (gi < keys.size() && keys[gi] != k) ++gi;
-                    if (gi == keys.size()) {
-                        keys.push_back(k);
-                        groups.emplace_back();
-                    }
-                    groups[gi].push_back(o);
+            std::vector<std::string> keys;
+            std::vector<std::vector<const RecOp*>> groups;
+            for (int v = 0; v < count; ++v) {
+                const RecOp* o = &rec[v].ops[i];
+                std::string k = variant_key(*o);
+                size_t gi = 0;
+                while (gi < keys.size() && keys[gi] != k) ++gi;
+                if (gi == keys.size()) {
+                    keys.push_back(k);
+                    groups.emplace_back();
                 }
-                for (auto& grp : groups) {
-                    Pending P;
-                    memset(&P.L, 0, sizeof(P.L));
-                    P.L.kind = grp[0]->kind;
-                    P.L.finalize = fin;
-                    const RecOp* proto = grp[0];
-                    for (const RecOp* o : grp)
-                        if (op_length(*o) > op_length(*proto)) proto = o;
-                    P.L.proto = *proto;
-                    P.L.g.n = (int)grp.size();
-                    std::vector<int> start(grp.size() + 1, 0), nbx(grp.size(), 1);
-                    for (size_t q = 0; q < grp.size(); ++q) {
-                        int nx, tot;
-                        op_tiles(*grp[q], fin, &nx, &tot);
-                        nbx[q] = nx;
-                        start[q + 1] = start[q] + tot;
-                    }
-                    P.L.g.total = start.back();
-                    P.L.g.grid = 0;
-                    blob.resize(align16(blob.size()));
-                    P.off_passes = blob.size();
-                    switch (P.L.kind) {
-                        case OP_R2C: append_payloads<R2CPass>(grp, blob); break;
-                        case OP_C2C: append_payloads<C2CPass>(grp, blob); break;
-                        case OP_MUL: append_payloads<MulPass>(grp, blob); break;
-                        case OP_C2R: append_payloads<C2RPass>(grp, blob); break;
-                        case OP_RENDER: append_payloads<RenderOp>(grp, blob); break;
-                        case OP_GRAD: append_payloads<GradOp>(grp, blob); break;
-                        case OP_LOSSFIN: append_payloads<LossFinOp>(grp, blob); break;
-                        case OP_KEYDECODE: append_payloads<KeyDecodeOp>(grp, blob); break;
-                        default: append_payloads<ZeroOp>(grp, blob); break;
-                    }
-                    blob.resize(align16(blob.size()));
-                    P.off_start = blob.size();
-                    blob.insert(blob.end(), reinterpret_cast<unsigned char*>(start.data()),
-                                reinterpret_cast<unsigned char*>(start.data() + start.size()));
-                    blob.resize(align16(blob.size()));
-                    P.off_nbx = blob.size();
-                    blob.insert(blob.end(), reinterpret_cast<unsigned char*>(nbx.data()),
-                                reinterpret_cast<unsigned char*>(nbx.data() + nbx.size()));
-                    pend.push_back(P);
+                groups[gi].push_back(o);
+            }
+            for (auto& grp : groups) {
+                Pending P;
+                memset(&P.L, 0, sizeof(P.L));
+                P.L.kind = grp[0]->kind;
+                const RecOp* proto = grp[0];
+                for (const RecOp* o : grp)
+                    if (op_length(*o) > op_length(*proto)) proto = o;
+                P.L.proto = *proto;
+                P.L.g.n = (int)grp.size();
+                std::vector<int> start(grp.size() + 1, 0), nbx(grp.size(), 1);
+                for (size_t q = 0; q < grp.size(); ++q) {
+                    int nx, tot;
+                    op_tiles(*grp[q], &nx, &tot);
+                    nbx[q] = nx;
+                    start[q + 1] = start[q] + tot;
                 }
+                P.L.g.total = start.back();
+                P.L.g.grid = 0;
+                blob.resize(align16(blob.size()));
+                P.off_passes = blob.size();
+                switch (P.L.kind) {
+                    case OP_R2C: append_payloads<R2CPass>(grp, blob); break;
+                    case OP_C2C: append_payloads<C2CPass>(grp, blob); break;
+                    case OP_MUL: append_payloads<MulPass>(grp, blob); break;
+                    case OP_C2R: append_payloads<C2RPass>(grp, blob); break;
+                    case OP_RENDER: append_payloads<RenderOp>(grp, blob); break;
+                    case OP_GRAD: append_payloads<GradOp>(grp, blob); break;
+                    default: break;
+                }
+                blob.resize(align16(blob.size()));
+                P.off_start = blob.size();
+                blob.insert(blob.end(), reinterpret_cast<unsigned char*>(start.data()),
+                            reinterpret_cast<unsigned char*>(start.data() + start.size()));
+                blob.resize(align16(blob.size()));
+                P.off_nbx = blob.size();
+                blob.insert(blob.end(), reinterpret_cast<unsigned char*>(nbx.data()),
+                            reinterpret_cast<unsigned char*>(nbx.data() + nbx.size()));
+                pend.push_back(P);
             }
         }
         cudaError_t e = cudaMalloc(&b->blob, blob.size() ? blob.size() : 16);
@@ -1614,7 +1593,7 @@ sfw_status sfw_batch_autotune(sfw_batch* b, const char* cache_path, void* stream
     std::string sig = "sfw-batch-v1";
     for (const BatchLaunch& L : b->launches) {
         char t[64];
-        snprintf(t, sizeof(t), " %d.%d.%d.%d", (int)L.kind, L.finalize, L.g.n, L.g.total);
+        snprintf(t, sizeof(t), " %d.%d.%d", (int)L.kind, L.g.n, L.g.total);
         sig += t;
     }
     if (cache_path) {
@@ -1655,7 +1634,7 @@ sfw_status sfw_batch_autotune(sfw_batch* b, const char* cache_path, void* stream
     sfw_status s = SFW_OK;
     for (BatchLaunch& L : b->launches) {
         const bool tunable = L.kind == OP_R2C || L.kind == OP_C2C || L.kind == OP_MUL || L.kind == OP_C2R ||
-                             L.kind == OP_RENDER || (L.kind == OP_GRAD && !L.finalize);
+                             L.kind == OP_RENDER || L.kind == OP_GRAD;
         if (!tunable || L.g.total <= 1) continue;
         const int resident = L.g.grid;  // default chosen by the first step
         const int cand[6] = {resident, b->num_sms, 2 * b->num_sms, 4 * b->num_sms, 8 * b->num_sms, L.g.total};

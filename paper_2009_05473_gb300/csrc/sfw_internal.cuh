@@ -176,6 +176,15 @@ struct C2RPass {
     unsigned long long* best_key;  // CERTMAX: one key or NULL
     unsigned long long* vox_key;   // CERTMAX: V per-voxel keys (atomicMax) or NULL
     int ktotal;           // CERTMAX: number of spectra; grid.y groups them by nspec
+    // last-tile epilogue (the tile that finishes last reduces and re-arms)
+    int ntiles;           // tiles of this pass (set by the launcher)
+    unsigned int* counter;  // zero between calls
+    double* loss_out;     // RESIDUAL: C = 1/2 sum r^2 + lambda sum w, or NULL
+    const float* w;       //   weights w[i * w_stride], i < nw
+    int nw, w_stride;
+    double lambda;
+    float* best_val;      // CERTMAX: decoded best_key (best_key is reset to 0)
+    int64_t* best_idx;
 };
 
 // A persistent grouped launch: n passes of one kernel variant, their
@@ -223,15 +232,16 @@ struct AtomsDev {
 // f on the box of shape E (dense), E index t <-> grid coordinate t - R.
 sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], float eps, float* f,
                          cudaStream_t st);
-// Per-atom adjoint sums -> gradient (6N doubles) given b on E.
+// Per-atom adjoint sums -> gradient (6N doubles) given b on E.  counters: N
+// unsigned ints, zero between calls (the last chunk-block of an atom finalises it).
 constexpr int kGradChunks = 32;
 sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
                             const float* b, double lambda, double* partials, double* grad,
-                            cudaStream_t st);
+                            unsigned int* counters, cudaStream_t st);
 // eta(theta_p) = <g_p, b>/lambda and its gradient for P parameter rows (m, sigma, d).
 sfw_status launch_eta_points(const AtomsDev& pts, const int E[3], const int R[3], float eps,
                              const float* b, double lambda, double* partials, double* eta,
-                             double* grad, cudaStream_t st);
+                             double* grad, unsigned int* counters, cudaStream_t st);
 // Top-k voxels -> parameter rows (m0, m1, m2, sigma_k, d_k), k = argk of the voxel.
 sfw_status launch_candidate_theta(const int64_t* vox, const int* argk, const float* grid_sd,
                                   int topk, const int n[3], float* theta, cudaStream_t st);
@@ -243,9 +253,6 @@ sfw_status launch_candidate_select(const float* theta, const float* grid_val, co
 sfw_status launch_unit_atom(const AtomsDev& a, int i, float* slot, cudaStream_t st);
 sfw_status launch_gram(const float* A, const float* y, int N, long long V, double* G, double* c,
                        cudaStream_t st);
-// sum_n w_n added to the loss: loss = 0.5 * sum(partials) + lambda * sum w
-sfw_status launch_loss_finalize(const double* partials, int nparts, const AtomsDev& a,
-                                double lambda, double* loss, cudaStream_t st);
 
 // ------------------------------------------------------------------ non-FFT ops as descriptors
 // (one launch each, or grouped over the volumes of a batch)
@@ -256,30 +263,21 @@ struct RenderOp {
     float eps;
     float* f;
 };
+// How the last chunk-block of an atom finalises its six adjoint sums.
+struct AdjFin {
+    int mode;                // 0: gradient of C (6N); 1: eta and d eta / d theta (P x 5 or NULL)
+    double lambda;
+    double* grad;
+    double* eta;
+    unsigned int* counters;  // one per atom, zero between calls
+};
 struct GradOp {
     AtomsDev a;
     int E[3], R[3];
     float eps;
     const float* b;
-    double lambda;
     double* partials;
-    double* grad;
-};
-struct LossFinOp {
-    const double* partials;
-    int nparts;
-    AtomsDev a;
-    double lambda;
-    double* loss;
-};
-struct KeyDecodeOp {
-    const unsigned long long* key;
-    float* val;
-    int64_t* idx;
-};
-struct ZeroOp {
-    void* ptr;
-    long long bytes;  // multiple of 8
+    AdjFin fin;
 };
 
 // Grouped launches of the non-FFT ops (device arrays of n ops).
@@ -287,21 +285,15 @@ sfw_status launch_render_group(const RenderOp* ops, const int* start, const int*
                                int total, int grid, cudaStream_t st);
 sfw_status launch_grad_group(const GradOp* ops, const int* start, const int* nbx, int n, int total,
                              int grid, cudaStream_t st);
-sfw_status launch_grad_finalize_group(const GradOp* ops, const int* start, const int* nbx, int n,
-                                      int total, cudaStream_t st);
-sfw_status launch_lossfin_group(const LossFinOp* ops, int n, cudaStream_t st);
-sfw_status launch_keydecode_group(const KeyDecodeOp* ops, int n, cudaStream_t st);
-sfw_status launch_zero_group(const ZeroOp* ops, int n, cudaStream_t st);
 // tiles of one render / adjoint op
 int render_tiles(const RenderOp& op, int* nbx);
 int grad_tiles(const GradOp& op, int* nbx);
-int grad_finalize_tiles(const GradOp& op, int* nbx);
 
 // ------------------------------------------------------------------ recording (batches)
 // While g_recorder is set on this thread, every launcher appends its op here
 // instead of launching; a batch replays the ops of all its volumes stage by stage.
 enum OpKind {
-    OP_R2C = 0, OP_C2C, OP_MUL, OP_C2R, OP_RENDER, OP_GRAD, OP_LOSSFIN, OP_KEYDECODE, OP_ZERO
+    OP_R2C = 0, OP_C2C, OP_MUL, OP_C2R, OP_RENDER, OP_GRAD
 };
 struct RecOp {
     OpKind kind;
@@ -311,9 +303,6 @@ struct RecOp {
     C2RPass c2r;
     RenderOp render;
     GradOp grad;
-    LossFinOp lossfin;
-    KeyDecodeOp keydec;
-    ZeroOp zero;
 };
 struct Recorder {
     std::vector<RecOp> ops;
@@ -323,9 +312,6 @@ struct Recorder {
     sfw_status add(const C2RPass& p) { RecOp o{}; o.kind = OP_C2R; o.c2r = p; ops.push_back(o); return SFW_OK; }
     sfw_status add(const RenderOp& p) { RecOp o{}; o.kind = OP_RENDER; o.render = p; ops.push_back(o); return SFW_OK; }
     sfw_status add(const GradOp& p) { RecOp o{}; o.kind = OP_GRAD; o.grad = p; ops.push_back(o); return SFW_OK; }
-    sfw_status add(const LossFinOp& p) { RecOp o{}; o.kind = OP_LOSSFIN; o.lossfin = p; ops.push_back(o); return SFW_OK; }
-    sfw_status add(const KeyDecodeOp& p) { RecOp o{}; o.kind = OP_KEYDECODE; o.keydec = p; ops.push_back(o); return SFW_OK; }
-    sfw_status add(const ZeroOp& p) { RecOp o{}; o.kind = OP_ZERO; o.zero = p; ops.push_back(o); return SFW_OK; }
 };
 extern thread_local Recorder* g_recorder;
 
@@ -341,12 +327,24 @@ sfw_status launch_argmax_final(const unsigned long long* partial, int n, float* 
                                cudaStream_t st);
 sfw_status launch_topk(const float* v, long long count, int topk, unsigned long long* scratch,
                        long long scratch_len, float* val_out, int64_t* idx_out, cudaStream_t st);
-sfw_status launch_key_decode(const unsigned long long* key, float* val, int64_t* idx,
-                             cudaStream_t st);
 sfw_status launch_spec_stats(const float2* s, long long count, float* stats /*2 floats*/,
                              cudaStream_t st);
 sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out,
                                cudaStream_t st);
+
+#ifdef __CUDACC__
+// True in every thread of the block that finishes last among `nblocks` blocks
+// sharing `counter` (the block's global writes are made visible first).
+__device__ __forceinline__ bool last_block(unsigned int* counter, int nblocks) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == (unsigned int)(nblocks - 1);
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+#endif
 
 // Monotone map of a float to an unsigned key (NaN handled by callers).
 __host__ __device__ inline unsigned int float_order_key(float v) {
