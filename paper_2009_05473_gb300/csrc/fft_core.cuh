@@ -482,7 +482,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 // Stage spectrum s of the tile (rows j < L of W lines) into shared memory S[j][i].
 // A row whose W values are all present and 16-byte aligned travels as 16-byte
 // cp.async chunks; other rows are copied element by element.
-template <int W, int KIND>
+template <int W, int KIND, int NT = kThreads>
 __device__ __forceinline__ void stage_spec(const MulPass& p, int L, int s, const long long* off_spec,
                                            long long l0, unsigned char* S) {
     constexpr int ES = SpecInfo<KIND>::bytes;
@@ -491,7 +491,7 @@ __device__ __forceinline__ void stage_spec(const MulPass& p, int L, int s, const
     const unsigned char* base = reinterpret_cast<const unsigned char*>(p.spec);
     const long long sbase = (long long)s * p.spec_stride;
     const bool full = l0 + W <= p.nlines && off_spec[W - 1] == off_spec[0] + (W - 1);
-    for (int e = threadIdx.x; e < L * CH; e += kThreads) {
+    for (int e = threadIdx.x; e < L * CH; e += NT) {
         const int j = e / CH, c = e - (e / CH) * CH;
         unsigned char* drow = S + (size_t)j * SW * ES;
         const unsigned char* srow = base + (size_t)(sbase + off_spec[0] + j * p.lspec.Sj) * ES;
@@ -593,6 +593,242 @@ __global__ void __launch_bounds__(kThreads) k_mul_g(const MulPass* __restrict__ 
     }
 }
 
+
+// ------------------------------------------------------------------ register-resident transforms
+//
+// Lengths L = R1 * T with R1, T in {8, 16} (64, 128, 256) run as two Stockham
+// stages held in registers.  T lanes own a line; lane t keeps points t + T m
+// (m < R1).  Stage 1 is one radix-R1 DFT per lane (the points L / R1 = T apart),
+// giving y[t R1 + q]; the lane multiplies them by the stage-2 twiddles
+// w_L^(t q) and writes them to a warp-private exchange row; stage 2 reads
+// y[c + R1 r] (r < T) for its R1 / T butterflies c = t + T h and leaves
+// X[c + R1 r'] = X[t + T (h + (R1 / T) r')].  So a lane ends up holding the
+// points t + T m of the result: the layout its stage 1 reads, which lets a
+// forward spectrum stay in registers across the inverse transforms of a
+// convolution.  The exchange row pads one slot per R1 points and its pitch is
+// 8 (mod 16) float2, so the writes (17 t + q) and the reads (c + 17 r) of the two
+// lines in a half-warp fall in distinct banks.
+
+template <int L>
+struct RegGeom;
+template <> struct RegGeom<64> { static constexpr int R1 = 8, T = 8; };
+template <> struct RegGeom<128> { static constexpr int R1 = 16, T = 8; };
+template <> struct RegGeom<256> { static constexpr int R1 = 16, T = 16; };
+
+template <int L>
+struct RegFFT {
+    static constexpr int R1 = RegGeom<L>::R1;
+    static constexpr int T = RegGeom<L>::T;
+    static constexpr int LPW = 32 / T;                                // lines per warp
+    static constexpr int W = 16;                                      // lines per CTA
+    static constexpr int NW = W / LPW;                                // warps per CTA
+    static constexpr int NT = 32 * NW;                                // threads per CTA
+    static constexpr int XS = ((L + L / R1 + 7) / 16) * 16 + 8;       // exchange pitch
+    static constexpr int TWN = ((T - 1) * R1 + 1) & ~1;               // stage-2 twiddles (even)
+    static constexpr int DEPTH = 3;                                   // spectra in flight per warp
+};
+template <int L>
+__host__ __device__ constexpr bool reg_fft_length() { return L == 64 || L == 128 || L == 256; }
+
+// Stage-2 twiddles w_L^(t q) (t = 1..T-1, q < R1) of the factorisation R1 x T: the
+// last stage of the per-stage table (see twiddle_table), stored transposed at
+// q (T - 1) + t - 1 so that the lanes of a warp read consecutive entries.
+template <int L, int NT>
+__device__ __forceinline__ void reg_twiddles(const float2* __restrict__ tw, float2* TW) {
+    constexpr int R1 = RegGeom<L>::R1, T = RegGeom<L>::T;
+    for (int i = threadIdx.x; i < (T - 1) * R1; i += NT) {
+        const int q = i / (T - 1), tm = i - q * (T - 1);
+        TW[i] = __ldg(tw + (R1 - 1) + tm * R1 + q);
+    }
+}
+
+// In: v[m] = x[t + T m].  Out: v[m] = X[t + T m], X[k] = sum_j x[j] exp(DIR 2 pi i j k / L).
+// TW: stage-2 twiddles (reg_twiddles); xl: this line's exchange row (XS float2), private
+// to the warp.
+template <int L, int DIR>
+__device__ __forceinline__ void reg_fft(float2 (&v)[RegGeom<L>::R1], const float2* __restrict__ TW,
+                                        float2* xl, int t) {
+    constexpr int R1 = RegGeom<L>::R1, T = RegGeom<L>::T;
+    dft<R1, DIR>(v);
+    if (t > 0) {
+        const float2* wt = TW + (t - 1);
+#pragma unroll
+        for (int q = 1; q < R1; ++q) {
+            float2 c = wt[q * (T - 1)];
+            if (DIR > 0) c.y = -c.y;
+            v[q] = cmul(v[q], c);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < R1; ++q) xl[t * (R1 + 1) + q] = v[q];
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < R1 / T; ++h) {
+        float2 u[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) u[r] = xl[(t + T * h) + (R1 + 1) * r];
+        dft<T, DIR>(u);
+#pragma unroll
+        for (int r = 0; r < T; ++r) v[h + (R1 / T) * r] = u[r];
+    }
+    __syncwarp();
+}
+
+// Copy rows [0, L) of spectrum s for the warp's LPW lines into S[j][li] (row pitch
+// LPW * ES bytes).  When the lines are consecutive in the spectrum and every row
+// starts 16-byte aligned (packed), rows travel as 16- or 8-byte cp.async chunks;
+// otherwise element by element (lines >= nvalid read as 0).
+template <int KIND, int L, int LPW>
+__device__ __forceinline__ void stage_spec_warp(const MulPass& p, int s, const long long* offs, int nvalid,
+                                                bool packed, unsigned char* S, int lane) {
+    constexpr int ES = SpecInfo<KIND>::bytes;
+    constexpr int RB = LPW * ES;                    // bytes per row
+    const unsigned char* base = reinterpret_cast<const unsigned char*>(p.spec) + (long long)s * p.spec_stride * ES;
+    const long long rs = p.lspec.Sj * ES;           // bytes between rows
+    if (packed) {
+        constexpr int CB = RB >= 16 ? 16 : RB;      // chunk bytes (RB is 4..32)
+        constexpr int CPR = RB / CB;                // chunks per row
+        const unsigned char* b0 = base + offs[0] * ES;
+        for (int e = lane; e < L * CPR; e += 32) {
+            const int j = e / CPR, c = e - (e / CPR) * CPR;
+            const unsigned char* src = b0 + j * rs + c * CB;
+            const unsigned sd = (unsigned)__cvta_generic_to_shared(S + j * RB + c * CB);
+            if constexpr (CB == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sd), "l"(src));
+            else if constexpr (CB == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sd), "l"(src));
+            else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sd), "l"(src));
+        }
+    } else {
+        for (int e = lane; e < L * LPW; e += 32) {
+            const int j = e / LPW, i = e - (e / LPW) * LPW;
+            unsigned char* dst = S + j * RB + i * ES;
+            const unsigned char* src = base + (offs[i] + (long long)j * p.lspec.Sj) * ES;
+            if constexpr (ES == 8) {
+                if (i < nvalid) cp_async(dst, src, 8);
+                else *reinterpret_cast<float2*>(dst) = make_float2(0.f, 0.f);
+            } else if constexpr (ES == 4) {
+                if (i < nvalid) cp_async(dst, src, 4);
+                else *reinterpret_cast<float*>(dst) = 0.f;
+            } else {
+                *reinterpret_cast<unsigned short*>(dst) =
+                    i < nvalid ? *reinterpret_cast<const unsigned short*>(src) : (unsigned short)0;
+            }
+        }
+    }
+}
+
+// Spectrum multiply on a tile of 16 lines with the forward transform in registers.
+// Each warp runs alone on its LPW lines: one forward transform, then for every
+// spectrum s of the CTA's group, X * S_s, the inverse, and rows
+// [out_off, out_off + out_len) stored straight from registers.  The warp keeps
+// DEPTH spectra in flight in its own shared-memory ring (cp.async, __syncwarp).
+template <int KIND, int LL>
+__device__ __forceinline__ void mul_reg_body(const MulPass& p, int bx, int by) {
+    using G = RegFFT<LL>;
+    constexpr int L = LL, R1 = G::R1, T = G::T, LPW = G::LPW, D = G::DEPTH;
+    constexpr int ES = SpecInfo<KIND>::bytes;
+    constexpr int SB = L * LPW * ES;                 // bytes of one staged spectrum (per warp)
+    extern __shared__ float4 smem_raw[];
+    float2* TW = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* XW = TW + G::TWN + warp * (LPW * G::XS);                       // exchange rows
+    unsigned char* SW0 = reinterpret_cast<unsigned char*>(TW + G::TWN + G::NW * LPW * G::XS) + warp * (D * SB);
+    __shared__ long long offs[G::NW][3][LPW];        // in, out, spec offsets of the warp's lines
+    const long long lw = (long long)bx * G::W + warp * LPW;     // first line of the warp
+    const int nvalid = (int)max(0LL, min((long long)LPW, p.nlines - lw));
+    if (lane < LPW && lane < nvalid) {
+        offs[warp][0][lane] = line_offset(p.lin, lw + lane);
+        offs[warp][1][lane] = line_offset(p.lout, lw + lane);
+        offs[warp][2][lane] = line_offset(p.lspec, lw + lane);
+    }
+    reg_twiddles<L, G::NT>(p.tw, TW);
+    __syncthreads();
+    const int t = lane % T, li = lane / T;
+    float2* xl = XW + li * G::XS;
+    const bool valid = li < nvalid;
+    bool packed = nvalid == LPW;
+    if (packed) {
+        const long long o0 = offs[warp][2][0];
+#pragma unroll
+        for (int i = 1; i < LPW; ++i) packed = packed && offs[warp][2][i] == o0 + i;
+        constexpr int CB = LPW * ES >= 16 ? 16 : LPW * ES;   // chunk size of stage_spec_warp
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(p.spec) + (uintptr_t)(o0 * ES);
+        const long long rs = p.lspec.Sj * ES;
+        const long long ss = p.spec_stride * ES;
+        packed = packed && a0 % CB == 0 && rs % CB == 0 && ss % CB == 0;
+    }
+    const int k0 = (int)by * p.nspec;
+    const int nspec = min(p.nspec, p.ktotal - k0);
+    // prime the ring: spectra k0 .. k0 + D - 2 (one commit group each)
+#pragma unroll
+    for (int q = 0; q < D - 1; ++q) {
+        if (q < nspec) stage_spec_warp<KIND, L, LPW>(p, k0 + q, offs[warp][2], nvalid, packed, SW0 + q * SB, lane);
+        cp_async_commit();
+    }
+    float2 X[R1];
+    {
+        const float2* src = p.in + (valid ? offs[warp][0][li] : 0);
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int jj = t + T * m - p.in_off;
+            X[m] = (valid && jj >= 0 && jj < p.in_len) ? __ldg(src + (long long)jj * p.lin.Sj)
+                                                        : make_float2(0.f, 0.f);
+        }
+    }
+    reg_fft<L, -1>(X, TW, xl, t);
+    float2* dst = p.out + (valid ? offs[warp][1][li] : 0);
+    for (int s = 0; s < nspec; ++s) {
+        // refill the slot freed at s - 1 with spectrum s + D - 1
+        if (s + D - 1 < nspec)
+            stage_spec_warp<KIND, L, LPW>(p, k0 + s + D - 1, offs[warp][2], nvalid, packed,
+                                          SW0 + ((s + D - 1) % D) * SB, lane);
+        cp_async_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1));
+        __syncwarp();
+        const unsigned char* S = SW0 + (s % D) * SB;
+        float2 v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int e = (t + T * m) * LPW + li;
+            if constexpr (KIND == SPEC_R32 || KIND == SPEC_RBF16) {
+                const float h = spec_value<KIND>(S, e).x;
+                v[m] = make_float2(X[m].x * h, X[m].y * h);
+            } else {
+                float2 h = spec_value<KIND>(S, e);
+                if (p.conj_spec) h.y = -h.y;
+                v[m] = cmul(X[m], h);
+            }
+        }
+        reg_fft<L, 1>(v, TW, xl, t);
+        if (valid) {
+            float2* o = dst + (long long)(k0 + s) * p.out_stride;
+#pragma unroll
+            for (int m = 0; m < R1; ++m) {
+                const int j = t + T * m - p.out_off;
+                if (j >= 0 && j < p.out_len) o[(long long)j * p.lout.Sj] = v[m];
+            }
+        }
+        __syncwarp();   // every lane is done with slot s % D before it is refilled
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+template <int KIND, int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_mul_reg(MulPass p) {
+    mul_reg_body<KIND, LL>(p, blockIdx.x, blockIdx.y);
+}
+
+template <int KIND, int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_mul_reg_g(const MulPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        mul_reg_body<KIND, LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
 
 template <int W, int LL>
 __device__ __forceinline__ void r2c_body(const R2CPass& p, int bx, int by) {
@@ -894,22 +1130,22 @@ inline int spec_bytes(int kind) {
 // grouped launch (g: n passes of the same template variant in device memory).
 template <class Single, class Grouped, class PassT>
 inline sfw_status run_either(Single ks, Grouped kg, const char* name, const PassT& p, dim3 grid1,
-                             size_t smem, cudaStream_t st, GroupArgs* g) {
+                             size_t smem, cudaStream_t st, GroupArgs* g, int nt = kThreads) {
     if (!g) {
         SFW_TRY(prepare(ks, smem));
-        SFW_LAUNCH(st, name, ks<<<grid1, kThreads, smem, st>>>(p));
+        SFW_LAUNCH(st, name, ks<<<grid1, nt, smem, st>>>(p));
     } else {
         SFW_TRY(prepare(kg, smem));
         if (g->grid <= 0) {  // resident CTAs, computed once (before any capture)
             int dev = 0, sms = 1, per = 1;
             SFW_CUDA(cudaGetDevice(&dev));
             SFW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kg, kThreads, smem));
+            SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kg, nt, smem));
             if (per < 1) per = 1;
             g->grid = g->total < per * sms ? g->total : per * sms;
         }
         if (g->total <= 0) return SFW_OK;
-        SFW_LAUNCH(st, name, kg<<<g->grid, kThreads, smem, st>>>(
+        SFW_LAUNCH(st, name, kg<<<g->grid, nt, smem, st>>>(
             reinterpret_cast<const PassT*>(g->passes), g->start, g->nbx, g->n));
     }
     return launch_check(name);
@@ -937,8 +1173,21 @@ sfw_status run_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
     pass_tiles(p, &W, &nbx, &nby);
     const int es = spec_bytes(p.spec_kind);
     const size_t sp = ((size_t)p.L * (W + 16 / es) * es + 15) & ~(size_t)15;
-    const size_t smem = tile_bytes(p.L, W, 3) + 2 * sp;
     const dim3 grid1((unsigned)nbx, (unsigned)nby);
+    if constexpr (reg_fft_length<LL>()) {
+        using G = RegFFT<LL>;
+        const size_t smem = sizeof(float2) * ((size_t)G::TWN + (size_t)G::NW * G::LPW * G::XS) +
+                            (size_t)G::NW * G::DEPTH * LL * G::LPW * es;
+#define SFW_MULR(KK) return run_either(k_mul_reg<KK, LL>, k_mul_reg_g<KK, LL>, "k_mul_reg", p, grid1, smem, st, g, G::NT)
+        switch (p.spec_kind) {
+            case SPEC_C64: SFW_MULR(SPEC_C64);
+            case SPEC_R32: SFW_MULR(SPEC_R32);
+            case SPEC_CBF16: SFW_MULR(SPEC_CBF16);
+            default: SFW_MULR(SPEC_RBF16);
+        }
+#undef SFW_MULR
+    }
+    const size_t smem = tile_bytes(p.L, W, 3) + 2 * sp;
 #define SFW_MUL(WW, KK) return run_either(k_mul<WW, KK, LL>, k_mul_g<WW, KK, LL>, "k_mul", p, grid1, smem, st, g)
     switch (p.spec_kind) {
         case SPEC_C64: if (W == 16) SFW_MUL(16, SPEC_C64); else SFW_MUL(8, SPEC_C64);

@@ -63,6 +63,9 @@ int next_smooth_even(int x) {
     }
 }
 
+// Radix of the first stage of the register-resident transforms (0: not one of their lengths).
+static int reg_first_radix(int L) { return L == 64 ? 8 : (L == 128 || L == 256) ? 16 : 0; }
+
 namespace {
 std::mutex g_tw_mu;
 std::map<std::tuple<int, int, int>, float2*> g_tw;  // (device, L, max radix) -> table
@@ -115,6 +118,10 @@ sfw_status twiddle_table(int L, int maxr, const float2** out) {
 // Make the tables of length L for every tile width a pass of that length can
 // use (so that launches, and stream captures, never allocate).
 sfw_status TwiddleCache::get(int L, const float2** out) {
+    if (reg_first_radix(L)) {
+        const float2* t = nullptr;
+        SFW_TRY(twiddle_table(L, reg_first_radix(L), &t));
+    }
     const int ws[2] = {8, 16};
     for (int q = 0; q < 2; ++q) {
         const float2* t = nullptr;
@@ -127,9 +134,10 @@ sfw_status TwiddleCache::get(int L, const float2** out) {
 
 void TwiddleCache::release() { tables.clear(); }
 
-// The factors and twiddles of a pass follow the lines each warp owns (W / 8).
-static sfw_status fit_factors(int L, int W, Factors* fac, const float2** tw) {
-    const int mr = max_radix(L, W / 8);
+// The factors and twiddles of a pass follow the lines each warp owns (W / 8);
+// passes on the register-resident path use the factorisation R1 x T.
+static sfw_status fit_factors(int L, int W, Factors* fac, const float2** tw, bool reg = false) {
+    const int mr = (reg && reg_first_radix(L)) ? reg_first_radix(L) : max_radix(L, W / 8);
     if (!factorize(L, fac, mr)) return fail(SFW_ERR_SHAPE, "cannot factor %d", L);
     return twiddle_table(L, mr, tw);
 }
@@ -154,6 +162,8 @@ bool fft_specialised(int L) {
 
 // Lines per CTA: 16 up to length 256, else 8 (shared memory).
 int tile_width(int L) { return L <= 256 ? 16 : 8; }
+
+int reg_line_group(int L) { return (L == 64 || L == 128) ? 4 : L == 256 ? 2 : 0; }
 
 void pass_tiles(const C2CPass& p, int* W, int* nbx, int* nby) {
     *W = tile_width(p.L);
@@ -202,7 +212,7 @@ sfw_status launch_mul(const MulPass& p0, cudaStream_t st, GroupArgs* g) {
     if (!g) {
         int W, nbx, nby;
         pass_tiles(p, &W, &nbx, &nby);
-        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw, true));
     }
     if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {

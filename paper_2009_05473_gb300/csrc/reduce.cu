@@ -236,20 +236,31 @@ sfw_status launch_spec_stats(const float2* s, long long count, float* stats, cud
     return launch_check("k_spec_stats");
 }
 
-__global__ void k_spec_convert(const float2* s, long long count, int kind, void* out) {
+__global__ void k_spec_convert(const float2* s, long long count, int kind, void* out, int rows,
+                               long long nl, int group) {
+    const long long per = (long long)rows * nl;
+    const long long ng = group > 0 ? (nl + group - 1) / group : 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x) {
         const float2 v = s[i];
-        if (kind == SPEC_R32) reinterpret_cast<float*>(out)[i] = v.x;
-        else if (kind == SPEC_CBF16) reinterpret_cast<__nv_bfloat162*>(out)[i] = __float22bfloat162_rn(v);
-        else if (kind == SPEC_RBF16) reinterpret_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v.x);
-        else reinterpret_cast<float2*>(out)[i] = v;
+        long long o = i;
+        if (group > 0) {
+            const long long k = i / per, rem = i - k * per;
+            const long long j = rem / nl, l = rem - j * nl;
+            o = ((k * ng + l / group) * rows + j) * group + l % group;
+        }
+        if (kind == SPEC_R32) reinterpret_cast<float*>(out)[o] = v.x;
+        else if (kind == SPEC_CBF16) reinterpret_cast<__nv_bfloat162*>(out)[o] = __float22bfloat162_rn(v);
+        else if (kind == SPEC_RBF16) reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v.x);
+        else reinterpret_cast<float2*>(out)[o] = v;
     }
 }
 
-sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out,
-                               cudaStream_t st) {
-    SFW_LAUNCH(st, "k_spec_convert", k_spec_convert<<<1024, 256, 0, st>>>(s, count, kind, out));
+sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out, int rows,
+                               long long nl, int group, cudaStream_t st) {
+    if (rows < 1 || nl < 1 || count % ((long long)rows * nl) != 0)
+        return fail(SFW_ERR_SHAPE, "spec_convert: %lld values are not whole %d x %lld spectra", count, rows, nl);
+    SFW_LAUNCH(st, "k_spec_convert", k_spec_convert<<<1024, 256, 0, st>>>(s, count, kind, out, rows, nl, group));
     return launch_check("k_spec_convert");
 }
 

@@ -477,7 +477,9 @@ struct sfw_plan {
     int Pc[3], H2c;
     Factors facc[3];
     const float2* twc[3];
-    void* table;        // K x Pc0 x Pc1 x H2c spectra
+    void* table;        // K spectra of Pc0 rows x (Pc1 H2c) lines (layout: table_lines)
+    LineSet table_lines;          // line -> offset within a spectrum (rows table_lines.Sj apart)
+    long long table_stride;       // elements between spectra
     int table_kind;
     size_t table_bytes;
     int real_table;
@@ -647,9 +649,27 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
             esz = p->real_table ? 4 : 8;
         }
         p->table_kind = kind;
-        p->table_bytes = esz * (size_t)K * spec_elems;
+        // axis-0 lines of the certificate: Pc1 x H2c per spectrum, Pc0 rows.  For the
+        // register-resident lengths each warp's lines sit together with all their rows.
+        const long long nl = (long long)p->Pc[1] * p->H2c;
+        const int grp = reg_line_group(p->Pc[0]);
+        if (grp > 0) {
+            const long long ng = (nl + grp - 1) / grp;
+            p->table_lines = ls((long long)grp * p->Pc[0], 1, grp, grp);
+            p->table_stride = ng * grp * p->Pc[0];
+        } else {
+            p->table_lines = ls(0, 1, nl, nl);
+            p->table_stride = spec_elems;
+        }
+        p->table_bytes = esz * (size_t)K * (size_t)p->table_stride;
         if ((st_ret = plan_alloc(p, &p->table, p->table_bytes))) break;
-        if ((st_ret = launch_spec_convert(full, (long long)K * spec_elems, kind, p->table, st))) break;
+        if (cudaMemsetAsync(p->table, 0, p->table_bytes, st) != cudaSuccess) {
+            st_ret = cuda_fail(cudaGetLastError(), "table clear");
+            break;
+        }
+        if ((st_ret = launch_spec_convert(full, (long long)K * spec_elems, kind, p->table, p->Pc[0], nl,
+                                          grp, st)))
+            break;
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) st_ret = cuda_fail(e, "table build");
     } while (0);
@@ -1027,8 +1047,8 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
         q.fac = p->facc[0];
         q.tw = p->twc[0];
         q.spec = p->table;
-        q.lspec = ls(0, 1, nl, nl);
-        q.spec_stride = (long long)P0 * nl;
+        q.lspec = p->table_lines;
+        q.spec_stride = p->table_stride;
         q.ktotal = K;
         {   // split the kernels so that the launch holds about 8 CTAs per SM
             const long long tiles = (nl + 15) / 16;

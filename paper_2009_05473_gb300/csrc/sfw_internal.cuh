@@ -201,6 +201,8 @@ struct GroupArgs {
 
 // Tile width W and tile grid (nbx, nby) of a pass (same rule for single and grouped launches).
 int tile_width(int L);
+// Lines per warp of the register-resident transforms of length L (0: other lengths).
+int reg_line_group(int L);
 void pass_tiles(const C2CPass& p, int* W, int* nbx, int* nby);
 void pass_tiles(const MulPass& p, int* W, int* nbx, int* nby);
 void pass_tiles(const R2CPass& p, int* W, int* nbx, int* nby);
@@ -329,8 +331,11 @@ sfw_status launch_topk(const float* v, long long count, int topk, unsigned long 
                        long long scratch_len, float* val_out, int64_t* idx_out, cudaStream_t st);
 sfw_status launch_spec_stats(const float2* s, long long count, float* stats /*2 floats*/,
                              cudaStream_t st);
-sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out,
-                               cudaStream_t st);
+// Spectra (count / (rows * nl) of them, rows x nl lines) converted to `kind`.  group > 0
+// stores them line-group-major: groups of `group` consecutive lines hold all their
+// rows contiguously, [spectrum][line / group][row][line % group] (padding lines 0).
+sfw_status launch_spec_convert(const float2* s, long long count, int kind, void* out, int rows,
+                               long long nl, int group, cudaStream_t st);
 
 #ifdef __CUDACC__
 // True in every thread of the block that finishes last among `nblocks` blocks
