@@ -812,6 +812,67 @@ __device__ __forceinline__ void mul_reg_body(const MulPass& p, int bx, int by) {
     asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
+// Batched complex transform of lines of a register-resident length: each warp
+// loads its LPW lines straight into registers (rows [in_off, in_off + in_len)),
+// transforms them and stores rows [out_off, out_off + out_len) scaled.
+template <int DIR, int LL>
+__device__ __forceinline__ void c2c_reg_body(const C2CPass& p, int bx, int by) {
+    using G = RegFFT<LL>;
+    constexpr int L = LL, R1 = G::R1, T = G::T, LPW = G::LPW;
+    extern __shared__ float4 smem_raw[];
+    float2* TW = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* XW = TW + G::TWN + warp * (LPW * G::XS);
+    __shared__ long long offs[G::NW][2][LPW];
+    const long long lw = (long long)bx * G::W + warp * LPW;
+    const int nvalid = (int)max(0LL, min((long long)LPW, p.nlines - lw));
+    if (lane < nvalid) {
+        offs[warp][0][lane] = line_offset(p.lin, lw + lane);
+        offs[warp][1][lane] = line_offset(p.lout, lw + lane);
+    }
+    reg_twiddles<L, G::NT>(p.tw, TW);
+    __syncthreads();
+    const int t = lane % T, li = lane / T;
+    const bool valid = li < nvalid;
+    float2 v[R1];
+    {
+        const float2* src = p.in + (valid ? offs[warp][0][li] : 0);
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int jj = t + T * m - p.in_off;
+            v[m] = (valid && jj >= 0 && jj < p.in_len) ? __ldg(src + (long long)jj * p.lin.Sj)
+                                                        : make_float2(0.f, 0.f);
+        }
+    }
+    reg_fft<L, DIR>(v, TW, XW + li * G::XS, t);
+    if (valid) {
+        float2* o = p.out + offs[warp][1][li];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int j = t + T * m - p.out_off;
+            if (j >= 0 && j < p.out_len) o[(long long)j * p.lout.Sj] = cscale(v[m], p.scale);
+        }
+    }
+}
+
+template <int DIR, int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_c2c_reg(C2CPass p) {
+    c2c_reg_body<DIR, LL>(p, blockIdx.x, blockIdx.y);
+}
+
+template <int DIR, int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_c2c_reg_g(const C2CPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        c2c_reg_body<DIR, LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
+
 template <int KIND, int LL>
 __global__ void __launch_bounds__(RegFFT<LL>::NT) k_mul_reg(MulPass p) {
     mul_reg_body<KIND, LL>(p, blockIdx.x, blockIdx.y);
@@ -1156,8 +1217,14 @@ sfw_status run_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g) {
     if (!g && p.nlines <= 0) return SFW_OK;
     int W, nbx, nby;
     pass_tiles(p, &W, &nbx, &nby);
-    const size_t smem = tile_bytes(p.L, W, 2);
     const dim3 grid1((unsigned)nbx);
+    if constexpr (reg_fft_length<LL>()) {
+        using G = RegFFT<LL>;
+        const size_t rs = sizeof(float2) * ((size_t)G::TWN + (size_t)G::NW * G::LPW * G::XS);
+        if (p.dir < 0) return run_either(k_c2c_reg<-1, LL>, k_c2c_reg_g<-1, LL>, "k_c2c_reg", p, grid1, rs, st, g, G::NT);
+        return run_either(k_c2c_reg<1, LL>, k_c2c_reg_g<1, LL>, "k_c2c_reg", p, grid1, rs, st, g, G::NT);
+    }
+    const size_t smem = tile_bytes(p.L, W, 2);
     if (W == 16) {
         if (p.dir < 0) return run_either(k_c2c<16, -1, LL>, k_c2c_g<16, -1, LL>, "k_c2c", p, grid1, smem, st, g);
         return run_either(k_c2c<16, 1, LL>, k_c2c_g<16, 1, LL>, "k_c2c", p, grid1, smem, st, g);

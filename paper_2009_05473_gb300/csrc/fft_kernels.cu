@@ -196,7 +196,7 @@ sfw_status launch_c2c(const C2CPass& p0, cudaStream_t st, GroupArgs* g) {
     if (!g) {
         int W, nbx, nby;
         pass_tiles(p, &W, &nbx, &nby);
-        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw, true));
     }
     if (g_recorder && !g) return g_recorder->add(p);
     switch (p.L) {
