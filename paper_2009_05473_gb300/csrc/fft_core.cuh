@@ -1138,6 +1138,167 @@ __device__ __forceinline__ void c2r_body(const C2RPass& p, int bx, int by) {
     }
 }
 
+// Certificate epilogue on the register-resident transform (lengths 64/128/256, rows
+// [0, out_len) kept with out_len <= L / 2).  Each complex line carries the real
+// lines 2 li (real part) and 2 li + 1 (imaginary part); a warp owns LPW complex
+// lines and stages the half spectra of its 2 LPW real lines (pitch HS, 4 mod 8
+// float2 so the two lines a half-warp reads fall in distinct banks), two spectra
+// deep.  Lane t keeps the running max over the CTA's kernels of its outputs
+// t + T m (m < R1 / 2) of both real lines, then publishes them as candidate keys.
+template <int LL>
+struct RegC2R {
+    using G = RegFFT<LL>;
+    static constexpr int H = LL / 2 + 1;
+    static constexpr int HS = ((H + 3) / 8) * 8 + 4;
+    static constexpr int RL = 2 * G::LPW;          // real lines per warp
+    static constexpr int D = 2;                    // staged spectra per warp
+    static constexpr int SB = RL * HS;             // float2 per staged spectrum
+    static size_t smem() {
+        return sizeof(float2) * ((size_t)G::TWN + (size_t)G::NW * G::LPW * G::XS + (size_t)G::NW * D * SB);
+    }
+};
+
+template <int LL>
+__device__ __forceinline__ void c2r_reg_max_body(const C2RPass& p, int bx, int by) {
+    using G = RegFFT<LL>;
+    using C = RegC2R<LL>;
+    constexpr int L = LL, R1 = G::R1, T = G::T, LPW = G::LPW, H = C::H, HS = C::HS, RL = C::RL;
+    constexpr int MH = R1 / 2;                     // kept outputs per lane and real line
+    extern __shared__ float4 smem_raw[];
+    float2* TW = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* XW = TW + G::TWN + warp * (LPW * G::XS);
+    float2* STG = TW + G::TWN + G::NW * LPW * G::XS + warp * (C::D * C::SB);
+    __shared__ long long offs[G::NW][2][RL];
+    const long long lw = ((long long)bx * G::W + warp * LPW) * 2;   // first real line of the warp
+    const int nvalid = (int)max(0LL, min((long long)RL, p.nlines - lw));
+    if (lane < nvalid) {
+        offs[warp][0][lane] = line_offset(p.lin, lw + lane);
+        offs[warp][1][lane] = line_offset(p.lout, lw + lane);
+    }
+    reg_twiddles<L, G::NT>(p.tw, TW);
+    __syncthreads();
+    const int t = lane % T, li = lane / T;
+    float2* xl = XW + li * G::XS;
+    const int k0 = (int)by * p.nspec;
+    const int nspec = min(p.nspec, p.ktotal - k0);
+    auto stage = [&](int s, float2* dst) {
+        const float2* in = p.in + (long long)s * p.in_spec_stride;
+        for (int e = lane; e < RL * H; e += 32) {
+            const int r = e / H, k = e - (e / H) * H;
+            if (r < nvalid) cp_async(dst + r * HS + k, in + offs[warp][0][r] + k, 8);
+            else dst[r * HS + k] = make_float2(0.f, 0.f);
+        }
+    };
+    stage(k0, STG);
+    cp_async_commit();
+    float mx[2][MH];
+    int ak[2][MH];
+#pragma unroll
+    for (int m = 0; m < MH; ++m) {
+        mx[0][m] = mx[1][m] = -INFINITY;
+        ak[0][m] = ak[1][m] = 0;
+    }
+    bool saw_nan = false;
+    const bool v0 = 2 * li < nvalid, v1 = 2 * li + 1 < nvalid;
+    for (int s = 0; s < nspec; ++s) {
+        if (s + 1 < nspec) stage(k0 + s + 1, STG + ((s + 1) & 1) * C::SB);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        const float2* Rs = STG + (s & 1) * C::SB;
+        const float2* ra = Rs + (2 * li) * HS;
+        const float2* rb = ra + HS;
+        float2 v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int j = t + T * m;
+            const bool lo = 2 * j <= L;
+            const int k = lo ? j : L - j;
+            const float2 a = ra[k], b = rb[k];
+            v[m] = lo ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
+        }
+        reg_fft<L, 1>(v, TW, xl, t);
+        const int kk = k0 + s;
+#pragma unroll
+        for (int m = 0; m < MH; ++m) {
+            const int j = t + T * m;
+            if (j < p.out_len) {
+                const float a = v[m].x * p.scale, b = v[m].y * p.scale;
+                if (p.eta_out) {
+                    float* e = p.eta_out + (long long)kk * p.V + j;
+                    if (v0) e[offs[warp][1][2 * li]] = a;
+                    if (v1) e[offs[warp][1][2 * li + 1]] = b;
+                }
+                saw_nan = saw_nan || (v0 && a != a) || (v1 && b != b);
+                if (a > mx[0][m]) {
+                    mx[0][m] = a;
+                    ak[0][m] = kk;
+                }
+                if (b > mx[1][m]) {
+                    mx[1][m] = b;
+                    ak[1][m] = kk;
+                }
+            }
+        }
+        __syncwarp();   // every lane is done with this slot before it is refilled
+    }
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!(h ? v1 : v0)) continue;
+        const long long ob = offs[warp][1][2 * li + h];
+#pragma unroll
+        for (int m = 0; m < MH; ++m) {
+            const int j = t + T * m;
+            if (j < p.out_len && nspec > 0) {
+                const long long o = ob + j;
+                const unsigned long long key = candidate_key(mx[h][m], (unsigned long long)ak[h][m] * p.V + o);
+                if (p.vox_key) atomicMax(p.vox_key + o, key);
+                if (key > best) best = key;
+            }
+        }
+    }
+    if (saw_nan) best = ~0ull;
+    if (p.best_key) {
+        for (int off = 16; off > 0; off >>= 1) {
+            unsigned long long o2 = __shfl_down_sync(0xffffffffu, best, off);
+            if (o2 > best) best = o2;
+        }
+        if (lane == 0 && best) atomicMax(p.best_key, best);
+        __syncthreads();
+        if (last_block(p.counter, p.ntiles) && threadIdx.x == 0) {
+            const unsigned long long k = atomicExch(p.best_key, 0ull);
+            if (k == ~0ull || k == 0ull) {
+                if (p.best_val) *p.best_val = __int_as_float(0x7fc00000);
+                if (p.best_idx) *p.best_idx = -1;
+            } else {
+                if (p.best_val) *p.best_val = float_from_order_key((unsigned int)(k >> 32));
+                if (p.best_idx) *p.best_idx = (int64_t)(0xffffffffu - (unsigned int)(k & 0xffffffffu));
+            }
+            *p.counter = 0u;
+        }
+    }
+}
+
+template <int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_c2r_reg_max(C2RPass p) {
+    c2r_reg_max_body<LL>(p, blockIdx.x, blockIdx.y);
+}
+
+template <int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_c2r_reg_max_g(const C2RPass* __restrict__ ps,
+        const int* __restrict__ start, const int* __restrict__ nbx, int n) {
+    const int total = start[n];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int q = 0;
+        while (start[q + 1] <= t) ++q;
+        const int local = t - start[q];
+        c2r_reg_max_body<LL>(ps[q], local % nbx[q], local / nbx[q]);
+        __syncthreads();
+    }
+}
+
 template <int W, int MODE, int SLOTS, int LL>
 __global__ void __launch_bounds__(kThreads) k_c2r(C2RPass p) {
     c2r_body<W, MODE, SLOTS, LL>(p, blockIdx.x, blockIdx.y);
@@ -1159,6 +1320,13 @@ __global__ void __launch_bounds__(kThreads) k_c2r_g(const C2RPass* __restrict__ 
 
 
 // ------------------------------------------------------------------ launchers
+
+// The certificate epilogue runs on the register-resident transform when the length
+// has one and the kept rows are [0, out_len) with out_len <= L / 2.
+inline bool c2r_on_reg(const C2RPass& p) {
+    return (p.L == 64 || p.L == 128 || p.L == 256) && p.mode == C2R_CERTMAX && p.out_off == 0 &&
+           2 * p.out_len <= p.L;
+}
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel, size):
 // the attribute call is kept out of stream captures after the first use.
@@ -1282,6 +1450,13 @@ sfw_status run_c2r(const C2RPass& p, cudaStream_t st, int* blocks_out, GroupArgs
     pass_tiles(p, &W, &nbx, &nby);
     if (blocks_out) *blocks_out = nbx;
     if (!g && p.nlines <= 0) return SFW_OK;
+    if constexpr (reg_fft_length<LL>()) {
+        if (c2r_on_reg(p)) {
+            const dim3 grid1((unsigned)nbx, (unsigned)nby);
+            return run_either(k_c2r_reg_max<LL>, k_c2r_reg_max_g<LL>, "k_c2r_reg_max", p, grid1,
+                              RegC2R<LL>::smem(), st, g, RegFFT<LL>::NT);
+        }
+    }
     const int need = (2 * (W / 8) * p.out_len + 31) / 32;
     if (p.mode == C2R_CERTMAX && need > kC2RMaxSlots)
         return fail(SFW_ERR_SHAPE, "c2r: %d outputs per line exceed the epilogue tile", p.out_len);

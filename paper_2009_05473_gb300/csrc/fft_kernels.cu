@@ -185,8 +185,9 @@ void pass_tiles(const R2CPass& p, int* W, int* nbx, int* nby) {
 
 // The certificate epilogue keeps 2 (W / 8) * out_len running maxima per warp in
 // registers (SLOTS per lane): its tiles are 8 lines wide; other modes use tile_width.
+// On the register-resident path (c2r_on_reg) a tile is 16 complex = 32 real lines.
 void pass_tiles(const C2RPass& p, int* W, int* nbx, int* nby) {
-    *W = p.mode == C2R_CERTMAX ? 8 : tile_width(p.L);
+    *W = c2r_on_reg(p) ? 16 : p.mode == C2R_CERTMAX ? 8 : tile_width(p.L);
     *nbx = (int)((p.nlines + 2 * *W - 1) / (2 * *W));
     *nby = p.mode == C2R_CERTMAX ? (p.ktotal + p.nspec - 1) / p.nspec : 1;
 }
@@ -244,7 +245,7 @@ sfw_status launch_c2r(const C2RPass& p0, cudaStream_t st, int* blocks_out, Group
     if (!g) {
         int W, nbx, nby;
         pass_tiles(p, &W, &nbx, &nby);
-        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw));
+        SFW_TRY(fit_factors(p.L, W, &p.fac, &p.tw, c2r_on_reg(p)));
         p.ntiles = nbx * nby;
     }
     if (g_recorder && !g) {
