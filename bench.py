@@ -420,7 +420,7 @@ def cpu_baseline(workload):
     return {"value": cands / t, "unit": "candidates/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"one full step of the FP64 oracle on {workload} ({cands} candidates; "
                        f"{t:.1f} s): direct-sum render/adjoint on {oracle.num_threads()} OpenMP "
-                       "threads, numpy FFT (1 thread) for the blur and the grid certificate")}
+                       "threads, scipy.fft on all host threads for the blur and the grid certificate")}
 
 
 def run_reference(args):
