@@ -164,25 +164,20 @@ sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], floa
 
 constexpr int kGradThreads = 256;
 
-__device__ __forceinline__ double block_sum(double v, double* s_red) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int q = 0; q < kGradThreads / 32; ++q) t += s_red[q];
-    return t;
-}
-
-// Warp 0 sums the chunk partials of atom n in a fixed order (lane c takes chunk c).
+// Warp 0 sums the chunk partials of atom n in a fixed order (lane c takes chunks
+// c, c + 32, ...); the six loads of a chunk are issued together.
 __device__ __forceinline__ void warp_chunk_sums(int n, int chunks, const double* partials, double s[6]) {
     const int lane = threadIdx.x & 31;
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = lane; c < chunks; c += 32) {
+        const double* p = partials + ((long long)n * chunks + c) * 6;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] += __ldcg(p + q);
+    }
+#pragma unroll
     for (int q = 0; q < 6; ++q) {
-        double v = 0.0;
-        for (int c = lane; c < chunks; c += 32) v += __ldcg(partials + ((long long)n * chunks + c) * 6 + q);
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        s[q] = v;
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+        s[q] = v[q];
     }
 }
 
@@ -194,7 +189,6 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
                                                int R1, int R2, float log_inv_eps2,
                                                const float* __restrict__ b, double* partials, int n,
                                                int c, int nchunks, const AdjFin& fin) {
-    __shared__ double s_red[kGradThreads / 32];
     const float m0 = a.m[a.ms * n + 0], m1 = a.m[a.ms * n + 1], m2 = a.m[a.ms * n + 2];
     const float sg = a.sigma[a.ps * n], dd = a.d[a.ps * n];
     const float c2 = atom_cut2(sg, dd, log_inv_eps2);
@@ -205,21 +199,22 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
     const int lo0 = max(0, (int)ceilf(m0 + R0 - rmax)), hi0 = min(E0 - 1, (int)floorf(m0 + R0 + rmax));
     const int lo1 = max(0, (int)ceilf(m1 + R1 - rmax)), hi1 = min(E1 - 1, (int)floorf(m1 + R1 + rmax));
     const int lo2 = max(0, (int)ceilf(m2 + R2 - rmax)), hi2 = min(E2 - 1, (int)floorf(m2 + R2 + rmax));
-    const long long n0 = max(0, hi0 - lo0 + 1), n1 = max(0, hi1 - lo1 + 1), n2 = max(0, hi2 - lo2 + 1);
-    const long long nb = n0 * n1 * n2;
+    const int n0 = max(0, hi0 - lo0 + 1), n1 = max(0, hi1 - lo1 + 1);
+    const int nrows = n0 * n1;
 
+    // warps of the atom's chunk-blocks take whole (t0, t1) rows of the box; the lanes
+    // walk the part of a row inside the cut-off sphere along the contiguous axis.  A
+    // warp loads RB rows (up to 64 points each) before evaluating any of them: the
+    // loads of b, not the arithmetic, set the time of a row.
+    constexpr int RB = 4;
+    const int lane = threadIdx.x & 31;
+    const int wpb = kGradThreads / 32;
+    const int wstride = nchunks * wpb;
     float sg_b = 0.f, sm0 = 0.f, sm1 = 0.f, sm2 = 0.f, ss = 0.f, sd = 0.f;
-    for (long long v = (long long)c * kGradThreads + threadIdx.x; v < nb;
-         v += (long long)nchunks * kGradThreads) {
-        const int i2 = (int)(v % n2);
-        const long long r = v / n2;
-        const int i1 = (int)(r % n1);
-        const int i0 = (int)(r / n1);
-        const int t0 = lo0 + i0, t1 = lo1 + i1, t2 = lo2 + i2;
-        const float e0 = m0 - (float)(t0 - R0), e1 = m1 - (float)(t1 - R1), e2 = m2 - (float)(t2 - R2);
-        const float r2 = e0 * e0 + e1 * e1 + e2 * e2;
-        if (r2 > c2) continue;
-        const float bt = b[((long long)t0 * E1 + t1) * E2 + t2];
+    auto point = [&](float e0, float e1, float r01, int t2, float bt) {
+        const float e2 = m2 - (float)(t2 - R2);
+        const float r2 = r01 + e2 * e2;
+        if (r2 > c2) return;
         const float lq = __log2f(r2 * is2);
         const float u = 0.5f * exp2f(hd * lq);
         const float g = exp2f(-kLog2e * u);
@@ -234,11 +229,63 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
             ss += gb * (dd / sg) * u;              // dg/dsigma = g (d/sigma) u
             sd += -gb * u * (0.5f * kLn2 * lq);    // dg/dd = -g u ln(rho/sigma)
         }
+    };
+    for (int row0 = c * wpb + (threadIdx.x >> 5); row0 < nrows; row0 += RB * wstride) {
+        float e0s[RB], e1s[RB], r01s[RB], bv[RB][2];
+        int a2s[RB], b2s[RB];
+        const float* brows[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            const int row = row0 + q * wstride;
+            a2s[q] = 0;
+            b2s[q] = -1;
+            e0s[q] = e1s[q] = r01s[q] = 0.f;
+            brows[q] = b;
+            if (row < nrows) {
+                const int i0 = row / n1, i1 = row - (row / n1) * n1;
+                const int t0 = lo0 + i0, t1 = lo1 + i1;
+                e0s[q] = m0 - (float)(t0 - R0);
+                e1s[q] = m1 - (float)(t1 - R1);
+                r01s[q] = e0s[q] * e0s[q] + e1s[q] * e1s[q];
+                if (r01s[q] <= c2) {
+                    const float h = sqrtf(c2 - r01s[q]);
+                    a2s[q] = max(lo2, (int)ceilf(m2 + R2 - h));
+                    b2s[q] = min(hi2, (int)floorf(m2 + R2 + h));
+                    brows[q] = b + ((long long)t0 * E1 + t1) * E2;
+                }
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int t2 = a2s[q] + 32 * hh + lane;
+                bv[q][hh] = t2 <= b2s[q] ? brows[q][t2] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int t2 = a2s[q] + 32 * hh + lane;
+                if (t2 <= b2s[q]) point(e0s[q], e1s[q], r01s[q], t2, bv[q][hh]);
+            }
+            // rows longer than 64 points (broad atoms)
+            for (int t2 = a2s[q] + 64 + lane; t2 <= b2s[q]; t2 += 32) point(e0s[q], e1s[q], r01s[q], t2, brows[q][t2]);
+        }
     }
-    double out[6] = {sm0, sm1, sm2, ss, sd, sg_b};
+    // warp sums in FP32 (a pairwise tree of 32), the block's warp sums in FP64, one
+    // quantity per thread (the FP64 pipe is narrow on this part)
+    __shared__ double s_part[6][kGradThreads / 32];
+    const float out[6] = {sm0, sm1, sm2, ss, sd, sg_b};
+#pragma unroll
     for (int q = 0; q < 6; ++q) {
-        const double t = block_sum(out[q], s_red);
-        if (threadIdx.x == 0) partials[((long long)n * nchunks + c) * 6 + q] = t;
+        float v = out[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) s_part[q][threadIdx.x >> 5] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double t = 0.0;
+        for (int w = 0; w < kGradThreads / 32; ++w) t += s_part[threadIdx.x][w];
+        partials[((long long)n * nchunks + c) * 6 + threadIdx.x] = t;
     }
     if (!fin.counters || !last_block(fin.counters + n, nchunks)) return;
     if (threadIdx.x < 32) {
@@ -264,7 +311,7 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
     }
 }
 
-__global__ void __launch_bounds__(kGradThreads)
+__global__ void __launch_bounds__(kGradThreads, 3)
 k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2,
             const float* __restrict__ b, double* partials, AdjFin fin) {
     atom_grad_body(a, E0, E1, E2, R0, R1, R2, log_inv_eps2, b, partials, blockIdx.x, blockIdx.y,
@@ -276,7 +323,7 @@ int grad_tiles(const GradOp& op, int* nbx) {
     return op.a.N * kGradChunks;
 }
 
-__global__ void __launch_bounds__(kGradThreads)
+__global__ void __launch_bounds__(kGradThreads, 3)
 k_atom_grad_g(const GradOp* __restrict__ ops, const int* __restrict__ start, const int* __restrict__ nbx,
               int n) {
     const int total = start[n];

@@ -236,7 +236,7 @@ sfw_status launch_render(const AtomsDev& a, const int E[3], const int R[3], floa
                          cudaStream_t st);
 // Per-atom adjoint sums -> gradient (6N doubles) given b on E.  counters: N
 // unsigned ints, zero between calls (the last chunk-block of an atom finalises it).
-constexpr int kGradChunks = 32;
+constexpr int kGradChunks = 32;   // blocks per atom of the adjoint sums
 sfw_status launch_atom_grad(const AtomsDev& a, const int E[3], const int R[3], float eps,
                             const float* b, double lambda, double* partials, double* grad,
                             unsigned int* counters, cudaStream_t st);

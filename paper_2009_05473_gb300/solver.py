@@ -62,9 +62,18 @@ def nonneg_quadratic_min(G: np.ndarray, q: np.ndarray, tol: float = 1e-12,
 
 
 def box_bfgs(fg: Callable[[np.ndarray], Tuple[float, np.ndarray]], x0: np.ndarray,
-             lo: np.ndarray, hi: np.ndarray, gtol: float, max_iter: int = 200) -> Tuple[np.ndarray, float, int]:
-    """Minimise on a box: BFGS on the variables not held at a bound, Armijo line
-    search along the projected path, inverse-Hessian reset when the direction fails."""
+             lo: np.ndarray, hi: np.ndarray, gtol: float, max_iter: int = 200,
+             f_rel_noise: float = 1e-6) -> Tuple[np.ndarray, float, int]:
+    """Minimise on a box: BFGS on the variables not held at a bound, backtracking
+    along the projected path, inverse-Hessian reset when the direction fails.
+
+    A trial step is accepted by the Armijo test or, when the objective changed by
+    less than its rounding level (f_rel_noise |f|: the loss and the certificate are
+    summed from FP32 device values), by the approximate Wolfe condition of Hager and
+    Zhang (SIAM J. Optim. 16, 2005): the slope along the step at the trial point is at
+    most 0.8 of the slope's magnitude at the start.  Near a minimiser the Armijo
+    decrease falls below the FP32 resolution of the loss while the gradient still
+    points the way, so without the second test the search stops early."""
     x = np.minimum(np.maximum(np.asarray(x0, np.float64), lo), hi)
     f, g = fg(x)
     Hi = np.eye(x.size)
@@ -83,8 +92,12 @@ def box_bfgs(fg: Callable[[np.ndarray], Tuple[float, np.ndarray]], x0: np.ndarra
         for _ in range(50):
             xt = np.minimum(np.maximum(x + step * d, lo), hi)
             ft, gt = fg(xt)
-            if np.isfinite(ft) and ft <= f + 1e-4 * float(g @ (xt - x)):
-                break
+            if np.isfinite(ft):
+                gs = float(g @ (xt - x))
+                if ft <= f + 1e-4 * gs:
+                    break
+                if gs < 0.0 and ft <= f + f_rel_noise * abs(f) and float(gt @ (xt - x)) <= -0.8 * gs:
+                    break
             step *= 0.5
         else:
             break
