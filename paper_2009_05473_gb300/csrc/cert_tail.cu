@@ -1,0 +1,233 @@
+// The last two passes of the grid certificate (Eq. 5; Algorithm 1 step 1) fused:
+// for one i0 slab of one kernel k, the inverse transform along axis 1 and the real
+// inverse along axis 2, then the running max / argmax over the CTA's kernels.
+//
+// The slab in[k][i0] (P1 x H2 complex, contiguous) arrives in shared memory by
+// 16-byte cp.async.  Axis 1: each warp transforms 4 columns (register-resident
+// transform, length P1), the columns of a warp 8 apart so that the two columns a
+// half-warp reads sit in distinct banks (the row pitch H2 is 1 mod 16 float2), and
+// writes the kept rows back in place.  Axis 2: complex line c carries real rows c
+// (real part) and c + P1/4 (imaginary part) of the slab; the lanes rebuild the
+// Hermitian extension at the load, transform (length P2), and keep their outputs'
+// running maxima in registers across the kernels.  The slab never returns to HBM,
+// which saves the (K, n0, n1, H2) intermediate of the two-pass form.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "fft_core.cuh"
+
+namespace sfw {
+
+constexpr int kTailThreads = 256;
+constexpr int kTailWarps = kTailThreads / 32;
+
+template <int P1, int P2>
+struct TailGeom {
+    static constexpr int H2 = P2 / 2 + 1;
+    static constexpr int SLAB = P1 * H2;                      // float2
+    static constexpr int XS = RegFFT<P1>::XS > RegFFT<P2>::XS ? RegFFT<P1>::XS : RegFFT<P2>::XS;
+    static constexpr int XL = 4;                              // exchange rows per warp
+    static constexpr int NC = P1 / 4;                         // complex lines of axis 2
+    static constexpr int NT1 = (P2 / 2) / 4 + 1;              // axis-1 tasks (4 columns each)
+    static constexpr int NT2 = NC / RegFFT<P2>::LPW;          // axis-2 tasks
+    static size_t smem() {
+        return sizeof(float2) * ((size_t)SLAB + RegFFT<P1>::TWN + RegFFT<P2>::TWN + (size_t)kTailWarps * XL * XS);
+    }
+};
+
+template <int P1, int P2>
+__global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p) {
+    using G = TailGeom<P1, P2>;
+    static_assert(RegFFT<P1>::T == 8 && RegFFT<P2>::T == 8, "4 lines per warp on both axes");
+    static_assert(G::NT2 <= kTailWarps, "one axis-2 task per warp");
+    constexpr int H2 = G::H2;
+    constexpr int R1a = RegGeom<P1>::R1, R1b = RegGeom<P2>::R1;
+    constexpr int MH = R1b / 2;                 // kept outputs per lane and real row
+    extern __shared__ float4 smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);
+    float2* TW1 = S + G::SLAB;
+    float2* TW2 = TW1 + RegFFT<P1>::TWN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* XW = TW2 + RegFFT<P2>::TWN + warp * (G::XL * G::XS);
+    const int t = lane & 7, li = lane >> 3;
+    float2* xl = XW + li * G::XS;
+    reg_twiddles<P1, kTailThreads>(p.tw1, TW1);
+    reg_twiddles<P2, kTailThreads>(p.tw2, TW2);
+    const int i0 = blockIdx.x;
+    const int k0 = (int)blockIdx.y * p.nspec;
+    const int nk = min(p.nspec, p.ktotal - k0);
+
+    // axis-2 task of this warp: complex line c = warp + (NC / 4) li, rows c and c + NC
+    const bool has2 = warp < G::NT2;
+    const int cA = warp + (G::NC / 4) * li, cB = cA + G::NC;
+    float mx[2][MH];
+    int ak[2][MH];
+#pragma unroll
+    for (int m = 0; m < MH; ++m) {
+        mx[0][m] = mx[1][m] = -INFINITY;
+        ak[0][m] = ak[1][m] = 0;
+    }
+    bool saw_nan = false;
+
+    for (int s = 0; s < nk; ++s) {
+        const int kk = k0 + s;
+        const float2* src = p.in + ((long long)kk * p.n0 + i0) * G::SLAB;
+        for (int e = threadIdx.x; e < G::SLAB / 2; e += kTailThreads) cp_async16(S + 2 * e, src + 2 * e);
+        cp_async_commit();
+        cp_async_wait0();
+        __syncthreads();
+        // axis 1: columns (P2 / 2 of them in groups of 32, then the last one, P2 / 2)
+        for (int task = warp; task < G::NT1; task += kTailWarps) {
+            const int main_tasks = G::NT1 - 1;
+            const int col = task < main_tasks ? (task >> 3) * 32 + (task & 7) + 8 * li : P2 / 2;
+            const bool cv = task < main_tasks || li == 0;
+            float2 v[R1a];
+#pragma unroll
+            for (int m = 0; m < R1a; ++m) v[m] = cv ? S[(t + 8 * m) * H2 + col] : make_float2(0.f, 0.f);
+            reg_fft<P1, 1>(v, TW1, xl, t);
+            if (cv) {
+#pragma unroll
+                for (int m = 0; m < R1a / 2; ++m) S[(t + 8 * m) * H2 + col] = v[m];
+            }
+        }
+        __syncthreads();
+        // axis 2: real inverse of rows cA (real part) and cB (imaginary part)
+        if (has2) {
+            const float2* ra = S + cA * H2;
+            const float2* rb = S + cB * H2;
+            float2 v[R1b];
+#pragma unroll
+            for (int m = 0; m < R1b; ++m) {
+                const int j = t + 8 * m;
+                const bool lo = 2 * j <= P2;
+                const int k = lo ? j : P2 - j;
+                const float2 a = ra[k], b = rb[k];
+                v[m] = lo ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
+            }
+            reg_fft<P2, 1>(v, TW2, xl, t);
+#pragma unroll
+            for (int m = 0; m < MH; ++m) {
+                const int i2 = t + 8 * m;
+                if (i2 < p.n2) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = h ? cB : cA;
+                        if (row < p.n1) {
+                            const float val = (h ? v[m].y : v[m].x) * p.scale;
+                            if (p.eta_out)
+                                p.eta_out[(long long)kk * p.V + ((long long)i0 * p.n1 + row) * p.n2 + i2] = val;
+                            saw_nan = saw_nan || val != val;
+                            if (val > mx[h][m]) {
+                                mx[h][m] = val;
+                                ak[h][m] = kk;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the slab is reloaded for the next kernel
+    }
+
+    unsigned long long best = 0ull;
+    if (has2 && nk > 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int row = h ? cB : cA;
+            if (row >= p.n1) continue;
+#pragma unroll
+            for (int m = 0; m < MH; ++m) {
+                const int i2 = t + 8 * m;
+                if (i2 < p.n2) {
+                    const long long o = ((long long)i0 * p.n1 + row) * p.n2 + i2;
+                    const unsigned long long key = candidate_key(mx[h][m], (unsigned long long)ak[h][m] * p.V + o);
+                    if (p.vox_key) atomicMax(p.vox_key + o, key);
+                    if (key > best) best = key;
+                }
+            }
+        }
+    }
+    if (saw_nan) best = ~0ull;
+    if (p.best_key) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o2 = __shfl_down_sync(0xffffffffu, best, off);
+            if (o2 > best) best = o2;
+        }
+        if (lane == 0 && best) atomicMax(p.best_key, best);
+        __syncthreads();
+        // the last CTA decodes the key and re-arms it (0) for the next call
+        if (last_block(p.counter, p.ntiles) && threadIdx.x == 0) {
+            const unsigned long long k = atomicExch(p.best_key, 0ull);
+            if (k == ~0ull || k == 0ull) {
+                if (p.best_val) *p.best_val = __int_as_float(0x7fc00000);
+                if (p.best_idx) *p.best_idx = -1;
+            } else {
+                if (p.best_val) *p.best_val = float_from_order_key((unsigned int)(k >> 32));
+                if (p.best_idx) *p.best_idx = (int64_t)(0xffffffffu - (unsigned int)(k & 0xffffffffu));
+            }
+            *p.counter = 0u;
+        }
+    }
+}
+
+bool cert_tail_supported(int P1, int P2, int n1, int n2) {
+    return (P1 == 64 || P1 == 128) && (P2 == 64 || P2 == 128) && 2 * n1 <= P1 && 2 * n2 <= P2;
+}
+
+template <int P1, int P2>
+static sfw_status run_tail(CertTailPass p, int groups, cudaStream_t st) {
+    using G = TailGeom<P1, P2>;
+    const size_t smem = G::smem();
+    SFW_TRY(prepare(k_cert_tail<P1, P2>, smem));
+    int dev = 0;
+    SFW_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int>, int> chosen;  // (dev, P1, P2, n0, K) -> groups
+    const auto key = std::make_tuple(dev, P1, P2, p.n0, p.ktotal);
+    if (groups <= 0) {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = chosen.find(key);
+        if (it != chosen.end()) groups = it->second;
+    }
+    if (groups <= 0) {
+        // kernels per CTA: the fewest rounds of resident CTAs, then the most kernels per CTA
+        int sms = 1, per = 1;
+        SFW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cert_tail<P1, P2>, kTailThreads, smem));
+        const long long slots = (long long)(per > 0 ? per : 1) * sms;
+        long long best_cost = -1;
+        for (int ns = 1; ns <= p.ktotal; ++ns) {
+            const long long g = (p.ktotal + ns - 1) / ns;
+            const long long rounds = (p.n0 * g + slots - 1) / slots;
+            const long long cost = rounds * ns;
+            if (best_cost < 0 || cost <= best_cost) {
+                best_cost = cost;
+                groups = (int)g;
+            }
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        chosen[key] = groups;
+    }
+    p.nspec = (p.ktotal + groups - 1) / groups;
+    groups = (p.ktotal + p.nspec - 1) / p.nspec;
+    p.ntiles = p.n0 * groups;
+    const dim3 grid((unsigned)p.n0, (unsigned)groups);
+    SFW_LAUNCH(st, "k_cert_tail", (k_cert_tail<P1, P2><<<grid, kTailThreads, smem, st>>>(p)));
+    return launch_check("k_cert_tail");
+}
+
+sfw_status launch_cert_tail(const CertTailPass& p0, int groups, cudaStream_t st) {
+    CertTailPass p = p0;
+    if (!cert_tail_supported(p.P1, p.P2, p.n1, p.n2) || p.H2 != p.P2 / 2 + 1)
+        return fail(SFW_ERR_SHAPE, "fused certificate tail: unsupported lengths %d x %d", p.P1, p.P2);
+    if (p.n0 < 1 || p.ktotal < 1) return SFW_OK;
+    SFW_TRY(twiddle_table(p.P1, p.P1 == 64 ? 8 : 16, &p.tw1));
+    SFW_TRY(twiddle_table(p.P2, p.P2 == 64 ? 8 : 16, &p.tw2));
+    if (p.P1 == 64 && p.P2 == 64) return run_tail<64, 64>(p, groups, st);
+    if (p.P1 == 64) return run_tail<64, 128>(p, groups, st);
+    if (p.P2 == 64) return run_tail<128, 64>(p, groups, st);
+    return run_tail<128, 128>(p, groups, st);
+}
+
+}  // namespace sfw

@@ -154,6 +154,7 @@ struct PassTags {
 static const PassTags kBlurTags = {"blur_r2c", "blur_c2c_fwd", "blur_axis0", "blur_c2c_inv", "blur_c2r"};
 static const PassTags kBackTags = {"bp_r2c", "bp_c2c_fwd", "bp_axis0", "bp_c2c_inv", "bp_c2r"};
 static const PassTags kTableTags = {"table_r2c", "table_c2c_fwd", "table_axis0", "table_c2c_inv", "table_c2r"};
+static const char* const kCertTailTag = "cert_tail";
 static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max"};
 
 static LineSet ls(long long Sa, long long Sb, long long Sj, long long B) {
@@ -1069,67 +1070,91 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
             SFW_TRY(launch_mul(q, st));
         }
     }
-    {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
-        C2CPass q;
-        q.in = p->cC;
-        q.out = p->cA;
-        q.lin = ls((long long)P1 * H2, 1, H2, H2);
-        q.lout = ls((long long)n1 * H2, 1, H2, H2);
-        q.nlines = (long long)K * n0 * H2;
-        q.L = P1;
-        q.in_off = 0;
-        q.in_len = P1;
-        q.out_off = 0;
-        q.out_len = n1;
-        q.dir = 1;
-        q.scale = 1.f;
-        q.fac = p->facc[1];
-        q.tw = p->twc[1];
-        {
-            LaunchTag lt__(kCertTags.inv1);
-            SFW_TRY(launch_c2c(q, st));
-        }
-    }
     const bool want_vox = max_out || argk_out;
     if (want_vox) {
         if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the argmax-only certificate");
         cudaError_t e = cudaMemsetAsync(p->vox_key, 0, sizeof(unsigned long long) * (size_t)p->V, st);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
     }
-    C2RPass q;
-    memset(&q, 0, sizeof(q));
-    q.in = p->cA;
-    q.lin = ls((long long)n1 * H2, H2, 1, n1);
-    q.nlines = (long long)n0 * n1;
-    q.in_spec_stride = (long long)n0 * n1 * H2;
-    q.ktotal = K;
-    q.L = P2;
-    q.fac = p->facc[2];
-    q.tw = p->twc[2];
-    q.out_off = 0;
-    q.out_len = n2;
-    q.lout = ls((long long)n1 * n2, n2, 1, n1);
-    q.scale = (float)(1.0 / lambda);
-    q.mode = C2R_CERTMAX;
-    q.eta_out = eta_out;
-    q.V = p->V;
-    q.vox_key = want_vox ? p->vox_key : nullptr;
-    q.best_key = (best_val || best_idx) ? p->best_key : nullptr;
-    q.best_val = best_val;
-    q.best_idx = best_idx;
-    q.counter = p->ctr + 1;
-    // split the kernels into groups so that the launch fills the GPU (about 3 CTAs per SM)
-    q.nspec = K;
-    {
-        const int tiles = c2r_blocks(q);
-        int groups = (8 * p->num_sms + tiles - 1) / tiles;
-        if (groups < 1) groups = 1;
-        if (groups > K) groups = K;
-        q.nspec = (K + groups - 1) / groups;
-    }
-    {
-        LaunchTag lt__(kCertTags.c2r);
-        SFW_TRY(launch_c2r(q, st, nullptr));
+    if (cert_tail_supported(P1, P2, n1, n2) && !g_recorder) {
+        // axis-1 inverse, real axis-2 inverse and the max over k in one pass per i0 slab
+        CertTailPass t;
+        memset(&t, 0, sizeof(t));
+        t.in = p->cC;
+        t.n0 = n0;
+        t.n1 = n1;
+        t.n2 = n2;
+        t.P1 = P1;
+        t.P2 = P2;
+        t.H2 = H2;
+        t.ktotal = K;
+        t.scale = (float)(1.0 / lambda);
+        t.eta_out = eta_out;
+        t.V = p->V;
+        t.vox_key = want_vox ? p->vox_key : nullptr;
+        t.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+        t.best_val = best_val;
+        t.best_idx = best_idx;
+        t.counter = p->ctr + 1;
+        LaunchTag lt__(kCertTailTag);
+        SFW_TRY(launch_cert_tail(t, 0, st));
+    } else {
+        {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
+            C2CPass q;
+            q.in = p->cC;
+            q.out = p->cA;
+            q.lin = ls((long long)P1 * H2, 1, H2, H2);
+            q.lout = ls((long long)n1 * H2, 1, H2, H2);
+            q.nlines = (long long)K * n0 * H2;
+            q.L = P1;
+            q.in_off = 0;
+            q.in_len = P1;
+            q.out_off = 0;
+            q.out_len = n1;
+            q.dir = 1;
+            q.scale = 1.f;
+            q.fac = p->facc[1];
+            q.tw = p->twc[1];
+            {
+                LaunchTag lt__(kCertTags.inv1);
+                SFW_TRY(launch_c2c(q, st));
+            }
+        }
+        C2RPass q;
+        memset(&q, 0, sizeof(q));
+        q.in = p->cA;
+        q.lin = ls((long long)n1 * H2, H2, 1, n1);
+        q.nlines = (long long)n0 * n1;
+        q.in_spec_stride = (long long)n0 * n1 * H2;
+        q.ktotal = K;
+        q.L = P2;
+        q.fac = p->facc[2];
+        q.tw = p->twc[2];
+        q.out_off = 0;
+        q.out_len = n2;
+        q.lout = ls((long long)n1 * n2, n2, 1, n1);
+        q.scale = (float)(1.0 / lambda);
+        q.mode = C2R_CERTMAX;
+        q.eta_out = eta_out;
+        q.V = p->V;
+        q.vox_key = want_vox ? p->vox_key : nullptr;
+        q.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+        q.best_val = best_val;
+        q.best_idx = best_idx;
+        q.counter = p->ctr + 1;
+        // split the kernels into groups so that the launch fills the GPU (about 3 CTAs per SM)
+        q.nspec = K;
+        {
+            const int tiles = c2r_blocks(q);
+            int groups = (8 * p->num_sms + tiles - 1) / tiles;
+            if (groups < 1) groups = 1;
+            if (groups > K) groups = K;
+            q.nspec = (K + groups - 1) / groups;
+        }
+        {
+            LaunchTag lt__(kCertTags.c2r);
+            SFW_TRY(launch_c2r(q, st, nullptr));
+        }
     }
     if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
     return SFW_OK;

@@ -187,6 +187,30 @@ struct C2RPass {
     int64_t* best_idx;
 };
 
+// Certificate tail fused in one pass (lengths P1 in {64, 128}, P2 in {64, 128, 256}):
+// per (i0, kernel group) CTA and kernel k, the slab in[k][i0] (P1 x H2 complex,
+// contiguous) -> inverse along axis 1 (keep n1 rows) -> real inverse along axis 2
+// (keep n2) -> running max / argmax over the group, candidate keys as in C2RPass.
+struct CertTailPass {
+    const float2* in;           // (K, n0, P1, H2) complex
+    int n0, n1, n2, P1, P2, H2;
+    int ktotal, nspec;          // kernels; kernels per CTA (grid.y = groups)
+    const float2* tw1;          // twiddles of P1 (register factorisation)
+    const float2* tw2;          // twiddles of P2
+    float scale;                // 1 / lambda
+    float* eta_out;             // K x V or NULL
+    long long V;
+    unsigned long long* best_key;
+    unsigned long long* vox_key;
+    int ntiles;
+    unsigned int* counter;
+    float* best_val;
+    int64_t* best_idx;
+};
+// True when the fused tail handles these lengths (shared memory holds one slab).
+bool cert_tail_supported(int P1, int P2, int n1, int n2);
+sfw_status launch_cert_tail(const CertTailPass& p, int groups, cudaStream_t st);
+
 // A persistent grouped launch: n passes of one kernel variant, their
 // descriptors and tile prefix sums in device memory.  Pass q owns tiles
 // [start[q], start[q+1]); tile t of it maps to (t % nbx[q], t / nbx[q]).
