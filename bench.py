@@ -217,15 +217,15 @@ def run_ours(args):
 
     bufs = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
             "grad": torch.empty(6 * vol.N, dtype=torch.float64, device=dev),
-            "residual": torch.empty(vol.n, dtype=torch.float32, device=dev)}
-    cbufs = {"max": torch.empty(vol.n, dtype=torch.float32, device=dev),
-             "argk": torch.empty(vol.n, dtype=torch.int32, device=dev),
-             "best_val": torch.empty(1, dtype=torch.float32, device=dev),
-             "best_idx": torch.empty(1, dtype=torch.int64, device=dev)}
+            "residual": torch.empty(vol.n, dtype=torch.float32, device=dev),
+            "best_val": torch.empty(1, dtype=torch.float32, device=dev),
+            "best_idx": torch.empty(1, dtype=torch.int64, device=dev)}
+    # one SFW iteration's device work (sfw_step): residual + loss, then the back-projection
+    # and adjoint on this stream while the grid certificate runs on the auxiliary one
+    aux = torch.cuda.Stream(device=dev)
 
     def step():
-        plan.slide_loss_grad(y, est, lam, want_residual=True, out=bufs)
-        plan.certificate(bufs["residual"], lam, want_max=False, out=cbufs)
+        plan.step(y, est, lam, aux_stream=aux, out=bufs)
 
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -325,12 +325,11 @@ def run_ours(args):
         y_dev.copy_(y_host, non_blocking=True)
         for k in ("m", "sigma", "d", "w"):
             getattr(a_dev, k).copy_(p_host[k], non_blocking=True)
-        loss, grad, r = plan.slide_loss_grad(y_dev, a_dev, lam, want_residual=True, out=bufs)
-        c = plan.certificate(r, lam, want_max=False, out=cbufs)
-        out_host["loss"].copy_(loss, non_blocking=True)
-        out_host["grad"].copy_(grad, non_blocking=True)
-        out_host["best_val"].copy_(c["best_val"], non_blocking=True)
-        out_host["best_idx"].copy_(c["best_idx"], non_blocking=True)
+        o = plan.step(y_dev, a_dev, lam, aux_stream=aux, out=bufs)
+        out_host["loss"].copy_(o["loss"], non_blocking=True)
+        out_host["grad"].copy_(o["grad"], non_blocking=True)
+        out_host["best_val"].copy_(o["best_val"], non_blocking=True)
+        out_host["best_idx"].copy_(o["best_idx"], non_blocking=True)
         torch.cuda.synchronize()
         if i >= 3:
             e2e_t += time.perf_counter() - t0

@@ -220,6 +220,30 @@ sfw_status sfw_slide_loss_grad(sfw_plan* plan, const float* y, const sfw_atoms* 
                                double lambda, double* loss_out, double* grad_out,
                                float* residual_out, void* stream);
 
+/* One SFW iteration's data-parallel work in one call: the sliding loss and
+ * gradient of sfw_slide_loss_grad (Eq. 4; step 4 of Algorithm 1) and the grid
+ * certificate maximum of sfw_certificate_grid (Eq. 5; step 1 of Algorithm 1)
+ * for the same residual, so step 1 of the next iteration needs no extra pass.
+ *   y, atoms, lambda (> 0), loss_out, grad_out (or NULL), residual_out (or
+ *   NULL)  as for sfw_slide_loss_grad
+ *   best_val, best_idx  device 1 float / 1 int64 or NULL: as for
+ *             sfw_certificate_grid (max over k and voxels of eta_k, its flat
+ *             index k V + lin(m); NaN / -1 if a NaN occurred)
+ *   stream    the call's stream: it orders the call after earlier work and
+ *             later work after the whole call
+ *   aux_stream  another stream on the same device, or NULL.  Given, the
+ *             certificate runs on it once the residual is ready (an event
+ *             recorded on stream) while the back-projection and the adjoint
+ *             sums continue on stream; stream then waits for aux_stream (a
+ *             second event).  Both events belong to the plan: overlapping
+ *             sfw_step calls on one plan are the caller's race.  Works under
+ *             stream capture (the fork becomes a branch of the graph).
+ * Results equal those of the two separate calls.  SFW_ERR_ARG on bad
+ * arguments or a plan without certificate grid. */
+sfw_status sfw_step(sfw_plan* plan, const float* y, const sfw_atoms* atoms, double lambda,
+                    double* loss_out, double* grad_out, float* residual_out, float* best_val,
+                    int64_t* best_idx, void* stream, void* aux_stream);
+
 /* Per-launch timing.  sfw_profile_start records a CUDA event pair on the
  * launching stream around each of the next max_launches kernels this library
  * launches (any thread) whose tag equals only_tag (host string; NULL = every

@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_topk,  # noqa: F401
                    sfw_eta_points, sfw_forward, sfw_gram,
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
-                   sfw_slide_loss_grad, sfw_version)
+                   sfw_slide_loss_grad, sfw_step, sfw_version)
 
 __all__ = ["Plan", "AtomSet", "Batch", "argmax", "launch_count", "SfwError", "build_library"]
 
@@ -214,6 +214,30 @@ class Plan:
         sfw_slide_loss_grad(self.handle, _ptr(y), atoms.abi(), lam, _ptr(loss), _ptr(grad),
                             _ptr(r) if want_residual else 0, _stream_ptr(stream))
         return loss, grad, (r if want_residual else None)
+
+    def step(self, y, atoms: AtomSet, lam: float, aux_stream=None, stream=None, out=None,
+             want_grad: bool = True):
+        """One SFW iteration's device work (libsfw ``sfw_step``): the sliding loss, its
+        gradient and the residual, and the grid certificate maximum of that residual.  With
+        ``aux_stream`` (a torch.cuda.Stream) the certificate overlaps the back-projection.
+        Returns dict(loss, grad, residual, best_val, best_idx)."""
+        torch = _torch()
+        out = {} if out is None else out
+        if out.get("loss") is None:
+            out["loss"] = torch.empty(1, dtype=torch.float64, device="cuda")
+        if want_grad and (out.get("grad") is None or out["grad"].numel() != 6 * atoms.N):
+            out["grad"] = torch.empty(6 * atoms.N, dtype=torch.float64, device="cuda")
+        if out.get("residual") is None:
+            out["residual"] = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        if out.get("best_val") is None:
+            out["best_val"] = torch.empty(1, dtype=torch.float32, device="cuda")
+        if out.get("best_idx") is None:
+            out["best_idx"] = torch.empty(1, dtype=torch.int64, device="cuda")
+        sfw_step(self.handle, _ptr(y), atoms.abi(), lam, _ptr(out["loss"]),
+                 _ptr(out["grad"]) if want_grad else 0, _ptr(out["residual"]), _ptr(out["best_val"]),
+                 _ptr(out["best_idx"]), _stream_ptr(stream),
+                 int(aux_stream.cuda_stream) if aux_stream is not None else 0)
+        return out
 
 
 class Batch:

@@ -514,6 +514,7 @@ struct sfw_plan {
     int gram_cap;                 // atoms gram_cols can hold
     float* unit_slot;             // one atom (m0, m1, m2, sigma, d, w = 1)
     int num_sms;
+    cudaEvent_t ev_fork, ev_join;  // sfw_step: residual ready / certificate done
     unsigned long long* red_scratch;
     long long red_scratch_len;
     size_t ws_bytes;
@@ -543,6 +544,9 @@ static sfw_status plan_alloc_t(sfw_plan* p, T** ptr, size_t count) {
 
 static void plan_free(sfw_plan* p) {
     if (!p) return;
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    p->ev_fork = p->ev_join = nullptr;
     if (p->gram_cols) cudaFree(p->gram_cols);
     p->gram_cols = nullptr;
     for (void* q : p->allocations) cudaFree(q);
@@ -889,6 +893,11 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         }
         p->red_scratch_len = 1 << 20;
         if ((s = plan_alloc_t(p, &p->red_scratch, (size_t)p->red_scratch_len))) break;
+        if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            s = cuda_fail(cudaGetLastError(), "plan events");
+            break;
+        }
         if (K > 0) {
             const size_t a_el = (size_t)K * p->n[0] * p->n[1] * p->H2c;
             const size_t b_el = (size_t)p->n[0] * p->Pc[1] * p->H2c;
@@ -953,17 +962,10 @@ sfw_status sfw_forward(sfw_plan* p, const sfw_atoms* atoms, float* y_out, void* 
     return blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, nullptr);
 }
 
-sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
-                               double* loss_out, double* grad_out, float* residual_out,
-                               void* stream) {
-    clear_error();
-    if (!p || !y || !loss_out) return fail(SFW_ERR_ARG, "plan, y, loss_out must be non-NULL");
-    SFW_TRY(check_atoms(atoms, true));
-    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and >= 0");
-    if (atoms->N > p->grad_parts_atoms) return fail(SFW_ERR_ARG, "too many atoms");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+// Rendering, blur, residual r = y - Phi mu and the criterion C (Eq. 4), on st.
+static sfw_status residual_and_loss(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                                    double* loss_out, float* r, cudaStream_t st) {
     AtomsDev a = to_dev(atoms);
-    float* r = residual_out ? residual_out : p->r;
     SFW_TRY(launch_render(a, p->E, p->R, p->eps, p->fE, st));
     C2RPass ep;
     memset(&ep, 0, sizeof(ep));
@@ -981,20 +983,87 @@ sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* ato
     int blocks = 0;
     SFW_TRY(blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, &blocks));
     if (blocks > p->loss_parts_len) return fail(SFW_ERR_SHAPE, "loss partial buffer too small");
-    if (!grad_out) return SFW_OK;  // loss only
+    return SFW_OK;
+}
+
+// Back-projection b = Phi^T r and the analytic gradient of C (Eq. 4), on st.
+static sfw_status loss_gradient(sfw_plan* p, const sfw_atoms* atoms, double lambda, const float* r,
+                                double* grad_out, cudaStream_t st) {
+    AtomsDev a = to_dev(atoms);
     SFW_TRY(blur_transpose(p->blur, r, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
     return launch_atom_grad(a, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, grad_out,
                             p->adj_ctr, st);
+}
+
+static sfw_status slide_args(const sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                             const double* loss_out) {
+    if (!p || !y || !loss_out) return fail(SFW_ERR_ARG, "plan, y, loss_out must be non-NULL");
+    SFW_TRY(check_atoms(atoms, true));
+    if (!(lambda >= 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and >= 0");
+    if (atoms->N > p->grad_parts_atoms) return fail(SFW_ERR_ARG, "too many atoms");
+    return SFW_OK;
+}
+
+sfw_status sfw_slide_loss_grad(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                               double* loss_out, double* grad_out, float* residual_out,
+                               void* stream) {
+    clear_error();
+    SFW_TRY(slide_args(p, y, atoms, lambda, loss_out));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* r = residual_out ? residual_out : p->r;
+    SFW_TRY(residual_and_loss(p, y, atoms, lambda, loss_out, r, st));
+    if (!grad_out) return SFW_OK;  // loss only
+    return loss_gradient(p, atoms, lambda, r, grad_out, st);
+}
+
+static sfw_status certificate_impl(sfw_plan* p, const float* residual, double lambda, float* eta_out,
+                                   float* max_out, int32_t* argk_out, float* best_val,
+                                   int64_t* best_idx, cudaStream_t st);
+
+static sfw_status certificate_args(const sfw_plan* p, const float* residual, double lambda) {
+    if (!p || !residual) return fail(SFW_ERR_ARG, "plan and residual must be non-NULL");
+    if (p->K == 0) return fail(SFW_ERR_ARG, "plan has no certificate grid");
+    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
+    return SFW_OK;
+}
+
+sfw_status sfw_step(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                    double* loss_out, double* grad_out, float* residual_out, float* best_val,
+                    int64_t* best_idx, void* stream, void* aux_stream) {
+    clear_error();
+    SFW_TRY(slide_args(p, y, atoms, lambda, loss_out));
+    if (!p->K) return fail(SFW_ERR_ARG, "plan has no certificate grid");
+    if (!(lambda > 0.0)) return fail(SFW_ERR_ARG, "lambda must be > 0 for the certificate");
+    if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the single calls");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t aux = aux_stream ? static_cast<cudaStream_t>(aux_stream) : st;
+    float* r = residual_out ? residual_out : p->r;
+    SFW_TRY(residual_and_loss(p, y, atoms, lambda, loss_out, r, st));
+    if (aux != st) {
+        SFW_CUDA(cudaEventRecord(p->ev_fork, st));
+        SFW_CUDA(cudaStreamWaitEvent(aux, p->ev_fork, 0));
+    }
+    SFW_TRY(certificate_impl(p, r, lambda, nullptr, nullptr, nullptr, best_val, best_idx, aux));
+    if (grad_out) SFW_TRY(loss_gradient(p, atoms, lambda, r, grad_out, st));
+    if (aux != st) {
+        SFW_CUDA(cudaEventRecord(p->ev_join, aux));
+        SFW_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
+    }
+    return SFW_OK;
 }
 
 sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambda, float* eta_out,
                                 float* max_out, int32_t* argk_out, float* best_val,
                                 int64_t* best_idx, void* stream) {
     clear_error();
-    if (!p || !residual) return fail(SFW_ERR_ARG, "plan and residual must be non-NULL");
-    if (p->K == 0) return fail(SFW_ERR_ARG, "plan has no certificate grid");
-    if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SFW_TRY(certificate_args(p, residual, lambda));
+    return certificate_impl(p, residual, lambda, eta_out, max_out, argk_out, best_val, best_idx,
+                            static_cast<cudaStream_t>(stream));
+}
+
+static sfw_status certificate_impl(sfw_plan* p, const float* residual, double lambda, float* eta_out,
+                                   float* max_out, int32_t* argk_out, float* best_val,
+                                   int64_t* best_idx, cudaStream_t st) {
     const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
     const int P0 = p->Pc[0], P1 = p->Pc[1], P2 = p->Pc[2], H2 = p->H2c;
     const int K = p->K;

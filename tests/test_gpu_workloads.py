@@ -198,3 +198,48 @@ def test_vol128_bf16_certificate_and_fp32_rescore(sfw, oracle_mod):
     # the FP32 table seeds the same candidate directly
     out = p32.certificate(rd, lam, want_max=False)
     assert int(out["best_idx"].item()) == i_ref
+
+
+@pytest.mark.parametrize("which", ["vol32", "vol64"])
+def test_step_equals_separate_calls(sfw, oracle_mod, vol64, which):
+    """sfw_step (one SFW iteration's device work, certificate on an auxiliary stream) gives
+    bit-identical loss, gradient, residual and grid argmax to sfw_slide_loss_grad followed
+    by sfw_certificate_grid; also without the auxiliary stream and replayed from a CUDA graph
+    that captured the fork."""
+    import torch
+    if which == "vol64":
+        vol, y, lam, plan, (m, s, d, w), yd = vol64
+    else:
+        vol = sfw_inputs.vol32_iso_n3()
+        y = _f32(oracle_mod.observe(vol, fft=True))
+        lam = oracle_mod.lambda_rule(vol.n, vol.R, vol.psf, y, vol.grid_kernels(), fft=True)
+        plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+        m, s, d, w = (_f32(a) for a in _estimate(vol))
+        yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    atoms = sfw.AtomSet.from_numpy(m, s, d, w)
+    loss, grad, res = plan.slide_loss_grad(yd, atoms, lam, want_residual=True)
+    cert = plan.certificate(res, lam, want_max=False)
+    ref = {"loss": loss.clone(), "grad": grad.clone(), "residual": res.clone(),
+           "best_val": cert["best_val"].clone(), "best_idx": cert["best_idx"].clone()}
+
+    def same(out):
+        for k, v in ref.items():
+            assert torch.equal(out[k], v), k
+
+    aux = torch.cuda.Stream()
+    same(plan.step(yd, atoms, lam, aux_stream=aux))
+    same(plan.step(yd, atoms, lam))
+    # captured: the fork onto the auxiliary stream becomes a branch of the graph
+    out = plan.step(yd, atoms, lam, aux_stream=aux)
+    torch.cuda.synchronize()
+    for v in out.values():
+        v.zero_()
+    cap = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            plan.step(yd, atoms, lam, aux_stream=aux, out=out)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    same(out)
