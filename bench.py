@@ -136,6 +136,7 @@ def algorithmic_bytes(tag: str, plan, vol) -> float:
         "cert_c2c_inv": K * n0 * Pc[1] * H2c * c8 + K * n0 * n1 * H2c * c8,
         "cert_c2r_max": K * n0 * n1 * H2c * c8 + V * 8,
         "cert_tail": K * n0 * Pc[1] * H2c * c8,
+        "cert_head": V * 4 + n0 * Pc[1] * H2c * c8,
         "blur_r2c": VE * 4 + E[0] * E[1] * H2 * c8,
         "blur_c2c_fwd": E[0] * E[1] * H2 * c8 + E[0] * P[1] * H2 * c8,
         "blur_axis0": E[0] * P[1] * H2 * c8 + P[0] * P[1] * H2 * c8 + n0 * P[1] * H2 * c8,

@@ -1,16 +1,17 @@
-// The last two passes of the grid certificate (Eq. 5; Algorithm 1 step 1) fused:
-// for one i0 slab of one kernel k, the inverse transform along axis 1 and the real
-// inverse along axis 2, then the running max / argmax over the CTA's kernels.
+// The grid certificate's passes along axes 1 and 2 (Eq. 5; Algorithm 1 step 1) done
+// per i0 slab, one CTA per slab, so the slab stays in shared memory between the two
+// axes: the head (forward: real transform of the residual's rows along axis 2, then
+// the columns along axis 1) and the tail (per kernel k: the columns' inverse along
+// axis 1, the rows' real inverse along axis 2, and the running max / argmax over the
+// CTA's kernels).
 //
-// The slab in[k][i0] (P1 x H2 complex, contiguous) arrives in shared memory by
-// 16-byte cp.async.  Axis 1: each warp transforms 4 columns (register-resident
-// transform, length P1), the columns of a warp 8 apart so that the two columns a
-// half-warp reads sit in distinct banks (the row pitch H2 is 1 mod 16 float2), and
-// writes the kept rows back in place.  Axis 2: complex line c carries real rows c
-// (real part) and c + P1/4 (imaginary part) of the slab; the lanes rebuild the
-// Hermitian extension at the load, transform (length P2), and keep their outputs'
-// running maxima in registers across the kernels.  The slab never returns to HBM,
-// which saves the (K, n0, n1, H2) intermediate of the two-pass form.
+// Both use the register-resident transform (lengths 64 / 128).  Columns: each warp
+// transforms 4 columns 8 apart, so that the two columns a half-warp reads sit in
+// distinct banks (the complex row pitch H2 is 1 mod 16 float2).  Rows: complex line c
+// carries real rows c (real part) and c + rows/2 (imaginary part).  The tail's slab
+// in[k][i0] (P1 x H2 complex, contiguous) arrives by 16-byte cp.async; the head's
+// result leaves by one bulk copy from shared to global memory.  Neither intermediate
+// of the per-axis form, (n0, n1, H2) or (K, n0, n1, H2), is written.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -169,6 +170,127 @@ __global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p) {
             *p.counter = 0u;
         }
     }
+}
+
+// 18 warps: the 17 column tasks (P2 = 128) of the head run in one round.
+constexpr int kHeadWarps = 18;
+constexpr int kHeadThreads = 32 * kHeadWarps;
+
+template <int P1, int P2>
+struct HeadGeom {
+    static constexpr int RSN = (P1 / 2) * (P2 / 2 + 1);        // real slab bound (floats)
+    static size_t smem() {
+        using G = TailGeom<P1, P2>;
+        return sizeof(float2) * ((size_t)G::SLAB + RegFFT<P1>::TWN + RegFFT<P2>::TWN +
+                                 (size_t)kHeadWarps * G::XL * G::XS) + sizeof(float) * (size_t)RSN;
+    }
+};
+
+template <int P1, int P2>
+__global__ void __launch_bounds__(kHeadThreads) k_cert_head(CertHeadPass p) {
+    using G = TailGeom<P1, P2>;
+    static_assert(RegFFT<P1>::T == 8 && RegFFT<P2>::T == 8, "4 lines per warp on both axes");
+    constexpr int H2 = G::H2;
+    constexpr int R1a = RegGeom<P1>::R1, R1b = RegGeom<P2>::R1;
+    constexpr int NCH = P1 / 4;                  // complex lines of axis 2 (rows c, c + NCH)
+    extern __shared__ float4 smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);
+    float2* TW1 = S + G::SLAB;
+    float2* TW2 = TW1 + RegFFT<P1>::TWN;
+    float2* XW0 = TW2 + RegFFT<P2>::TWN;
+    float* RS = reinterpret_cast<float*>(XW0 + kHeadWarps * G::XL * G::XS);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = lane & 7, li = lane >> 3;
+    float2* xl = XW0 + warp * (G::XL * G::XS) + li * G::XS;
+    const int i0 = blockIdx.x;
+    const int n1 = p.n1, n2 = p.n2;
+    const int NP = n2 | 1;                       // odd row pitch of the real slab
+    {
+        const float* src = p.r + (long long)i0 * n1 * n2;
+        for (int e = threadIdx.x; e < n1 * n2; e += kHeadThreads) {
+            const int i1 = e / n2;
+            RS[i1 * NP + (e - i1 * n2)] = __ldg(src + e);
+        }
+    }
+    reg_twiddles<P1, kHeadThreads>(p.tw1, TW1);
+    reg_twiddles<P2, kHeadThreads>(p.tw2, TW2);
+    __syncthreads();
+    // axis 2: rows c and c + NCH as one complex line, forward, then split the two spectra
+    if (warp < NCH / 4) {
+        const int ra = warp + (NCH / 4) * li, rb = ra + NCH;
+        float2 v[R1b];
+#pragma unroll
+        for (int m = 0; m < R1b; ++m) {
+            const int j = t + 8 * m;
+            const float a = (ra < n1 && j < n2) ? RS[ra * NP + j] : 0.f;
+            const float b = (rb < n1 && j < n2) ? RS[rb * NP + j] : 0.f;
+            v[m] = make_float2(a, b);
+        }
+        reg_fft<P2, -1>(v, TW2, xl, t);
+#pragma unroll
+        for (int m = 0; m < R1b; ++m) xl[t + 8 * m] = v[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < (H2 + 7) / 8; ++m) {
+            const int k = t + 8 * m;
+            if (k < H2) {
+                const float2 z = xl[k], zm = xl[(P2 - k) & (P2 - 1)];
+                S[ra * H2 + k] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+                S[rb * H2 + k] = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // axis 1: columns, rows [0, n1) zero-padded to P1, all P1 outputs in place
+    for (int task = warp; task < G::NT1; task += kHeadWarps) {
+        const int main_tasks = G::NT1 - 1;
+        const int col = task < main_tasks ? (task >> 3) * 32 + (task & 7) + 8 * li : P2 / 2;
+        const bool cv = task < main_tasks || li == 0;
+        float2 v[R1a];
+#pragma unroll
+        for (int m = 0; m < R1a; ++m)
+            v[m] = (cv && t + 8 * m < n1) ? S[(t + 8 * m) * H2 + col] : make_float2(0.f, 0.f);
+        reg_fft<P1, -1>(v, TW1, xl, t);
+        if (cv) {
+#pragma unroll
+            for (int m = 0; m < R1a; ++m) S[(t + 8 * m) * H2 + col] = v[m];
+        }
+    }
+    // the slab leaves in one bulk copy (shared -> global), issued once its writes are
+    // visible to the copy engine
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2* dst = p.out + (long long)i0 * G::SLAB;
+        const unsigned src = (unsigned)__cvta_generic_to_shared(S);
+        const unsigned bytes = (unsigned)(sizeof(float2) * G::SLAB);
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+                     :: "l"(dst), "r"(src), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+    }
+}
+
+template <int P1, int P2>
+static sfw_status run_head(const CertHeadPass& p, cudaStream_t st) {
+    const size_t smem = HeadGeom<P1, P2>::smem();
+    SFW_TRY(prepare(k_cert_head<P1, P2>, smem));
+    SFW_LAUNCH(st, "k_cert_head", (k_cert_head<P1, P2><<<p.n0, kHeadThreads, smem, st>>>(p)));
+    return launch_check("k_cert_head");
+}
+
+sfw_status launch_cert_head(const CertHeadPass& p0, cudaStream_t st) {
+    CertHeadPass p = p0;
+    if (!cert_tail_supported(p.P1, p.P2, p.n1, p.n2) || p.H2 != p.P2 / 2 + 1)
+        return fail(SFW_ERR_SHAPE, "fused certificate head: unsupported lengths %d x %d", p.P1, p.P2);
+    if (p.n0 < 1) return SFW_OK;
+    SFW_TRY(twiddle_table(p.P1, p.P1 == 64 ? 8 : 16, &p.tw1));
+    SFW_TRY(twiddle_table(p.P2, p.P2 == 64 ? 8 : 16, &p.tw2));
+    if (p.P1 == 64 && p.P2 == 64) return run_head<64, 64>(p, st);
+    if (p.P1 == 64) return run_head<64, 128>(p, st);
+    if (p.P2 == 64) return run_head<128, 64>(p, st);
+    return run_head<128, 128>(p, st);
 }
 
 bool cert_tail_supported(int P1, int P2, int n1, int n2) {

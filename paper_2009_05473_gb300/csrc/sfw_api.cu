@@ -154,6 +154,7 @@ struct PassTags {
 static const PassTags kBlurTags = {"blur_r2c", "blur_c2c_fwd", "blur_axis0", "blur_c2c_inv", "blur_c2r"};
 static const PassTags kBackTags = {"bp_r2c", "bp_c2c_fwd", "bp_axis0", "bp_c2c_inv", "bp_c2r"};
 static const PassTags kTableTags = {"table_r2c", "table_c2c_fwd", "table_axis0", "table_c2c_inv", "table_c2r"};
+static const char* const kCertHeadTag = "cert_head";
 static const char* const kCertTailTag = "cert_tail";
 static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max"};
 
@@ -1067,42 +1068,59 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
     const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
     const int P0 = p->Pc[0], P1 = p->Pc[1], P2 = p->Pc[2], H2 = p->H2c;
     const int K = p->K;
-    {   // axis 2 forward of r: (n0, n1, n2) -> (n0, n1, H2)
-        R2CPass q;
-        q.in = residual;
-        q.lin = ls((long long)n1 * n2, n2, 1, n1);
-        q.nlines = (long long)n0 * n1;
-        q.in_off = 0;
-        q.in_len = n2;
-        q.L = P2;
-        q.fac = p->facc[2];
-        q.tw = p->twc[2];
-        q.out = p->cA;
-        q.lout = ls((long long)n1 * H2, H2, 1, n1);
-        {
-            LaunchTag lt__(kCertTags.r2c);
-            SFW_TRY(launch_r2c(q, st));
+    const bool slabs = cert_tail_supported(P1, P2, n1, n2) && !g_recorder;
+    if (slabs) {
+        // axis-2 real forward and axis-1 forward in one pass per i0 slab -> cB
+        CertHeadPass h;
+        memset(&h, 0, sizeof(h));
+        h.r = residual;
+        h.out = p->cB;
+        h.n0 = n0;
+        h.n1 = n1;
+        h.n2 = n2;
+        h.P1 = P1;
+        h.P2 = P2;
+        h.H2 = H2;
+        LaunchTag lt__(kCertHeadTag);
+        SFW_TRY(launch_cert_head(h, st));
+    } else {
+        {   // axis 2 forward of r: (n0, n1, n2) -> (n0, n1, H2)
+            R2CPass q;
+            q.in = residual;
+            q.lin = ls((long long)n1 * n2, n2, 1, n1);
+            q.nlines = (long long)n0 * n1;
+            q.in_off = 0;
+            q.in_len = n2;
+            q.L = P2;
+            q.fac = p->facc[2];
+            q.tw = p->twc[2];
+            q.out = p->cA;
+            q.lout = ls((long long)n1 * H2, H2, 1, n1);
+            {
+                LaunchTag lt__(kCertTags.r2c);
+                SFW_TRY(launch_r2c(q, st));
+            }
         }
-    }
-    {   // axis 1 forward: -> (n0, P1, H2)
-        C2CPass q;
-        q.in = p->cA;
-        q.out = p->cB;
-        q.lin = ls((long long)n1 * H2, 1, H2, H2);
-        q.lout = ls((long long)P1 * H2, 1, H2, H2);
-        q.nlines = (long long)n0 * H2;
-        q.L = P1;
-        q.in_off = 0;
-        q.in_len = n1;
-        q.out_off = 0;
-        q.out_len = P1;
-        q.dir = -1;
-        q.scale = 1.f;
-        q.fac = p->facc[1];
-        q.tw = p->twc[1];
-        {
-            LaunchTag lt__(kCertTags.fwd1);
-            SFW_TRY(launch_c2c(q, st));
+        {   // axis 1 forward: -> (n0, P1, H2)
+            C2CPass q;
+            q.in = p->cA;
+            q.out = p->cB;
+            q.lin = ls((long long)n1 * H2, 1, H2, H2);
+            q.lout = ls((long long)P1 * H2, 1, H2, H2);
+            q.nlines = (long long)n0 * H2;
+            q.L = P1;
+            q.in_off = 0;
+            q.in_len = n1;
+            q.out_off = 0;
+            q.out_len = P1;
+            q.dir = -1;
+            q.scale = 1.f;
+            q.fac = p->facc[1];
+            q.tw = p->twc[1];
+            {
+                LaunchTag lt__(kCertTags.fwd1);
+                SFW_TRY(launch_c2c(q, st));
+            }
         }
     }
     {   // axis 0: forward once, then for each kernel k: times table_k, inverse -> (K, n0, P1, H2)
@@ -1145,7 +1163,7 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
         cudaError_t e = cudaMemsetAsync(p->vox_key, 0, sizeof(unsigned long long) * (size_t)p->V, st);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
     }
-    if (cert_tail_supported(P1, P2, n1, n2) && !g_recorder) {
+    if (slabs) {
         // axis-1 inverse, real axis-2 inverse and the max over k in one pass per i0 slab
         CertTailPass t;
         memset(&t, 0, sizeof(t));

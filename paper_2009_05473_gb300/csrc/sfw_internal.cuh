@@ -211,6 +211,19 @@ struct CertTailPass {
 bool cert_tail_supported(int P1, int P2, int n1, int n2);
 sfw_status launch_cert_tail(const CertTailPass& p, int groups, cudaStream_t st);
 
+// Certificate head fused in one pass (same lengths as the tail): per i0 slab, the real
+// forward transform of the residual rows along axis 2 (zero-padded n2 -> P2) and the
+// forward transform of the columns along axis 1 (n1 -> P1): r (n0, n1, n2) -> out
+// (n0, P1, H2) complex.
+struct CertHeadPass {
+    const float* r;
+    float2* out;
+    int n0, n1, n2, P1, P2, H2;
+    const float2* tw1;
+    const float2* tw2;
+};
+sfw_status launch_cert_head(const CertHeadPass& p, cudaStream_t st);
+
 // A persistent grouped launch: n passes of one kernel variant, their
 // descriptors and tile prefix sums in device memory.  Pass q owns tiles
 // [start[q], start[q+1]); tile t of it maps to (t % nbx[q], t / nbx[q]).
