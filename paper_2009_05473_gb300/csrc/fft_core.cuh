@@ -1028,6 +1028,15 @@ __device__ __forceinline__ void c2r_body(const C2RPass& p, int bx, int by) {
     const int k0 = (MODE == C2R_CERTMAX) ? (int)by * p.nspec : 0;
     const int nspec = (MODE == C2R_CERTMAX) ? min(p.nspec, p.ktotal - k0) : 1;
     stage_half<W>(p, L, k0, off_in, l0, R0, HS);
+    // residual: the tile's observation rows travel with the spectrum, into the second
+    // staging buffer (one spectrum per CTA in this mode; 2W out_len floats fit in it)
+    float* Ys = reinterpret_cast<float*>(R1);
+    if constexpr (MODE == C2R_RESIDUAL) {
+        for (int e = threadIdx.x; e < 2 * W * p.out_len; e += kThreads) {
+            const int q = e / p.out_len, j = e - (e / p.out_len) * p.out_len;
+            if (l0 + q < p.nlines) cp_async(Ys + e, p.y + off_out[q] + j, 4);
+        }
+    }
     cp_async_commit();
     for (int s = 0; s < nspec; ++s) {
         if (s + 1 < nspec) stage_half<W>(p, L, k0 + s + 1, off_in, l0, (s & 1) ? R0 : R1, HS);
@@ -1047,7 +1056,7 @@ __device__ __forceinline__ void c2r_body(const C2RPass& p, int bx, int by) {
                 if constexpr (MODE == C2R_STORE) {
                     p.out[o] = v;
                 } else {
-                    const float r = p.y[o] - v;
+                    const float r = Ys[q * p.out_len + j] - v;
                     if (p.out) p.out[o] = r;
                     acc += (double)r * (double)r;
                 }
