@@ -243,3 +243,29 @@ def test_step_equals_separate_calls(sfw, oracle_mod, vol64, which):
         g.replay()
     torch.cuda.synchronize()
     same(out)
+
+
+@pytest.mark.parametrize("n", [(16, 61, 32), (10, 32, 62)])
+def test_certificate_slabs_ragged(sfw, oracle_mod, n):
+    """The slab head/tail kernels on shapes whose certificate grid is 128 x 64 and 64 x 128 on
+    axes (1, 2), with n1 = 61 or n2 = 62 below half the transform length (zero-padded rows and
+    columns, partially kept outputs): every eta_k(m) against the oracle's Fourier-domain grid
+    certificate (pinned to the direct definition on the CPU) and the grid argmax."""
+    import torch
+    vol = sfw_inputs.make_volume("slab", n, (2, 3, 3), (1.0, 1.2, 1.6), 3, seed=11, min_sep=3.0,
+                                 grid_sigmas=(1.0, 2.0), grid_ds=(2.0,))
+    y = _f32(oracle_mod.observe(vol, fft=True))
+    kernels = vol.grid_kernels()
+    lam = oracle_mod.lambda_rule(vol.n, vol.R, vol.psf, y, kernels, fft=True)
+    plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+    P = plan.info["P_cert"]
+    assert P[1] in (64, 128) and P[2] in (64, 128) and P[1] != P[2]
+    m, s, d, w = (_f32(a) for a in _estimate(vol))
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    _, _, res = plan.slide_loss_grad(yd, sfw.AtomSet.from_numpy(m, s, d, w), lam, want_residual=True)
+    r32 = res.cpu().numpy().astype(np.float64)
+    out = plan.certificate(res, lam, want_eta=True)
+    eta = out["eta"].cpu().numpy()
+    ref = oracle_mod.eta_grid_fft(vol.n, vol.R, vol.psf, r32, lam, kernels)
+    assert _rel_inf(eta, ref) <= 1e-5
+    assert int(out["best_idx"].item()) == int(np.argmax(ref))
