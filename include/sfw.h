@@ -239,7 +239,14 @@ sfw_status sfw_slide_loss_grad(sfw_plan* plan, const float* y, const sfw_atoms* 
  *             sfw_step calls on one plan are the caller's race.  Works under
  *             stream capture (the fork becomes a branch of the graph).
  * Results equal those of the two separate calls.  SFW_ERR_ARG on bad
- * arguments or a plan without certificate grid. */
+ * arguments or a plan without certificate grid.
+ * Graph: when a call has the same pointers, N and lambda as the call before
+ * it (data may change in place), the call captures the step into a CUDA graph
+ * of the plan (on two streams the plan owns; capturing runs nothing) and
+ * launches it on stream; later identical calls only launch the graph.  A call
+ * with other arguments drops the graph (after a device synchronisation).
+ * Calls made while stream is being captured by the caller, and calls while a
+ * profile is recorded, launch their kernels directly. */
 sfw_status sfw_step(sfw_plan* plan, const float* y, const sfw_atoms* atoms, double lambda,
                     double* loss_out, double* grad_out, float* residual_out, float* best_val,
                     int64_t* best_idx, void* stream, void* aux_stream);

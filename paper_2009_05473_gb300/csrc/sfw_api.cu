@@ -82,6 +82,8 @@ LaunchTag::~LaunchTag() { t_tag = prev; }
 
 // Events are recorded with cudaEventRecordExternal so that, inside a stream
 // capture, they become event-record nodes of the graph and time every replay.
+bool prof_active() { return g_prof_on.load(std::memory_order_relaxed); }
+
 void prof_begin(cudaStream_t st, const char* name) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -516,6 +518,21 @@ struct sfw_plan {
     float* unit_slot;             // one atom (m0, m1, m2, sigma, d, w = 1)
     int num_sms;
     cudaEvent_t ev_fork, ev_join;  // sfw_step: residual ready / certificate done
+    cudaStream_t cap_own, aux_own; // sfw_step captures its graph on these (origin, branch)
+    // sfw_step's own CUDA graph: captured at the second consecutive call with the same
+    // arguments, replayed while they stay the same
+    struct StepKey {
+        const void* ptr[10];
+        int N;
+        double lambda;
+        bool operator==(const StepKey& o) const {
+            for (int i = 0; i < 10; ++i)
+                if (ptr[i] != o.ptr[i]) return false;
+            return N == o.N && lambda == o.lambda;
+        }
+    } step_key;
+    bool step_seen;
+    cudaGraphExec_t step_exec;
     unsigned long long* red_scratch;
     long long red_scratch_len;
     size_t ws_bytes;
@@ -545,6 +562,11 @@ static sfw_status plan_alloc_t(sfw_plan* p, T** ptr, size_t count) {
 
 static void plan_free(sfw_plan* p) {
     if (!p) return;
+    if (p->step_exec) cudaGraphExecDestroy(p->step_exec);
+    p->step_exec = nullptr;
+    if (p->aux_own) cudaStreamDestroy(p->aux_own);
+    if (p->cap_own) cudaStreamDestroy(p->cap_own);
+    p->aux_own = p->cap_own = nullptr;
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     p->ev_fork = p->ev_join = nullptr;
@@ -895,7 +917,9 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         p->red_scratch_len = 1 << 20;
         if ((s = plan_alloc_t(p, &p->red_scratch, (size_t)p->red_scratch_len))) break;
         if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&p->aux_own, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&p->cap_own, cudaStreamNonBlocking) != cudaSuccess) {
             s = cuda_fail(cudaGetLastError(), "plan events");
             break;
         }
@@ -1028,17 +1052,9 @@ static sfw_status certificate_args(const sfw_plan* p, const float* residual, dou
     return SFW_OK;
 }
 
-sfw_status sfw_step(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
-                    double* loss_out, double* grad_out, float* residual_out, float* best_val,
-                    int64_t* best_idx, void* stream, void* aux_stream) {
-    clear_error();
-    SFW_TRY(slide_args(p, y, atoms, lambda, loss_out));
-    if (!p->K) return fail(SFW_ERR_ARG, "plan has no certificate grid");
-    if (!(lambda > 0.0)) return fail(SFW_ERR_ARG, "lambda must be > 0 for the certificate");
-    if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the single calls");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaStream_t aux = aux_stream ? static_cast<cudaStream_t>(aux_stream) : st;
-    float* r = residual_out ? residual_out : p->r;
+static sfw_status step_body(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                            double* loss_out, double* grad_out, float* r, float* best_val,
+                            int64_t* best_idx, cudaStream_t st, cudaStream_t aux) {
     SFW_TRY(residual_and_loss(p, y, atoms, lambda, loss_out, r, st));
     if (aux != st) {
         SFW_CUDA(cudaEventRecord(p->ev_fork, st));
@@ -1051,6 +1067,72 @@ sfw_status sfw_step(sfw_plan* p, const float* y, const sfw_atoms* atoms, double 
         SFW_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
     }
     return SFW_OK;
+}
+
+sfw_status sfw_step(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                    double* loss_out, double* grad_out, float* residual_out, float* best_val,
+                    int64_t* best_idx, void* stream, void* aux_stream) {
+    clear_error();
+    SFW_TRY(slide_args(p, y, atoms, lambda, loss_out));
+    if (!p->K) return fail(SFW_ERR_ARG, "plan has no certificate grid");
+    if (!(lambda > 0.0)) return fail(SFW_ERR_ARG, "lambda must be > 0 for the certificate");
+    if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the single calls");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t aux = aux_stream ? static_cast<cudaStream_t>(aux_stream) : st;
+    float* r = residual_out ? residual_out : p->r;
+
+    sfw_plan::StepKey key;
+    const void* ptrs[10] = {y, atoms->m, atoms->sigma, atoms->d, atoms->w, loss_out, grad_out, r,
+                            best_val, best_idx};
+    for (int i = 0; i < 10; ++i) key.ptr[i] = ptrs[i];
+    key.N = atoms->N;
+    key.lambda = lambda;
+    // under a caller's capture or the profiler's events: launch directly and leave the
+    // cached graph alone
+    bool graphable = !prof_active();
+    if (graphable) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            graphable = false;
+        } else {
+            graphable = cs == cudaStreamCaptureStatusNone;
+        }
+    }
+    if (!graphable) return step_body(p, y, atoms, lambda, loss_out, grad_out, r, best_val, best_idx, st, aux);
+    const bool same = p->step_seen && key == p->step_key;
+    if (same && p->step_exec) {
+        SFW_CUDA(cudaGraphLaunch(p->step_exec, st));
+        return SFW_OK;
+    }
+    if (same) {
+        // second identical call in a row: capture the step on the plan's streams (capturing
+        // runs nothing), then launch the graph on the caller's stream
+        SFW_CUDA(cudaStreamBeginCapture(p->cap_own, cudaStreamCaptureModeThreadLocal));
+        const sfw_status sb = step_body(p, y, atoms, lambda, loss_out, grad_out, r, best_val, best_idx,
+                                        p->cap_own, p->aux_own);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(p->cap_own, &g);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t ei = cudaErrorUnknown;
+        if (sb == SFW_OK && ec == cudaSuccess && g) ei = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (sb != SFW_OK) return sb;
+        if (ec != cudaSuccess) return cuda_fail(ec, "sfw_step capture");
+        if (ei != cudaSuccess) return cuda_fail(ei, "sfw_step graph instantiate");
+        p->step_exec = ex;
+        SFW_CUDA(cudaGraphLaunch(p->step_exec, st));
+        return SFW_OK;
+    }
+    if (p->step_exec) {
+        // the arguments changed: the cached graph is dropped once its launches are done
+        SFW_CUDA(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(p->step_exec);
+        p->step_exec = nullptr;
+    }
+    p->step_key = key;
+    p->step_seen = true;
+    return step_body(p, y, atoms, lambda, loss_out, grad_out, r, best_val, best_idx, st, aux);
 }
 
 sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambda, float* eta_out,

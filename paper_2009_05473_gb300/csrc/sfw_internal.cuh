@@ -38,6 +38,7 @@ inline void counted_launch() { g_launches.fetch_add(1, std::memory_order_relaxed
 // launching stream around every kernel, aggregated per tag.  The tag is the
 // innermost active LaunchTag of this thread, else the kernel's own name.
 void prof_begin(cudaStream_t st, const char* name);
+bool prof_active();  // a profile is being recorded
 void prof_end(cudaStream_t st);
 struct LaunchTag {
     const char* prev;

@@ -229,6 +229,31 @@ def test_step_equals_separate_calls(sfw, oracle_mod, vol64, which):
     aux = torch.cuda.Stream()
     same(plan.step(yd, atoms, lam, aux_stream=aux))
     same(plan.step(yd, atoms, lam))
+    # repeated identical calls on a non-default stream: eager, then captured into the plan's
+    # graph, then replayed
+    main = torch.cuda.Stream()
+    main.wait_stream(torch.cuda.current_stream())
+    buf = {}
+    with torch.cuda.stream(main):
+        for _ in range(4):
+            o = plan.step(yd, atoms, lam, aux_stream=aux, out=buf)
+    torch.cuda.current_stream().wait_stream(main)
+    same(o)
+    # the graph reads the atoms in place: new values, same pointers
+    atoms2 = sfw.AtomSet.from_numpy(m + 0.25, s, d, w * 1.1)
+    l2, g2, r2 = plan.slide_loss_grad(yd, atoms2, lam, want_residual=True)
+    c2 = plan.certificate(r2, lam, want_max=False)
+    for name in ("m", "sigma", "d", "w"):
+        getattr(atoms, name).copy_(getattr(atoms2, name))
+    main.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(main):
+        o2 = plan.step(yd, atoms, lam, aux_stream=aux, out=buf)
+    torch.cuda.current_stream().wait_stream(main)
+    for k, v in {"loss": l2, "grad": g2, "residual": r2, "best_val": c2["best_val"],
+                 "best_idx": c2["best_idx"]}.items():
+        assert torch.equal(o2[k], v), k
+    for name in ("m", "sigma", "d", "w"):
+        getattr(atoms, name).copy_(getattr(sfw.AtomSet.from_numpy(m, s, d, w), name))
     # captured: the fork onto the auxiliary stream becomes a branch of the graph
     out = plan.step(yd, atoms, lam, aux_stream=aux)
     torch.cuda.synchronize()
