@@ -318,7 +318,12 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
 sfw_status sfw_batch_destroy(sfw_batch* batch);
 /* Number of grouped launches one sfw_batch_step issues. */
 sfw_status sfw_batch_query(const sfw_batch* batch, int* launches_per_step);
-/* One hot-path step for every volume of the batch, asynchronous on stream. */
+/* One hot-path step for every volume of the batch, asynchronous on stream.
+ * After the residual stages, the certificate stages run on a stream the batch
+ * owns (an event forks it from stream) while the back-projection and
+ * gradient stages continue on stream; stream then waits for the branch (a
+ * second event), so work queued on stream afterwards sees the whole step.
+ * Under stream capture the fork is a branch of the graph. */
 sfw_status sfw_batch_step(sfw_batch* batch, void* stream);
 /* Autotuner: for every grouped launch, time persistent grids of {resident
  * CTAs, 1, 2, 4, 8 x SMs, all tiles} on the batch's live buffers (after one

@@ -1576,12 +1576,20 @@ struct sfw_batch {
     int num_sms;
     std::vector<sfw_plan*> plans;
     std::vector<BatchLaunch> launches;
+    std::vector<int> branch;   // per launch: 0 before the fork, 1 certificate, 2 back-projection
     void* blob;           // device descriptors of every grouped launch
+    cudaStream_t aux;     // the certificate branch of a step
+    cudaEvent_t ev_fork, ev_join;
 };
 
 static void batch_free(sfw_batch* b) {
     if (b->blob) cudaFree(b->blob);
     b->blob = nullptr;
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->aux) cudaStreamDestroy(b->aux);
+    b->ev_fork = b->ev_join = nullptr;
+    b->aux = nullptr;
 }
 
 // One grouped launch of a batch step (also timed alone by the autotuner).
@@ -1659,8 +1667,17 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
     }
     sfw_status s = SFW_OK;
     std::vector<Recorder> rec(count);
+    std::vector<size_t> n_fork(count), n_cert(count);
     do {
-        // record one step per volume through the single-volume code path
+        if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            s = cuda_fail(cudaGetLastError(), "batch streams");
+            break;
+        }
+        // record one step per volume through the single-volume code path, in the order
+        // residual + loss | certificate | back-projection + gradient (the two last
+        // branches run on two streams)
         for (int v = 0; v < count && !s; ++v) {
             sfw_plan* p = plans[v];
             const sfw_batch_volume& bv = vols[v];
@@ -1671,16 +1688,24 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
             at.sigma = bv.sigma;
             at.d = bv.d;
             at.w = bv.w;
+            float* r = bv.residual ? bv.residual : p->r;
+            s = slide_args(p, bv.y, &at, lambdas[v], bv.loss);
+            if (!s) s = certificate_args(p, r, lambdas[v]);
+            if (s) break;
             g_recorder = &rec[v];
-            s = sfw_slide_loss_grad(p, bv.y, &at, lambdas[v], bv.loss, bv.grad, bv.residual, nullptr);
-            if (!s) s = sfw_certificate_grid(p, bv.residual, lambdas[v], nullptr, nullptr, nullptr,
-                                             bv.best_val, bv.best_idx, nullptr);
+            s = residual_and_loss(p, bv.y, &at, lambdas[v], bv.loss, r, nullptr);
+            n_fork[v] = rec[v].ops.size();
+            if (!s) s = certificate_impl(p, r, lambdas[v], nullptr, nullptr, nullptr, bv.best_val,
+                                         bv.best_idx, nullptr);
+            n_cert[v] = rec[v].ops.size();
+            if (!s && bv.grad) s = loss_gradient(p, &at, lambdas[v], r, bv.grad, nullptr);
             g_recorder = nullptr;
         }
         if (s) break;
         const size_t nops = rec[0].ops.size();
         for (int v = 1; v < count && !s; ++v) {
-            if (rec[v].ops.size() != nops) s = fail(SFW_ERR_UNSUPPORTED, "volumes record different steps");
+            if (rec[v].ops.size() != nops || n_fork[v] != n_fork[0] || n_cert[v] != n_cert[0])
+                s = fail(SFW_ERR_UNSUPPORTED, "volumes record different steps");
             for (size_t i = 0; i < nops && !s; ++i)
                 if (rec[v].ops[i].kind != rec[0].ops[i].kind) s = fail(SFW_ERR_UNSUPPORTED, "volumes record different steps");
         }
@@ -1744,6 +1769,7 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
                 blob.insert(blob.end(), reinterpret_cast<unsigned char*>(nbx.data()),
                             reinterpret_cast<unsigned char*>(nbx.data() + nbx.size()));
                 pend.push_back(P);
+                b->branch.push_back(i < n_fork[0] ? 0 : i < n_cert[0] ? 1 : 2);
             }
         }
         cudaError_t e = cudaMalloc(&b->blob, blob.size() ? blob.size() : 16);
@@ -1795,7 +1821,18 @@ sfw_status sfw_batch_step(sfw_batch* b, void* stream) {
     clear_error();
     if (!b) return fail(SFW_ERR_ARG, "batch is NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (BatchLaunch& L : b->launches) SFW_TRY(batch_launch(b, L, st));
+    const size_t n = b->launches.size();
+    for (size_t i = 0; i < n; ++i)
+        if (b->branch[i] == 0) SFW_TRY(batch_launch(b, b->launches[i], st));
+    // the certificates on the batch's stream while the back-projections continue
+    SFW_CUDA(cudaEventRecord(b->ev_fork, st));
+    SFW_CUDA(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+    for (size_t i = 0; i < n; ++i)
+        if (b->branch[i] == 1) SFW_TRY(batch_launch(b, b->launches[i], b->aux));
+    for (size_t i = 0; i < n; ++i)
+        if (b->branch[i] == 2) SFW_TRY(batch_launch(b, b->launches[i], st));
+    SFW_CUDA(cudaEventRecord(b->ev_join, b->aux));
+    SFW_CUDA(cudaStreamWaitEvent(st, b->ev_join, 0));
     return SFW_OK;
 }
 
