@@ -16,6 +16,9 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "fft_core.cuh"
 
 namespace sfw {
@@ -32,13 +35,36 @@ struct TailGeom {
     static constexpr int NC = P1 / 4;                         // complex lines of axis 2
     static constexpr int NT1 = (P2 / 2) / 4 + 1;              // axis-1 tasks (4 columns each)
     static constexpr int NT2 = NC / RegFFT<P2>::LPW;          // axis-2 tasks
-    static size_t smem() {
-        return sizeof(float2) * ((size_t)SLAB + RegFFT<P1>::TWN + RegFFT<P2>::TWN + (size_t)kTailWarps * XL * XS);
+    // slab capacity (float2): a whole number of TMA boxes may overrun the slab
+    __host__ __device__ static int cap(int boxg, int nbox) {
+        const int c = boxg * nbox * 4 > SLAB ? boxg * nbox * 4 : SLAB;
+        return (c + 15) & ~15;
+    }
+    static size_t smem(int slab_cap) {
+        return 128 + sizeof(float2) * ((size_t)slab_cap + RegFFT<P1>::TWN + RegFFT<P2>::TWN +
+                                       (size_t)kTailWarps * XL * XS);
     }
 };
 
-template <int P1, int P2>
-__global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p) {
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Wait (bounded) for the phase of parity `phase` of the barrier at bar to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase) {
+    for (int it = 0; it < (1 << 16); ++it) {
+        unsigned done = 0;
+        asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, q;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int P1, int P2, bool TMA>
+__global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p,
+                                                            const __grid_constant__ CUtensorMap tmap) {
     using G = TailGeom<P1, P2>;
     static_assert(RegFFT<P1>::T == 8 && RegFFT<P2>::T == 8, "4 lines per warp on both axes");
     static_assert(G::NT2 <= kTailWarps, "one axis-2 task per warp");
@@ -46,13 +72,20 @@ __global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p) {
     constexpr int R1a = RegGeom<P1>::R1, R1b = RegGeom<P2>::R1;
     constexpr int MH = R1b / 2;                 // kept outputs per lane and real row
     extern __shared__ float4 smem_raw[];
-    float2* S = reinterpret_cast<float2*>(smem_raw);
-    float2* TW1 = S + G::SLAB;
+    // the slab starts 128-byte aligned (TMA destination)
+    float2* S = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    float2* TW1 = S + (TMA ? G::cap(p.boxg, p.nbox) : G::cap(0, 0));
     float2* TW2 = TW1 + RegFFT<P1>::TWN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* XW = TW2 + RegFFT<P2>::TWN + warp * (G::XL * G::XS);
     const int t = lane & 7, li = lane >> 3;
     float2* xl = XW + li * G::XS;
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_late;
+    if (TMA && threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_u32(&s_bar)) : "memory");
+        s_late = 0;
+    }
     reg_twiddles<P1, kTailThreads>(p.tw1, TW1);
     reg_twiddles<P2, kTailThreads>(p.tw2, TW2);
     const int i0 = blockIdx.x;
@@ -71,13 +104,38 @@ __global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p) {
     }
     bool saw_nan = false;
 
+    __syncthreads();
     for (int s = 0; s < nk; ++s) {
         const int kk = k0 + s;
-        const float2* src = p.in + ((long long)kk * p.n0 + i0) * G::SLAB;
-        for (int e = threadIdx.x; e < G::SLAB / 2; e += kTailThreads) cp_async16(S + 2 * e, src + 2 * e);
-        cp_async_commit();
-        cp_async_wait0();
-        __syncthreads();
+        if constexpr (TMA) {
+            // the slab's line groups: nbox box copies {4, 1, boxg, 1} at (0, i0, b boxg, kk)
+            const unsigned bar = smem_u32(&s_bar);
+            if (threadIdx.x == 0) {
+                const unsigned bytes = (unsigned)(p.nbox * p.boxg * 32);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                             :: "r"(bar), "r"(bytes) : "memory");
+                for (int b = 0; b < p.nbox; ++b)
+                    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+                                 :: "r"(smem_u32(S + b * p.boxg * 4)), "l"(&tmap), "r"(0), "r"(i0),
+                                    "r"(b * p.boxg), "r"(kk), "r"(bar)
+                                 : "memory");
+            }
+            if (!mbar_wait(bar, (unsigned)(s & 1))) s_late = 1;
+            __syncthreads();
+            if (s_late) {
+                // the copies did not land in time: flag it, wait once more for them, stop
+                if (threadIdx.x == 0) atomicExch(p.err, 1);
+                mbar_wait(bar, (unsigned)(s & 1));
+                break;
+            }
+        } else {
+            const float2* src = p.in + ((long long)kk * p.n0 + i0) * G::SLAB;
+            for (int e = threadIdx.x; e < G::SLAB / 2; e += kTailThreads) cp_async16(S + 2 * e, src + 2 * e);
+            cp_async_commit();
+            cp_async_wait0();
+            __syncthreads();
+        }
         // axis 1: columns (P2 / 2 of them in groups of 32, then the last one, P2 / 2)
         for (int task = warp; task < G::NT1; task += kTailWarps) {
             const int main_tasks = G::NT1 - 1;
@@ -128,7 +186,10 @@ __global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p) {
                 }
             }
         }
-        __syncthreads();   // the slab is reloaded for the next kernel
+        // the slab is reloaded for the next kernel: order this kernel's shared-memory
+        // accesses before the copy engine's writes
+        if constexpr (TMA) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
     }
 
     unsigned long long best = 0ull;
@@ -297,16 +358,17 @@ bool cert_tail_supported(int P1, int P2, int n1, int n2) {
     return (P1 == 64 || P1 == 128) && (P2 == 64 || P2 == 128) && 2 * n1 <= P1 && 2 * n2 <= P2;
 }
 
-template <int P1, int P2>
-static sfw_status run_tail(CertTailPass p, int groups, cudaStream_t st) {
+template <int P1, int P2, bool TMA>
+static sfw_status run_tail(CertTailPass p, const CUtensorMap& tm, int groups, cudaStream_t st) {
     using G = TailGeom<P1, P2>;
-    const size_t smem = G::smem();
-    SFW_TRY(prepare(k_cert_tail<P1, P2>, smem));
+    const size_t smem = G::smem(TMA ? G::cap(p.boxg, p.nbox) : G::cap(0, 0));
+    auto kern = k_cert_tail<P1, P2, TMA>;
+    SFW_TRY(prepare(kern, smem));
     int dev = 0;
     SFW_CUDA(cudaGetDevice(&dev));
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int>, int> chosen;  // (dev, P1, P2, n0, K) -> groups
-    const auto key = std::make_tuple(dev, P1, P2, p.n0, p.ktotal);
+    static std::map<std::tuple<int, int, int, int, int, int>, int> chosen;  // (dev, P1, P2, TMA, n0, K) -> groups
+    const auto key = std::make_tuple(dev, P1, P2, (int)TMA, p.n0, p.ktotal);
     if (groups <= 0) {
         std::lock_guard<std::mutex> lk(mu);
         auto it = chosen.find(key);
@@ -316,7 +378,7 @@ static sfw_status run_tail(CertTailPass p, int groups, cudaStream_t st) {
         // kernels per CTA: the fewest rounds of resident CTAs, then the most kernels per CTA
         int sms = 1, per = 1;
         SFW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cert_tail<P1, P2>, kTailThreads, smem));
+        SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTailThreads, smem));
         const long long slots = (long long)(per > 0 ? per : 1) * sms;
         long long best_cost = -1;
         for (int ns = 1; ns <= p.ktotal; ++ns) {
@@ -335,21 +397,51 @@ static sfw_status run_tail(CertTailPass p, int groups, cudaStream_t st) {
     groups = (p.ktotal + p.nspec - 1) / p.nspec;
     p.ntiles = p.n0 * groups;
     const dim3 grid((unsigned)p.n0, (unsigned)groups);
-    SFW_LAUNCH(st, "k_cert_tail", (k_cert_tail<P1, P2><<<grid, kTailThreads, smem, st>>>(p)));
+    SFW_LAUNCH(st, "k_cert_tail", (kern<<<grid, kTailThreads, smem, st>>>(p, tm)));
     return launch_check("k_cert_tail");
 }
 
-sfw_status launch_cert_tail(const CertTailPass& p0, int groups, cudaStream_t st) {
+bool make_tail_tmap(const void* in, int n0, long long ngroups, int K, int boxg, void* tmap_out) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    });
+    if (!encode || boxg < 1 || boxg > 256 || n0 < 1 || K < 1) return false;
+    const cuuint64_t dims[4] = {4, (cuuint64_t)n0, (cuuint64_t)ngroups, (cuuint64_t)K};
+    const cuuint64_t strides[3] = {32, (cuuint64_t)n0 * 32, (cuuint64_t)ngroups * n0 * 32};
+    const cuuint32_t box[4] = {4, 1, (cuuint32_t)boxg, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMap* tm = static_cast<CUtensorMap*>(tmap_out);
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<void*>(in), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+sfw_status launch_cert_tail(const CertTailPass& p0, const void* tmap, int groups, cudaStream_t st) {
     CertTailPass p = p0;
     if (!cert_tail_supported(p.P1, p.P2, p.n1, p.n2) || p.H2 != p.P2 / 2 + 1)
         return fail(SFW_ERR_SHAPE, "fused certificate tail: unsupported lengths %d x %d", p.P1, p.P2);
     if (p.n0 < 1 || p.ktotal < 1) return SFW_OK;
+    if (tmap && (p.boxg < 4 || p.boxg > 256 || p.boxg % 4 || p.nbox < 1 || !p.err ||
+                 (long long)p.boxg * p.nbox * 4 < (long long)p.P1 * p.H2))
+        return fail(SFW_ERR_ARG, "fused certificate tail: bad box geometry");
     SFW_TRY(twiddle_table(p.P1, p.P1 == 64 ? 8 : 16, &p.tw1));
     SFW_TRY(twiddle_table(p.P2, p.P2 == 64 ? 8 : 16, &p.tw2));
-    if (p.P1 == 64 && p.P2 == 64) return run_tail<64, 64>(p, groups, st);
-    if (p.P1 == 64) return run_tail<64, 128>(p, groups, st);
-    if (p.P2 == 64) return run_tail<128, 64>(p, groups, st);
-    return run_tail<128, 128>(p, groups, st);
+    CUtensorMap tm;
+    if (tmap) memcpy(&tm, tmap, sizeof(tm));
+    else memset(&tm, 0, sizeof(tm));
+#define SFW_TAIL(A, B) return tmap ? run_tail<A, B, true>(p, tm, groups, st) : run_tail<A, B, false>(p, tm, groups, st)
+    if (p.P1 == 64 && p.P2 == 64) SFW_TAIL(64, 64);
+    if (p.P1 == 64) SFW_TAIL(64, 128);
+    if (p.P2 == 64) SFW_TAIL(128, 64);
+    SFW_TAIL(128, 128);
+#undef SFW_TAIL
 }
 
 }  // namespace sfw

@@ -519,6 +519,11 @@ struct sfw_plan {
     int num_sms;
     cudaEvent_t ev_fork, ev_join;  // sfw_step: residual ready / certificate done
     cudaStream_t cap_own, aux_own; // sfw_step captures its graph on these (origin, branch)
+    // certificate tail by TMA: tensor map of the line-group-major axis-0 output (opaque)
+    alignas(64) unsigned char tail_tmap[128];
+    bool tail_tma;
+    int tail_boxg, tail_nbox;
+    int* tail_err;                 // device flag: a tail CTA's copies did not land in time
     // sfw_step's own CUDA graph: captured at the second consecutive call with the same
     // arguments, replayed while they stay the same
     struct StepKey {
@@ -930,6 +935,20 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
             if ((s = plan_alloc_t(p, &p->cA, a_el))) break;
             if ((s = plan_alloc_t(p, &p->cB, b_el))) break;
             if ((s = plan_alloc_t(p, &p->cC, c_el))) break;
+            if ((s = plan_alloc_t(p, &p->tail_err, 1))) break;
+            if (cudaMemset(p->tail_err, 0, sizeof(int)) != cudaSuccess) {
+                s = cuda_fail(cudaGetLastError(), "tail flag");
+                break;
+            }
+            if (cert_tail_supported(p->Pc[1], p->Pc[2], p->n[1], p->n[2])) {
+                // line groups of 4 per slab, fetched in nbox box copies of boxg groups
+                const long long ng = (long long)p->Pc[1] * p->H2c / 4;
+                const int nbox = (int)((ng + 255) / 256);
+                const int boxg = (int)(((ng + nbox - 1) / nbox + 3) / 4 * 4);
+                p->tail_boxg = boxg;
+                p->tail_nbox = nbox;
+                p->tail_tma = make_tail_tmap(p->cC, p->n[0], ng, K, boxg, p->tail_tmap);
+            }
         }
         // H^ on the blur grid, scaled by 1/|P| (folds the inverse normalisation)
         if ((s = launch_wrap_psf(p->psf, p->R, g.P, p->fE, st))) break;
@@ -1230,7 +1249,9 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
         q.spec_kind = p->table_kind;
         q.conj_spec = 0;
         q.out = p->cC;
-        q.lout = ls(0, 1, nl, nl);
+        // the TMA tail reads it line-group-major, [k][l / 4][i0][l mod 4]: a warp's 4 lines
+        // and all its rows form one contiguous block
+        q.lout = (slabs && p->tail_tma) ? ls(4LL * n0, 1, 4, 4) : ls(0, 1, nl, nl);
         q.out_stride = (long long)n0 * nl;
         q.out_off = 0;
         q.out_len = n0;
@@ -1265,8 +1286,11 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
         t.best_val = best_val;
         t.best_idx = best_idx;
         t.counter = p->ctr + 1;
+        t.boxg = p->tail_boxg;
+        t.nbox = p->tail_nbox;
+        t.err = p->tail_err;
         LaunchTag lt__(kCertTailTag);
-        SFW_TRY(launch_cert_tail(t, 0, st));
+        SFW_TRY(launch_cert_tail(t, p->tail_tma ? p->tail_tmap : nullptr, 0, st));
     } else {
         {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
             C2CPass q;

@@ -193,7 +193,10 @@ struct C2RPass {
 // contiguous) -> inverse along axis 1 (keep n1 rows) -> real inverse along axis 2
 // (keep n2) -> running max / argmax over the group, candidate keys as in C2RPass.
 struct CertTailPass {
-    const float2* in;           // (K, n0, P1, H2) complex
+    const float2* in;           // (K, n0, P1, H2) complex; with a tensor map, line-group-major
+                                // [k][l / 4][i0][l mod 4], l = p1 H2 + h2 (read by TMA)
+    int boxg, nbox;             // TMA: line groups per box copy, box copies per slab
+    int* err;                   // TMA: set to 1 if a slab's copies did not complete in time
     int n0, n1, n2, P1, P2, H2;
     int ktotal, nspec;          // kernels; kernels per CTA (grid.y = groups)
     const float2* tw1;          // twiddles of P1 (register factorisation)
@@ -210,7 +213,12 @@ struct CertTailPass {
 };
 // True when the fused tail handles these lengths (shared memory holds one slab).
 bool cert_tail_supported(int P1, int P2, int n1, int n2);
-sfw_status launch_cert_tail(const CertTailPass& p, int groups, cudaStream_t st);
+// tmap: NULL (contiguous slabs, cp.async) or the 4-D tensor map of make_tail_tmap
+// (line-group-major slabs, TMA box copies), an opaque 128-byte CUtensorMap.
+sfw_status launch_cert_tail(const CertTailPass& p, const void* tmap, int groups, cudaStream_t st);
+// Encode the tensor map {4, n0, P1 H2 / 4, K} (8-byte elements) of the line-group-major
+// intermediate at in, boxes {4, 1, boxg, 1}; false if the driver entry point is missing.
+bool make_tail_tmap(const void* in, int n0, long long ngroups, int K, int boxg, void* tmap_out);
 
 // Certificate head fused in one pass (same lengths as the tail): per i0 slab, the real
 // forward transform of the residual rows along axis 2 (zero-padded n2 -> P2) and the
