@@ -117,6 +117,13 @@ sfw_status sfw_plan_destroy(sfw_plan* plan);
 /* Copy the plan's sizes into *info (host). */
 sfw_status sfw_plan_query(const sfw_plan* plan, sfw_plan_info* info);
 
+/* Device-side health of a plan (no counterpart in the paper).  Kernels that
+ * wait on the copy engine (the certificate tail's TMA slab copies) give up
+ * after a bounded number of polls, leave their results unspecified and set a
+ * flag of the plan instead of hanging.  This call synchronises the device,
+ * returns SFW_ERR_TIMEOUT if the flag is set (and clears it), else SFW_OK. */
+sfw_status sfw_plan_check(sfw_plan* plan);
+
 /* Forward operator Phi mu (Eq. 3 without noise), Section 1.1.
  *   atoms  device atom set (m, sigma, d, w)
  *   y_out  device, n0*n1*n2 floats, receives (H * sum_n G(theta_n, w_n)) on the grid */

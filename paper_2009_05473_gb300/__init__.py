@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_topk,  # noqa: F401
                    sfw_eta_points, sfw_forward, sfw_gram,
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
-                   sfw_slide_loss_grad, sfw_step, sfw_version)
+                   sfw_plan_check, sfw_slide_loss_grad, sfw_step, sfw_version)
 
 __all__ = ["Plan", "AtomSet", "Batch", "argmax", "launch_count", "SfwError", "build_library"]
 
@@ -214,6 +214,11 @@ class Plan:
         sfw_slide_loss_grad(self.handle, _ptr(y), atoms.abi(), lam, _ptr(loss), _ptr(grad),
                             _ptr(r) if want_residual else 0, _stream_ptr(stream))
         return loss, grad, (r if want_residual else None)
+
+    def check(self):
+        """Raise SfwError (SFW_ERR_TIMEOUT) if a bounded device wait of this plan's kernels ran
+        out since the last check (synchronises the device)."""
+        sfw_plan_check(self.handle)
 
     def step(self, y, atoms: AtomSet, lam: float, aux_stream=None, stream=None, out=None,
              want_grad: bool = True):

@@ -20,7 +20,7 @@ SFW_PREC_FP32 = 0
 SFW_PREC_BF16 = 1
 
 # every symbol declared in include/sfw.h
-EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
+EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_forward",
            "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
            "sfw_slide_loss_grad", "sfw_step", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
            "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_argmax_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
     L.sfw_step.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp, vp, vp, vp]
+    L.sfw_plan_check.argtypes = [vp]
     L.sfw_profile_start.argtypes = [i32, ctypes.c_char_p]
     L.sfw_gram.argtypes = [vp, ctypes.POINTER(Atoms), vp, vp, vp, vp]
     L.sfw_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(BatchVolume),
@@ -93,7 +94,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_batch_autotune.argtypes = [vp, ctypes.c_char_p, vp]
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
-    for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_forward",
+    for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_forward",
                  "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
                  "sfw_slide_loss_grad", "sfw_step", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
            "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect",
@@ -172,6 +173,10 @@ def sfw_slide_loss_grad(plan: int, y: int, atoms: Atoms, lam: float, loss_out: i
                         residual_out: int, stream: int) -> None:
     check(lib().sfw_slide_loss_grad(plan, y, ctypes.byref(atoms), float(lam), loss_out, grad_out,
                                     residual_out, stream), "sfw_slide_loss_grad")
+
+
+def sfw_plan_check(plan: int) -> None:
+    check(lib().sfw_plan_check(plan), "sfw_plan_check")
 
 
 def sfw_step(plan: int, y: int, atoms: Atoms, lam: float, loss_out: int, grad_out: int,

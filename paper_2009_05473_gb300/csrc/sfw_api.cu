@@ -1449,13 +1449,16 @@ sfw_status sfw_eta_points(sfw_plan* p, const float* residual, double lambda, int
 
 // Test hook (not part of the public header): copy an internal plan buffer to
 // host memory.  which: 0 = rendered atoms on E, 1 = H spectrum, 2 = back-projection on E.
-sfw_status sfw_debug_read(const sfw_plan* p, int which, void* host, size_t bytes) {
+sfw_status sfw_plan_check(sfw_plan* p) {
     clear_error();
-    if (!p || !host) return fail(SFW_ERR_ARG, "NULL");
-    const void* src = which == 0 ? (const void*)p->fE : which == 1 ? (const void*)p->Hspec : (const void*)p->bE;
+    if (!p) return fail(SFW_ERR_ARG, "plan is NULL");
+    if (!p->tail_err) return SFW_OK;
+    int flag = 0;
     SFW_CUDA(cudaDeviceSynchronize());
-    SFW_CUDA(cudaMemcpy(host, src, bytes, cudaMemcpyDeviceToHost));
-    return SFW_OK;
+    SFW_CUDA(cudaMemcpy(&flag, p->tail_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!flag) return SFW_OK;
+    SFW_CUDA(cudaMemset(p->tail_err, 0, sizeof(int)));
+    return fail(SFW_ERR_TIMEOUT, "a certificate-tail CTA gave up waiting for its slab copies");
 }
 
 sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_out,
