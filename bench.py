@@ -8,8 +8,13 @@ x 3 d = 15 kernels):
      blur, residual + loss, transposed blur, per-atom adjoint sums);
   2. grid certificate of the new residual over all voxels x 15 kernels, with
      the fused device argmax (the seed of the next local ascent).
-Metric: eta-grid candidates/s = V K / step time (also reported: steps/s,
-i.e. SFW iterations/s of this hot path).
+Metric: eta-grid candidates/s = V K / step time.  Also reported: steps/s; the
+sliding step's loss + gradient evaluations/s (its own replayed graph); the outer
+iterations/s of Algorithms 1 and 2 on the GPU path for the 32^3 and 64^3
+configurations (`sfw_outer`, skipped with --no-solver).
+`--workload batch64_uneven`: 64 uneven volumes stepped as one batch.
+`--workload fig2_sfw_vs_bsfw`: SFW against BSFW (time to stop, final criterion) on
+64^3 volumes with 4/6/8 atoms, a synthetic analogue of the paper's Fig. 2.
 
 The timed region replays a CUDA graph of the step; L2 (129 MB) is flushed by a
 256 MB write between steps, outside the per-step CUDA events.  The library
@@ -48,6 +53,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solver", action="store_true",
+                    help="skip the outer SFW/BSFW iteration rates (GPU solves on 32^3 and 64^3)")
+    ap.add_argument("--seeds", type=int, default=5, help="fig2_sfw_vs_bsfw: seeds per atom count")
     return ap.parse_args()
 
 
@@ -184,6 +192,27 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- our arm
 
+def observe_on_device(sfw, plan, vol, dev):
+    """y = Phi mu* + noise on the device (the library's own forward operator) and the
+    lambda rule 0.05 * max of the grid certificate of y at lambda = 1."""
+    import torch
+    truth = sfw.AtomSet.from_numpy(vol.m, vol.sigma, vol.d, vol.w, device=dev)
+    y = plan.forward(truth)
+    y += vol.noise_frac * y.max() * torch.tensor(vol.noise, dtype=torch.float32, device=dev)
+    c0 = plan.certificate(y, 1.0, want_max=False)
+    return y, 0.05 * float(c0["best_val"].item())
+
+
+def gpu_solve(sfw, plan, vol, dev, boosted):
+    """Algorithm 1 (SFW) or 2 (BSFW) on the GPU path: outer iterations, seconds, criterion."""
+    from paper_2009_05473_gb300 import solver
+    y, lam = observe_on_device(sfw, plan, vol, dev)
+    out = (solver.bsfw if boosted else solver.sfw)(plan, y, lam)
+    iters = len(out["history"])
+    return {"outer_iters": iters, "seconds": out["seconds"], "iters_per_s": iters / out["seconds"],
+            "C": out["C"], "atoms": int(out["w"].size), "true_atoms": int(vol.N)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -204,13 +233,9 @@ def run_ours(args):
     V, K = vol.V, plan.K
     dev = torch.device("cuda", local_rank)
 
-    # observation y = Phi mu* + noise, made on the device by the library's own forward operator
-    truth = sfw.AtomSet.from_numpy(vol.m, vol.sigma, vol.d, vol.w, device=dev)
-    y = plan.forward(truth)
-    y += vol.noise_frac * y.max() * torch.tensor(vol.noise, dtype=torch.float32, device=dev)
+    # observation y = Phi mu* + noise made on the device by the library's own forward operator;
     # lambda = 0.05 * max over the grid of Phi^T y  (first certificate max = 20)
-    c0 = plan.certificate(y, 1.0, want_max=False)
-    lam = 0.05 * float(c0["best_val"].item())
+    y, lam = observe_on_device(sfw, plan, vol, dev)
     # the current iterate of a sliding step: atoms near, not at, the truth
     rng = np.random.default_rng(1000 + rank)
     est = sfw.AtomSet.from_numpy(vol.m + rng.normal(0, 0.4, vol.m.shape), vol.sigma * 1.05,
@@ -340,6 +365,43 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_value = world * args.e2e_steps * cands / float(tt.item())
 
+    # the sliding step's loss + gradient alone (the evaluation BFGS repeats in step 4 of
+    # Algorithm 1): its own graph, replayed with the L2 flushed in between
+    sb = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
+          "grad": torch.empty(6 * vol.N, dtype=torch.float64, device=dev),
+          "residual": torch.empty(vol.n, dtype=torch.float32, device=dev)}
+    for _ in range(3):
+        plan.slide_loss_grad(y, est, lam, want_residual=True, out=sb)
+    torch.cuda.synchronize()
+    sgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(sgraph, stream=cap_stream):
+            plan.slide_loss_grad(y, est, lam, want_residual=True, out=sb)
+    torch.cuda.synchronize()
+    n_slide = 300
+    s_ms = 0.0
+    for i in range(n_slide):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sgraph.replay()
+        e1.record()
+        e1.synchronize()
+        s_ms += e0.elapsed_time(e1)
+    slide_evals_per_s = world * n_slide / (s_ms / 1e3)
+    del sgraph
+
+    # outer iterations of Algorithms 1 and 2 on the GPU path (configurations 1 and 2)
+    outer = None
+    if rank == 0 and world == 1 and not args.no_solver:
+        outer = {}
+        for wl in ("vol32_iso_n3", "vol64_aniso_n10"):
+            v = getattr(sfw_inputs, wl)(seed=0)
+            pl = sfw.Plan(v.n, v.R, v.psf, v.grid_sigmas, v.grid_ds)
+            outer[wl] = {"sfw": gpu_solve(sfw, pl, v, dev, False), "bsfw": gpu_solve(sfw, pl, v, dev, True)}
+            pl.close()
+
     line = None
     if rank == 0:
         line = {
@@ -359,8 +421,9 @@ def run_ours(args):
                        "atoms": vol.N, "kernels": K, "candidates_per_step": cands,
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                        "timing": "CUDA graph replay per step, CUDA events per step"},
-            "sfw_iters_per_s": world * args.steps / (t_max / 1e3),
-            "slide_evals_per_s": world * args.steps / (t_max / 1e3),
+            "steps_per_s": world * args.steps / (t_max / 1e3),
+            "slide_evals_per_s": slide_evals_per_s,
+            "sfw_outer": outer,
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
@@ -529,12 +592,49 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fig2(args):
+    """Synthetic analogue of the paper's Fig. 2 (Section 4): SFW (Algorithm 1) against BSFW
+    (Algorithm 2) on 64^3 volumes with 4, 6 and 8 atoms, `--seeds` seeds each, same PSF and
+    certificate grid as the 64^3 workload; time to stop and final criterion C (Eq. 4)."""
+    import torch
+    import paper_2009_05473_gb300 as sfw
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sfw.build_library()
+    base = sfw_inputs.vol64_aniso_n10(seed=0)
+    plan = sfw.Plan(base.n, base.R, base.psf, base.grid_sigmas, base.grid_ds)
+    runs, summary = [], {}
+    for N in (4, 6, 8):
+        rows = []
+        for sd in range(args.seeds):
+            v = sfw_inputs.make_volume(f"fig2_n{N}", base.n, base.R, base.psf_sigma, N, seed=100 * N + sd,
+                                       noise_frac=0.02, grid_sigmas=base.grid_sigmas, grid_ds=base.grid_ds)
+            a = gpu_solve(sfw, plan, v, dev, False)
+            b = gpu_solve(sfw, plan, v, dev, True)
+            rows.append({"N": N, "seed": 100 * N + sd, "sfw": a, "bsfw": b})
+        t_s = float(np.mean([r["sfw"]["seconds"] for r in rows]))
+        t_b = float(np.mean([r["bsfw"]["seconds"] for r in rows]))
+        dC = [(r["bsfw"]["C"] - r["sfw"]["C"]) / abs(r["sfw"]["C"]) for r in rows]
+        summary[str(N)] = {"sfw_seconds": t_s, "bsfw_seconds": t_b, "bsfw_time_saving": 1.0 - t_b / t_s,
+                           "bsfw_minus_sfw_C_rel_mean": float(np.mean(dC)),
+                           "bsfw_minus_sfw_C_rel_max": float(np.max(np.abs(dC)))}
+        runs += rows
+    plan.close()
+    print(json.dumps({"experiment": "fig2_sfw_vs_bsfw", "volume": list(base.n), "seeds_per_N": args.seeds,
+                      "summary": summary, "runs": runs}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64_uneven":
         run_batch(args)
+    elif args.workload == "fig2_sfw_vs_bsfw":
+        run_fig2(args)
     else:
         run_ours(args)
 
