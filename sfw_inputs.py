@@ -80,6 +80,20 @@ def gaussian_psf(psf_sigma, R) -> np.ndarray:
     return h / h.sum()
 
 
+def tilted_gaussian_psf(psf_sigma, R, angles) -> np.ndarray:
+    """Sampled anisotropic Gaussian whose principal axes are turned by angles[0] about axis 0
+    and then angles[1] about axis 1 (radians): covariance Q diag(sigma^2) Q^T on a (2R+1) box,
+    centred, normalised to sum 1.  Not separable along the grid axes; point-symmetric."""
+    a, b = angles
+    r0 = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
+    r1 = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
+    q = r1 @ r0
+    prec = q @ np.diag(1.0 / np.asarray(psf_sigma, np.float64) ** 2) @ q.T
+    x = np.stack(np.meshgrid(*[np.arange(-r, r + 1, dtype=np.float64) for r in R], indexing="ij"), -1)
+    h = np.exp(-0.5 * np.einsum("...i,ij,...j->...", x, prec, x))
+    return h / h.sum()
+
+
 def _draw_atoms(rng, n, N, sigma_rng, d_rng, w_rng, min_sep):
     lo = np.full(3, float(MARGIN))
     hi = np.array(n, dtype=np.float64) - 1.0 - MARGIN
@@ -101,7 +115,7 @@ def _draw_atoms(rng, n, N, sigma_rng, d_rng, w_rng, min_sep):
     return m, sig, dd, w
 
 
-def make_volume(name: str, n, R, psf_sigma, N, *, seed=0, noise_frac=0.02,
+def make_volume(name: str, n, R, psf_sigma, N, *, seed=0, noise_frac=0.02, psf=None,
                 grid_sigmas=(1.0, 2.0, 3.0), grid_ds=(2.0,), sigma_rng=(1.0, 3.0),
                 d_rng=(1.5, 2.5), w_rng=(0.5, 1.5), min_sep=4.0, rng=None) -> Volume:
     rng = np.random.default_rng(seed) if rng is None else rng
@@ -110,7 +124,8 @@ def make_volume(name: str, n, R, psf_sigma, N, *, seed=0, noise_frac=0.02,
     m, sig, dd, w = _draw_atoms(rng, n, N, sigma_rng, d_rng, w_rng, min_sep)
     noise = rng.standard_normal(n)
     return Volume(name=name, n=n, R=R, psf_sigma=tuple(float(s) for s in psf_sigma),
-                  psf=gaussian_psf(psf_sigma, R), m=m, sigma=sig, d=dd, w=w, noise=noise,
+                  psf=gaussian_psf(psf_sigma, R) if psf is None else np.asarray(psf, np.float64),
+                  m=m, sigma=sig, d=dd, w=w, noise=noise,
                   noise_frac=float(noise_frac), grid_sigmas=np.asarray(grid_sigmas, np.float64),
                   grid_ds=np.asarray(grid_ds, np.float64), seed=seed)
 
@@ -177,9 +192,18 @@ def random_atoms(rng, n, N, sigma_rng=(1.0, 3.0), d_rng=(1.5, 2.5), w_rng=(0.5, 
     return m, rng.uniform(*sigma_rng, N), rng.uniform(*d_rng, N), rng.uniform(*w_rng, N)
 
 
+def vol64_tilted_n10(seed=0) -> Volume:
+    """The 64^3 workload with a non-separable PSF: the (1.5, 1.5, 3) Gaussian turned by 0.5 rad
+    about axis 0 and 0.3 rad about axis 1, on the same 15x15x31 support."""
+    return make_volume("vol64_tilted_n10_k15", (64, 64, 64), ANISO_R, ANISO_PSF, 10, seed=seed,
+                       noise_frac=0.02, psf=tilted_gaussian_psf(ANISO_PSF, ANISO_R, (0.5, 0.3)),
+                       grid_sigmas=np.linspace(1.0, 3.0, 5), grid_ds=(1.5, 2.0, 2.5))
+
+
 WORKLOADS = {
     "vol32_iso9_n3_k3": vol32_iso_n3,
     "vol64_aniso_n10_k15": vol64_aniso_n10,
+    "vol64_tilted_n10_k15": vol64_tilted_n10,
     "vol128_aniso_n30_k32": vol128_aniso_n30,
     "vol256x256x64_n100": vol256x256x64_n100,
 }
