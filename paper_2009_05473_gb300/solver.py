@@ -191,9 +191,16 @@ class GPUSolver:
         return _unpack(x)
 
     # -- Algorithms 1 and 2 ---------------------------------------------------------------
-    def run(self, boosted: bool, max_iter: int = 50, log=None) -> Dict:
-        thetas = np.zeros((0, 5))
-        w = np.zeros(0)
+    def run(self, boosted: bool, max_iter: int = 50, log=None, thetas0=None, w0=None) -> Dict:
+        thetas = np.zeros((0, 5)) if thetas0 is None else np.array(thetas0, np.float64).reshape(-1, 5)
+        w = np.zeros(0) if w0 is None else np.array(w0, np.float64).ravel()
+        if w.size:
+            # a warm start: re-fit the given atoms' weights and positions at this lambda
+            w = self.lasso(thetas)
+            thetas, w = _prune(thetas, w)
+            if w.size:
+                thetas, w = self.slide(thetas, w)
+                thetas, w = _prune(thetas, w)
         hist: List[Dict] = []
         t0 = time.perf_counter()
         for it in range(max_iter):
@@ -238,6 +245,32 @@ def _prune(thetas, w):
         return thetas, w
     keep = w > 1e-10 * w.max()
     return thetas[keep], w[keep]
+
+
+def lambda_max(plan: Plan, y: torch.Tensor) -> float:
+    """Smallest lambda at which the empty measure passes the stopping test: the maximum of
+    the correlation <Phi G(theta, 1), y> over the domain (the certificate of Eq. 5 at
+    lambda = 1 with residual y), by step 1 of Algorithm 1 (grid argmax, then local ascent)."""
+    _, eta, _ = GPUSolver(plan, y, 1.0).certificate_max(np.zeros((0, 5)), np.zeros(0))
+    return float(eta)
+
+
+def lambda_path(plan: Plan, y: torch.Tensor, fractions=(0.5, 0.2, 0.1, 0.05), boosted: bool = True,
+                **kw) -> List[Dict]:
+    """Solutions along decreasing lambda = f * lambda_max (f in fractions, decreasing), each
+    solve warm-started from the previous one's atoms.  lambda only rescales the certificate
+    (Eq. 5), so the certificate maximum of y fixes the scale of the whole path; fractions
+    above 1 + tau give the empty measure."""
+    lmax = lambda_max(plan, y)
+    thetas, w = None, None
+    path = []
+    for f in sorted(fractions, reverse=True):
+        lam = f * lmax
+        out = GPUSolver(plan, y, lam, **kw).run(boosted=boosted, thetas0=thetas, w0=w)
+        thetas, w = out["thetas"], out["w"]
+        out["lambda"], out["fraction"] = lam, f
+        path.append(out)
+    return path
 
 
 def sfw(plan: Plan, y: torch.Tensor, lam: float, **kw) -> Dict:

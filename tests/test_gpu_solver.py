@@ -93,3 +93,28 @@ def test_solver_matches_oracle_vol32(sfw, oracle_mod, boosted):
         assert np.max(np.abs(a[:3] - b[:3])) <= 1e-3
         assert abs(a[3] - b[3]) <= 1e-3 * a[3] and abs(a[4] - b[4]) <= 1e-3 * a[4]
         assert abs(ref["w"][i_ref] - got["w"][i_gpu]) <= 1e-3 * ref["w"][i_ref]
+
+
+def test_lambda_path_vol32(sfw, oracle_mod):
+    """Regularisation path: above lambda_max the empty measure is the solution; at every lambda
+    of the path the grid certificate of the final residual stays <= 1 + tau (the stopping
+    test); the warm-started last point matches a cold solve at that lambda."""
+    import torch
+    from paper_2009_05473_gb300 import solver
+    vol = sfw_inputs.vol32_iso_n3()
+    y = _f32(oracle_mod.observe(vol, fft=True))
+    plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    lmax = solver.lambda_max(plan, yd)
+    path = solver.lambda_path(plan, yd, fractions=(1.05, 0.3, 0.1), boosted=False)
+    assert [p["fraction"] for p in path] == [1.05, 0.3, 0.1]
+    assert path[0]["w"].size == 0
+    assert path[1]["w"].size >= 1 and path[2]["w"].size >= path[1]["w"].size
+    for p in path[1:]:
+        atoms = sfw.AtomSet.from_numpy(p["thetas"][:, :3], p["thetas"][:, 3], p["thetas"][:, 4], p["w"])
+        _, _, res = plan.slide_loss_grad(yd, atoms, p["lambda"], want_residual=True, want_grad=False)
+        eta_max = float(plan.certificate(res, p["lambda"], want_max=False)["best_val"].item())
+        assert eta_max <= 1.0 + 1e-3
+    cold = solver.sfw(plan, yd, path[2]["lambda"])
+    assert abs(cold["C"] - path[2]["C"]) <= 1e-4 * abs(cold["C"])
+    assert lmax > 0
