@@ -155,6 +155,10 @@ def algorithmic_bytes(tag: str, plan, vol) -> float:
         "bp_axis0": n0 * P[1] * H2 * c8 + P[0] * P[1] * H2 * c8 + E[0] * P[1] * H2 * c8,
         "bp_c2c_inv": E[0] * P[1] * H2 * c8 + E[0] * E[1] * H2 * c8,
         "bp_c2r": E[0] * E[1] * H2 * c8 + VE * 4,
+        "blur_head": VE * 4 + E[0] * P[1] * H2 * c8,
+        "blur_tail": n0 * P[1] * H2 * c8 + V * 8,
+        "bp_head": V * 4 + n0 * P[1] * H2 * c8,
+        "bp_tail": E[0] * P[1] * H2 * c8 + VE * 4,
         "k_render": VE * 4,
     }
     return float(table.get(tag, 0.0))

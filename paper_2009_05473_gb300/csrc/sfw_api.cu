@@ -152,13 +152,56 @@ struct PassTags {
     const char* axis0;
     const char* inv1;
     const char* c2r;
+    const char* head;   // r2c + fwd1 per slab
+    const char* tail;   // inv1 + c2r per slab
 };
-static const PassTags kBlurTags = {"blur_r2c", "blur_c2c_fwd", "blur_axis0", "blur_c2c_inv", "blur_c2r"};
-static const PassTags kBackTags = {"bp_r2c", "bp_c2c_fwd", "bp_axis0", "bp_c2c_inv", "bp_c2r"};
-static const PassTags kTableTags = {"table_r2c", "table_c2c_fwd", "table_axis0", "table_c2c_inv", "table_c2r"};
+static const PassTags kBlurTags = {"blur_r2c", "blur_c2c_fwd", "blur_axis0", "blur_c2c_inv", "blur_c2r",
+                                   "blur_head", "blur_tail"};
+static const PassTags kBackTags = {"bp_r2c", "bp_c2c_fwd", "bp_axis0", "bp_c2c_inv", "bp_c2r",
+                                   "bp_head", "bp_tail"};
+static const PassTags kTableTags = {"table_r2c", "table_c2c_fwd", "table_axis0", "table_c2c_inv", "table_c2r",
+                                    "table_head", "table_tail"};
 static const char* const kCertHeadTag = "cert_head";
 static const char* const kCertTailTag = "cert_tail";
-static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max"};
+static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max",
+                                   nullptr, nullptr};
+
+// Axes 1 and 2 of a blur per slab of axis 0 (one CTA each) where the slab fits in
+// shared memory.  A batch records the slab passes only if those of every volume fit
+// (its volumes must record the same sequence of passes).
+static thread_local bool g_slab_batch = false;
+static bool use_slab(const SlabPass& s) {
+    if (g_recorder) return g_slab_batch;
+    return s.nslab > 0 && slab_smem(s) > 0;
+}
+
+static SlabPass slab_pass(const BlurGeom& g, int mode, int nslab) {
+    SlabPass s;
+    memset(&s, 0, sizeof(s));
+    s.mode = mode;
+    s.nslab = nslab;
+    s.P1 = g.P[1];
+    s.P2 = g.P[2];
+    s.H2 = g.H2;
+    return s;
+}
+
+// Whether all four slab passes of a blur and its transpose fit in shared memory.
+static bool blur_slabs_fit(const BlurGeom& g) {
+    SlabPass a = slab_pass(g, SLAB_HEAD, g.E[0]);
+    a.rows = g.E[1];
+    a.cols = g.E[2];
+    SlabPass b = slab_pass(g, SLAB_RESIDUAL, g.n[0]);
+    b.m1 = g.n[1];
+    b.m2 = g.n[2];
+    SlabPass c = slab_pass(g, SLAB_HEAD, g.n[0]);
+    c.rows = g.n[1];
+    c.cols = g.n[2];
+    SlabPass d = slab_pass(g, SLAB_STORE, g.E[0]);
+    d.m1 = g.E[1];
+    d.m2 = g.E[2];
+    return slab_smem(a) && slab_smem(b) && slab_smem(c) && slab_smem(d);
+}
 
 static LineSet ls(long long Sa, long long Sb, long long Sj, long long B) {
     LineSet s;
@@ -177,6 +220,15 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
     const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2];
     const int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2], H2 = g.H2;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    SlabPass head = slab_pass(g, SLAB_HEAD, E0);
+    head.rows = E1;
+    head.cols = E2;
+    head.rin = f;
+    head.cout = bufB;
+    if (use_slab(head)) {   // axes 2 and 1 forward per slab: f -> (E0, P1, H2)
+        LaunchTag lt__(tg.head);
+        SFW_TRY(launch_slab(head, st));
+    } else {
     {   // axis 2: real lines of f -> half spectra (E0, E1, H2)
         R2CPass p;
         p.in = f;
@@ -215,6 +267,7 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
             SFW_TRY(launch_c2c(p, st));
         }
     }
+    }
     {   // axis 0: forward, times H^, inverse, keep rows [R0, R0 + n0) -> (n0, P1, H2)
         MulPass p;
         const long long nl = (long long)P1 * H2;
@@ -241,6 +294,29 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         {
             LaunchTag lt__(tg.axis0);
             SFW_TRY(launch_mul(p, st));
+        }
+    }
+    if ((ep.mode == C2R_STORE || ep.mode == C2R_RESIDUAL) && ep.scale == 1.f) {
+        // axes 1 and 2 inverse per slab with the store or residual epilogue
+        SlabPass tail = slab_pass(g, ep.mode == C2R_STORE ? SLAB_STORE : SLAB_RESIDUAL, n0);
+        tail.cin = bufA;
+        tail.o1 = g.R[1];
+        tail.m1 = n1;
+        tail.o2 = g.R[2];
+        tail.m2 = n2;
+        tail.rout = ep.out;
+        tail.y = ep.y;
+        tail.partials = ep.partials;
+        tail.counter = ep.counter;
+        tail.loss_out = ep.loss_out;
+        tail.w = ep.w;
+        tail.nw = ep.nw;
+        tail.w_stride = ep.w_stride;
+        tail.lambda = ep.lambda;
+        if (use_slab(tail)) {
+            if (c2r_blocks_out) *c2r_blocks_out = n0;
+            LaunchTag lt__(tg.tail);
+            return launch_slab(tail, st);
         }
     }
     {   // axis 1 inverse: (n0, P1, H2) -> (n0, n1, H2), rows [R1, R1 + n1)
@@ -287,6 +363,17 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
     const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2];
     const int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2], H2 = g.H2;
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+    SlabPass head = slab_pass(g, SLAB_HEAD, n0);
+    head.rows = n1;
+    head.cols = n2;
+    head.o1 = g.R[1];
+    head.o2 = g.R[2];
+    head.rin = r;
+    head.cout = bufB;
+    if (use_slab(head)) {   // axes 2 and 1 forward per slab, r placed at [R1, R2): -> (n0, P1, H2)
+        LaunchTag lt__(tg.head);
+        SFW_TRY(launch_slab(head, st));
+    } else {
     {   // axis 2: grid lines of r placed at rows [R2, R2 + n2) -> (n0, n1, H2)
         R2CPass p;
         p.in = r;
@@ -325,6 +412,7 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
             SFW_TRY(launch_c2c(p, st));
         }
     }
+    }
     {   // axis 0: forward (rows at [R0, R0 + n0)), times conj(H^), inverse -> (E0, P1, H2)
         MulPass p;
         const long long nl = (long long)P1 * H2;
@@ -351,6 +439,17 @@ static sfw_status blur_transpose(const BlurGeom& g, const float* r, const void* 
         {
             LaunchTag lt__(tg.axis0);
             SFW_TRY(launch_mul(p, st));
+        }
+    }
+    {
+        SlabPass tail = slab_pass(g, SLAB_STORE, E0);
+        tail.cin = bufA;
+        tail.m1 = E1;
+        tail.m2 = E2;
+        tail.rout = b;
+        if (use_slab(tail)) {   // axes 1 and 2 inverse per slab: -> b (E0, E1, E2)
+            LaunchTag lt__(tg.tail);
+            return launch_slab(tail, st);
         }
     }
     {   // axis 1 inverse: (E0, P1, H2) -> (E0, E1, H2)
@@ -877,7 +976,8 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         if ((s = plan_alloc_t(p, &p->fE, (size_t)(p->VE > Ptot ? p->VE : Ptot)))) break;
         if ((s = plan_alloc_t(p, &p->bE, (size_t)p->VE))) break;
         if ((s = plan_alloc_t(p, &p->r, (size_t)p->V))) break;
-        p->loss_parts_len = (int)(((long long)p->n[0] * p->n[1] + 15) / 16) + 16;
+        // one partial per residual tile (per-axis passes) or per slab (slab passes)
+        p->loss_parts_len = (int)(((long long)p->n[0] * p->n[1] + 15) / 16) + 16 + p->n[0];
         if ((s = plan_alloc_t(p, &p->loss_parts, (size_t)p->loss_parts_len))) break;
         p->grad_parts_atoms = 4096;
         if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;
@@ -1536,6 +1636,9 @@ std::string variant_key(const RecOp& o) {
             snprintf(b, sizeof(b), "c2r/%d/%d/%d/%d", fft_specialised(o.c2r.L) ? o.c2r.L : 0, W, o.c2r.mode, slots);
             break;
         }
+        case OP_SLAB:
+            snprintf(b, sizeof(b), "slab/%d/%d", o.slab.mode, slab_specialised(o.slab) ? 1 : 0);
+            break;
         default:
             snprintf(b, sizeof(b), "op/%d", (int)o.kind);
     }
@@ -1548,6 +1651,7 @@ int op_length(const RecOp& o) {
         case OP_C2C: return o.c2c.L;
         case OP_MUL: return o.mul.L;
         case OP_C2R: return o.c2r.L;
+        case OP_SLAB: return (int)slab_smem(o.slab);   // the group's prototype needs the most
         default: return 0;
     }
 }
@@ -1562,6 +1666,7 @@ void op_tiles(const RecOp& o, int* nbx, int* total) {
         case OP_C2R: pass_tiles(o.c2r, &W, nbx, &nby); *total = *nbx * nby; break;
         case OP_RENDER: *total = render_tiles(o.render, nbx); break;
         case OP_GRAD: *total = grad_tiles(o.grad, nbx); break;
+        case OP_SLAB: *nbx = 1; *total = o.slab.nslab; break;
         default: *nbx = 1; *total = 1;
     }
 }
@@ -1574,6 +1679,7 @@ template <> const MulPass& op_payload<MulPass>(const RecOp& o) { return o.mul; }
 template <> const C2RPass& op_payload<C2RPass>(const RecOp& o) { return o.c2r; }
 template <> const RenderOp& op_payload<RenderOp>(const RecOp& o) { return o.render; }
 template <> const GradOp& op_payload<GradOp>(const RecOp& o) { return o.grad; }
+template <> const SlabPass& op_payload<SlabPass>(const RecOp& o) { return o.slab; }
 
 template <class T>
 void append_payloads(const std::vector<const RecOp*>& ops, std::vector<unsigned char>& blob) {
@@ -1592,6 +1698,7 @@ size_t payload_size(OpKind k) {
         case OP_C2R: return sizeof(C2RPass);
         case OP_RENDER: return sizeof(RenderOp);
         case OP_GRAD: return sizeof(GradOp);
+        case OP_SLAB: return sizeof(SlabPass);
         default: return 0;
     }
 }
@@ -1647,6 +1754,11 @@ static sfw_status batch_launch(sfw_batch* b, BatchLaunch& L, cudaStream_t st) {
             if (g.grid <= 0) g.grid = g.total < 8 * b->num_sms ? g.total : 8 * b->num_sms;
             LaunchTag t("batch_render");
             SFW_TRY(launch_render_group(static_cast<const RenderOp*>(g.passes), g.start, g.nbx, g.n, g.total, g.grid, st));
+            break;
+        }
+        case OP_SLAB: {
+            LaunchTag t(L.proto.slab.mode == SLAB_HEAD ? "batch_slab_head" : "batch_slab_tail");
+            SFW_TRY(launch_slab(L.proto.slab, st, &g));
             break;
         }
         case OP_GRAD: {
@@ -1705,6 +1817,8 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
         // record one step per volume through the single-volume code path, in the order
         // residual + loss | certificate | back-projection + gradient (the two last
         // branches run on two streams)
+        g_slab_batch = true;
+        for (int v = 0; v < count; ++v) g_slab_batch = g_slab_batch && blur_slabs_fit(plans[v]->blur);
         for (int v = 0; v < count && !s; ++v) {
             sfw_plan* p = plans[v];
             const sfw_batch_volume& bv = vols[v];
@@ -1766,6 +1880,13 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
                 for (const RecOp* o : grp)
                     if (op_length(*o) > op_length(*proto)) proto = o;
                 P.L.proto = *proto;
+                if (P.L.kind == OP_SLAB) {   // block size and shared memory of the largest slab
+                    for (const RecOp* o : grp) {
+                        const int w = slab_warps(o->slab), m = (int)slab_smem(o->slab);
+                        if (w > P.L.proto.slab.warps) P.L.proto.slab.warps = w;
+                        if (m > P.L.proto.slab.smem) P.L.proto.slab.smem = m;
+                    }
+                }
                 P.L.g.n = (int)grp.size();
                 std::vector<int> start(grp.size() + 1, 0), nbx(grp.size(), 1);
                 for (size_t q = 0; q < grp.size(); ++q) {
@@ -1785,6 +1906,7 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
                     case OP_C2R: append_payloads<C2RPass>(grp, blob); break;
                     case OP_RENDER: append_payloads<RenderOp>(grp, blob); break;
                     case OP_GRAD: append_payloads<GradOp>(grp, blob); break;
+                    case OP_SLAB: append_payloads<SlabPass>(grp, blob); break;
                     default: break;
                 }
                 blob.resize(align16(blob.size()));
@@ -1819,6 +1941,7 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
         }
     } while (0);
     g_recorder = nullptr;
+    g_slab_batch = false;
     if (s) {
         batch_free(b);
         delete b;
@@ -1912,7 +2035,7 @@ sfw_status sfw_batch_autotune(sfw_batch* b, const char* cache_path, void* stream
     sfw_status s = SFW_OK;
     for (BatchLaunch& L : b->launches) {
         const bool tunable = L.kind == OP_R2C || L.kind == OP_C2C || L.kind == OP_MUL || L.kind == OP_C2R ||
-                             L.kind == OP_RENDER || L.kind == OP_GRAD;
+                             L.kind == OP_RENDER || L.kind == OP_GRAD || L.kind == OP_SLAB;
         if (!tunable || L.g.total <= 1) continue;
         const int resident = L.g.grid;  // default chosen by the first step
         const int cand[6] = {resident, b->num_sms, 2 * b->num_sms, 4 * b->num_sms, 8 * b->num_sms, L.g.total};

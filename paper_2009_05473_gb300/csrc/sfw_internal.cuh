@@ -220,6 +220,46 @@ sfw_status launch_cert_tail(const CertTailPass& p, const void* tmap, int groups,
 // intermediate at in, boxes {4, 1, boxg, 1}; false if the driver entry point is missing.
 bool make_tail_tmap(const void* in, int n0, long long ngroups, int K, int boxg, void* tmap_out);
 
+// A blur slab pass (lengths of the blur grid, shared-memory transforms), one CTA per slab
+// of axis 0.  Head: real slab rows x cols (rows placed at [o1, o1 + rows) of the P1
+// transform, columns at [o2, o2 + cols) of P2) -> real forward along axis 2 -> forward
+// along axis 1 -> out (nslab, P1, H2) complex.  Tail: in (nslab, P1, H2) -> inverse along
+// axis 1 keeping rows [o1, o1 + m1) -> real inverse along axis 2 keeping [o2, o2 + m2) ->
+// out (nslab, m1, m2) real: stored, or the residual y - value with the criterion
+// C = 1/2 sum r^2 + lambda sum w (last-block reduction, as C2RPass).
+struct SlabPass {
+    int mode;                  // SLAB_HEAD, SLAB_STORE or SLAB_RESIDUAL
+    int nslab, P1, P2, H2;
+    int rows, cols;            // head: input slab shape
+    int o1, m1, o2, m2;        // head: o1, o2 placement; tail: kept window
+    const float* rin;          // head input (nslab, rows, cols)
+    const float2* cin;         // tail input (nslab, P1, H2)
+    float2* cout;              // head output (nslab, P1, H2)
+    float* rout;               // tail output (nslab, m1, m2); RESIDUAL: may be NULL
+    const float* y;            // RESIDUAL: observation (nslab, m1, m2)
+    double* partials;          // RESIDUAL: one double per slab
+    unsigned int* counter;
+    double* loss_out;
+    const float* w;
+    int nw, w_stride;
+    double lambda;
+    Factors fac1, fac2;        // factors of P1 and P2 (two lines per warp)
+    const float2* tw1;
+    const float2* tw2;
+    int warps;                 // warps per CTA (0: slab_warps)
+    int smem;                  // dynamic shared memory at least this (grouped launches)
+};
+enum SlabMode { SLAB_HEAD = 0, SLAB_STORE = 1, SLAB_RESIDUAL = 2 };
+struct GroupArgs;
+// Dynamic shared memory of a slab pass (0: does not fit), its warps per CTA and
+// whether it runs the (80, 96) specialisation.
+size_t slab_smem(const SlabPass& p);
+int slab_warps(const SlabPass& p);
+bool slab_specialised(const SlabPass& p);
+// One CTA per slab; with g, one grouped launch of g->n passes (g->passes) whose
+// factors and twiddles were filled when they were recorded.
+sfw_status launch_slab(const SlabPass& p, cudaStream_t st, GroupArgs* g = nullptr);
+
 // Certificate head fused in one pass (same lengths as the tail): per i0 slab, the real
 // forward transform of the residual rows along axis 2 (zero-padded n2 -> P2) and the
 // forward transform of the columns along axis 1 (n1 -> P1): r (n0, n1, n2) -> out
@@ -341,7 +381,7 @@ int grad_tiles(const GradOp& op, int* nbx);
 // While g_recorder is set on this thread, every launcher appends its op here
 // instead of launching; a batch replays the ops of all its volumes stage by stage.
 enum OpKind {
-    OP_R2C = 0, OP_C2C, OP_MUL, OP_C2R, OP_RENDER, OP_GRAD
+    OP_R2C = 0, OP_C2C, OP_MUL, OP_C2R, OP_RENDER, OP_GRAD, OP_SLAB
 };
 struct RecOp {
     OpKind kind;
@@ -351,6 +391,7 @@ struct RecOp {
     C2RPass c2r;
     RenderOp render;
     GradOp grad;
+    SlabPass slab;
 };
 struct Recorder {
     std::vector<RecOp> ops;
@@ -360,6 +401,7 @@ struct Recorder {
     sfw_status add(const C2RPass& p) { RecOp o{}; o.kind = OP_C2R; o.c2r = p; ops.push_back(o); return SFW_OK; }
     sfw_status add(const RenderOp& p) { RecOp o{}; o.kind = OP_RENDER; o.render = p; ops.push_back(o); return SFW_OK; }
     sfw_status add(const GradOp& p) { RecOp o{}; o.kind = OP_GRAD; o.grad = p; ops.push_back(o); return SFW_OK; }
+    sfw_status add(const SlabPass& p) { RecOp o{}; o.kind = OP_SLAB; o.slab = p; ops.push_back(o); return SFW_OK; }
 };
 extern thread_local Recorder* g_recorder;
 
