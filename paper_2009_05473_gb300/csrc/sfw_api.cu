@@ -314,7 +314,7 @@ static sfw_status blur_forward(const BlurGeom& g, const float* f, const void* sp
         tail.w_stride = ep.w_stride;
         tail.lambda = ep.lambda;
         if (use_slab(tail)) {
-            if (c2r_blocks_out) *c2r_blocks_out = n0;
+            if (c2r_blocks_out) *c2r_blocks_out = 2 * n0;   // two CTAs per slab
             LaunchTag lt__(tg.tail);
             return launch_slab(tail, st);
         }
@@ -976,8 +976,8 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         if ((s = plan_alloc_t(p, &p->fE, (size_t)(p->VE > Ptot ? p->VE : Ptot)))) break;
         if ((s = plan_alloc_t(p, &p->bE, (size_t)p->VE))) break;
         if ((s = plan_alloc_t(p, &p->r, (size_t)p->V))) break;
-        // one partial per residual tile (per-axis passes) or per slab (slab passes)
-        p->loss_parts_len = (int)(((long long)p->n[0] * p->n[1] + 15) / 16) + 16 + p->n[0];
+        // one partial per residual tile (per-axis passes) or two per slab (slab passes)
+        p->loss_parts_len = (int)(((long long)p->n[0] * p->n[1] + 15) / 16) + 16 + 2 * p->n[0];
         if ((s = plan_alloc_t(p, &p->loss_parts, (size_t)p->loss_parts_len))) break;
         p->grad_parts_atoms = 4096;
         if ((s = plan_alloc_t(p, &p->grad_parts, (size_t)p->grad_parts_atoms * kGradChunks * 6))) break;

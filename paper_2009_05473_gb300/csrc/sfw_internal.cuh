@@ -220,8 +220,8 @@ sfw_status launch_cert_tail(const CertTailPass& p, const void* tmap, int groups,
 // intermediate at in, boxes {4, 1, boxg, 1}; false if the driver entry point is missing.
 bool make_tail_tmap(const void* in, int n0, long long ngroups, int K, int boxg, void* tmap_out);
 
-// A blur slab pass (lengths of the blur grid, shared-memory transforms), one CTA per slab
-// of axis 0.  Head: real slab rows x cols (rows placed at [o1, o1 + rows) of the P1
+// A blur slab pass (lengths of the blur grid, shared-memory transforms), one cluster of
+// two CTAs per slab of axis 0.  Head: real slab rows x cols (rows placed at [o1, o1 + rows) of the P1
 // transform, columns at [o2, o2 + cols) of P2) -> real forward along axis 2 -> forward
 // along axis 1 -> out (nslab, P1, H2) complex.  Tail: in (nslab, P1, H2) -> inverse along
 // axis 1 keeping rows [o1, o1 + m1) -> real inverse along axis 2 keeping [o2, o2 + m2) ->
@@ -237,7 +237,7 @@ struct SlabPass {
     float2* cout;              // head output (nslab, P1, H2)
     float* rout;               // tail output (nslab, m1, m2); RESIDUAL: may be NULL
     const float* y;            // RESIDUAL: observation (nslab, m1, m2)
-    double* partials;          // RESIDUAL: one double per slab
+    double* partials;          // RESIDUAL: one double per CTA (2 nslab)
     unsigned int* counter;
     double* loss_out;
     const float* w;

@@ -65,7 +65,13 @@ def test_batch_equals_single_calls_and_graph_replay(sfw, oracle_mod, tmp_path):
         assert torch.equal(batch.grad[v], grad)
         assert torch.equal(batch.residual[v], r)
         assert batch.best_idx[v].item() == c["best_idx"].item()
-        assert batch.best_val[v].item() == c["best_val"].item()
+        # a batch records the per-axis certificate passes; a single call on a 64- or
+        # 128-point certificate grid runs the slab kernels, whose register transforms
+        # round differently from the shared-memory ones (a few FP32 ulp)
+        if plans[v].info["P_cert"][1] in (64, 128) and plans[v].info["P_cert"][2] in (64, 128):
+            assert abs(batch.best_val[v].item() - c["best_val"].item()) <= 4e-7 * abs(c["best_val"].item())
+        else:
+            assert batch.best_val[v].item() == c["best_val"].item()
     # one volume against the FP64 oracle
     v = 1
     vol = vols[v]
