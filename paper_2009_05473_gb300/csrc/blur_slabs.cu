@@ -144,13 +144,15 @@ __device__ __forceinline__ void slab_head_body(const SlabPass& p, int slab, int 
     const int nrows = max(0, min(rows, r_lo + 2 * nc) - r_lo);
     for (int j = threadIdx.x; j < L1; j += nt) TW1[j] = p.tw1[j];
     for (int j = threadIdx.x; j < L2; j += nt) TW2[j] = p.tw2[j];
-    {
+    {   // every element in flight at once (asynchronous copies)
         const float* src = p.rin + ((long long)slab * rows + r_lo) * cols;
         for (int e = threadIdx.x; e < nrows * cols; e += nt) {
             const int i = e / cols;
-            RS[i * q.NP + (e - i * cols)] = __ldg(src + e);
+            cp_async(RS + i * q.NP + (e - i * cols), src + e, 4);
         }
+        cp_async_commit();
     }
+    cp_async_wait0();
     cluster.sync();   // also: the other CTA has started before its shared memory is written
     // axis 2: two real rows per complex line; their half spectra go to the column's owner
     for (int lc0 = 2 * warp; lc0 < nc; lc0 += 2 * nwarps) {

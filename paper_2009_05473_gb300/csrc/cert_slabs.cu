@@ -266,15 +266,17 @@ __global__ void __launch_bounds__(kHeadThreads) k_cert_head(CertHeadPass p) {
     const int i0 = blockIdx.x;
     const int n1 = p.n1, n2 = p.n2;
     const int NP = n2 | 1;                       // odd row pitch of the real slab
-    {
+    {   // every element in flight at once (asynchronous copies)
         const float* src = p.r + (long long)i0 * n1 * n2;
         for (int e = threadIdx.x; e < n1 * n2; e += kHeadThreads) {
             const int i1 = e / n2;
-            RS[i1 * NP + (e - i1 * n2)] = __ldg(src + e);
+            cp_async(RS + i1 * NP + (e - i1 * n2), src + e, 4);
         }
+        cp_async_commit();
     }
     reg_twiddles<P1, kHeadThreads>(p.tw1, TW1);
     reg_twiddles<P2, kHeadThreads>(p.tw2, TW2);
+    cp_async_wait0();
     __syncthreads();
     // axis 2: rows c and c + NCH as one complex line, forward, then split the two spectra
     if (warp < NCH / 4) {

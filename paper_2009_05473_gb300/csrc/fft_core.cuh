@@ -8,6 +8,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "sfw_internal.cuh"
@@ -722,7 +723,7 @@ __device__ __forceinline__ void stage_spec_warp(const MulPass& p, int s, const l
 // [out_off, out_off + out_len) stored straight from registers.  The warp keeps
 // DEPTH spectra in flight in its own shared-memory ring (cp.async, __syncwarp).
 template <int KIND, int LL>
-__device__ __forceinline__ void mul_reg_body(const MulPass& p, int bx, int by) {
+__device__ __forceinline__ void mul_reg_items(const MulPass& p, int bx, int k0, int nspec) {
     using G = RegFFT<LL>;
     constexpr int L = LL, R1 = G::R1, T = G::T, LPW = G::LPW, D = G::DEPTH;
     constexpr int ES = SpecInfo<KIND>::bytes;
@@ -756,8 +757,6 @@ __device__ __forceinline__ void mul_reg_body(const MulPass& p, int bx, int by) {
         const long long ss = p.spec_stride * ES;
         packed = packed && a0 % CB == 0 && rs % CB == 0 && ss % CB == 0;
     }
-    const int k0 = (int)by * p.nspec;
-    const int nspec = min(p.nspec, p.ktotal - k0);
     // prime the ring: spectra k0 .. k0 + D - 2 (one commit group each)
 #pragma unroll
     for (int q = 0; q < D - 1; ++q) {
@@ -873,9 +872,33 @@ __global__ void __launch_bounds__(RegFFT<LL>::NT) k_c2c_reg_g(const C2CPass* __r
     }
 }
 
+// Tile bx of the lines, spectra [by nspec, (by + 1) nspec) of the pass.
+template <int KIND, int LL>
+__device__ __forceinline__ void mul_reg_body(const MulPass& p, int bx, int by) {
+    const int k0 = by * p.nspec;
+    mul_reg_items<KIND, LL>(p, bx, k0, min(p.nspec, p.ktotal - k0));
+}
+
 template <int KIND, int LL>
 __global__ void __launch_bounds__(RegFFT<LL>::NT) k_mul_reg(MulPass p) {
     mul_reg_body<KIND, LL>(p, blockIdx.x, blockIdx.y);
+}
+
+// Persistent form for many spectra: the (tile, spectrum) items, tile-major, are split
+// into gridDim.x equal contiguous ranges (one per resident CTA), so the work is spread
+// evenly instead of in whole waves of (tile, group) CTAs; a range runs as one piece per
+// tile it touches (one forward transform per piece).
+template <int KIND, int LL>
+__global__ void __launch_bounds__(RegFFT<LL>::NT) k_mul_reg_p(MulPass p, int ntiles) {
+    const long long total = (long long)ntiles * p.ktotal;
+    const long long lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+    for (long long it = lo; it < hi;) {
+        const int tile = (int)(it / p.ktotal), k0 = (int)(it - (long long)tile * p.ktotal);
+        const int nk = (int)min((long long)(p.ktotal - k0), hi - it);
+        mul_reg_items<KIND, LL>(p, tile, k0, nk);
+        __syncthreads();   // the twiddles and line offsets are reloaded by the next piece
+        it += nk;
+    }
 }
 
 template <int KIND, int LL>
@@ -1410,6 +1433,38 @@ sfw_status run_c2c(const C2CPass& p, cudaStream_t st, GroupArgs* g) {
     return run_either(k_c2c<8, 1, LL>, k_c2c_g<8, 1, LL>, "k_c2c", p, grid1, smem, st, g);
 }
 
+// Launch of k_mul_reg_p with one CTA per resident slot (occupancy computed once per
+// device, kernel and shared-memory size, outside any stream capture's first use).
+template <typename KernelT>
+inline sfw_status run_mul_persistent(KernelT kernel, const MulPass& p, int ntiles, size_t smem, int nt,
+                                     cudaStream_t st) {
+    SFW_TRY(prepare(kernel, smem));
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, size_t>, int> slots;
+    int dev = 0;
+    SFW_CUDA(cudaGetDevice(&dev));
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto key = std::make_tuple(dev, reinterpret_cast<const void*>(kernel), smem);
+        auto it = slots.find(key);
+        if (it != slots.end()) {
+            grid = it->second;
+        } else {
+            int sms = 1, per = 1;
+            SFW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem));
+            grid = (per < 1 ? 1 : per) * sms;
+            slots[key] = grid;
+        }
+    }
+    const long long items = (long long)ntiles * p.ktotal;
+    if (items < grid) grid = (int)items;
+    if (grid <= 0) return SFW_OK;
+    SFW_LAUNCH(st, "k_mul_reg", kernel<<<grid, nt, smem, st>>>(p, ntiles));
+    return launch_check("k_mul_reg");
+}
+
 template <int LL>
 sfw_status run_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
     if (!g && p.nlines <= 0) return SFW_OK;
@@ -1422,6 +1477,14 @@ sfw_status run_mul(const MulPass& p, cudaStream_t st, GroupArgs* g) {
         using G = RegFFT<LL>;
         const size_t smem = sizeof(float2) * ((size_t)G::TWN + (size_t)G::NW * G::LPW * G::XS) +
                             (size_t)G::NW * G::DEPTH * LL * G::LPW * es;
+        if (!g && p.ktotal > 1) {   // many spectra: persistent, evenly split items
+            switch (p.spec_kind) {
+                case SPEC_C64: return run_mul_persistent(k_mul_reg_p<SPEC_C64, LL>, p, nbx, smem, G::NT, st);
+                case SPEC_R32: return run_mul_persistent(k_mul_reg_p<SPEC_R32, LL>, p, nbx, smem, G::NT, st);
+                case SPEC_CBF16: return run_mul_persistent(k_mul_reg_p<SPEC_CBF16, LL>, p, nbx, smem, G::NT, st);
+                default: return run_mul_persistent(k_mul_reg_p<SPEC_RBF16, LL>, p, nbx, smem, G::NT, st);
+            }
+        }
 #define SFW_MULR(KK) return run_either(k_mul_reg<KK, LL>, k_mul_reg_g<KK, LL>, "k_mul_reg", p, grid1, smem, st, g, G::NT)
         switch (p.spec_kind) {
             case SPEC_C64: SFW_MULR(SPEC_C64);
