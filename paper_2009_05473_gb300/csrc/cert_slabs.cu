@@ -1,16 +1,15 @@
 // The grid certificate's passes along axes 1 and 2 (Eq. 5; Algorithm 1 step 1) done
-// per i0 slab, so the slab stays in shared memory between the two axes: the head (one
-// CTA per slab; forward: real transform of the residual's rows along axis 2, then the
-// columns along axis 1) and the tail (per (i0, kernel k) item, the items split evenly
-// over the resident CTAs: the columns' inverse along axis 1, the rows' real inverse
-// along axis 2, and the running max / argmax over the CTA's kernels of the slab).
+// per i0 slab, one CTA per slab, so the slab stays in shared memory between the two
+// axes: the head (forward: real transform of the residual's rows along axis 2, then
+// the columns along axis 1) and the tail (per kernel k: the columns' inverse along
+// axis 1, the rows' real inverse along axis 2, and the running max / argmax over the
+// CTA's kernels).
 //
 // Both use the register-resident transform (lengths 64 / 128).  Columns: each warp
 // transforms 4 columns 8 apart, so that the two columns a half-warp reads sit in
 // distinct banks (the complex row pitch H2 is 1 mod 16 float2).  Rows: complex line c
 // carries real rows c (real part) and c + rows/2 (imaginary part).  The tail's slab
-// in[k][i0] (P1 x H2 complex) arrives by TMA box copies (line-group-major layout) or,
-// without a tensor map, by 16-byte cp.async (contiguous layout); the head's
+// in[k][i0] (P1 x H2 complex, contiguous) arrives by 16-byte cp.async; the head's
 // result leaves by one bulk copy from shared to global memory.  Neither intermediate
 // of the per-axis form, (n0, n1, H2) or (K, n0, n1, H2), is written.
 #include <map>
@@ -63,10 +62,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase) {
     return false;
 }
 
-// The (i0, k) items, i0-major, are split into gridDim.x equal contiguous ranges (one
-// per resident CTA, so no CTA waits for a second wave); a range runs as one piece per
-// slab i0 it touches: the running max / argmax over the piece's kernels stays in
-// registers and is merged into the per-voxel keys when the piece ends.
 template <int P1, int P2, bool TMA>
 __global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p,
                                                             const __grid_constant__ CUtensorMap tmap) {
@@ -93,134 +88,124 @@ __global__ void __launch_bounds__(kTailThreads) k_cert_tail(CertTailPass p,
     }
     reg_twiddles<P1, kTailThreads>(p.tw1, TW1);
     reg_twiddles<P2, kTailThreads>(p.tw2, TW2);
+    const int i0 = blockIdx.x;
+    const int k0 = (int)blockIdx.y * p.nspec;
+    const int nk = min(p.nspec, p.ktotal - k0);
 
     // axis-2 task of this warp: complex line c = warp + (NC / 4) li, rows c and c + NC
     const bool has2 = warp < G::NT2;
     const int cA = warp + (G::NC / 4) * li, cB = cA + G::NC;
-    unsigned long long best = 0ull;
+    float mx[2][MH];
+    int ak[2][MH];
+#pragma unroll
+    for (int m = 0; m < MH; ++m) {
+        mx[0][m] = mx[1][m] = -INFINITY;
+        ak[0][m] = ak[1][m] = 0;
+    }
     bool saw_nan = false;
-    bool late = false;
-    int nload = 0;   // slab copies issued so far (the barrier's phase parity)
 
-    const long long total = (long long)p.n0 * p.ktotal;
-    const long long lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
     __syncthreads();
-    for (long long item = lo; item < hi && !late;) {
-        const int i0 = (int)(item / p.ktotal);
-        const int k0 = (int)(item - (long long)i0 * p.ktotal);
-        const int nk = (int)min((long long)(p.ktotal - k0), hi - item);
-        item += nk;
-        float mx[2][MH];
-        int ak[2][MH];
-#pragma unroll
-        for (int m = 0; m < MH; ++m) {
-            mx[0][m] = mx[1][m] = -INFINITY;
-            ak[0][m] = ak[1][m] = 0;
-        }
-        for (int s = 0; s < nk; ++s) {
-            const int kk = k0 + s;
-            if constexpr (TMA) {
-                // the slab's line groups: nbox box copies {4, 1, boxg, 1} at (0, i0, b boxg, kk)
-                const unsigned bar = smem_u32(&s_bar);
-                const unsigned phase = (unsigned)(nload & 1);
-                ++nload;
-                if (threadIdx.x == 0) {
-                    const unsigned bytes = (unsigned)(p.nbox * p.boxg * 32);
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
-                                 :: "r"(bar), "r"(bytes) : "memory");
-                    for (int b = 0; b < p.nbox; ++b)
-                        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                                     " [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
-                                     :: "r"(smem_u32(S + b * p.boxg * 4)), "l"(&tmap), "r"(0), "r"(i0),
-                                        "r"(b * p.boxg), "r"(kk), "r"(bar)
-                                     : "memory");
-                }
-                if (!mbar_wait(bar, phase)) s_late = 1;
-                __syncthreads();
-                if (s_late) {
-                    // the copies did not land in time: flag it, wait once more for them, stop
-                    if (threadIdx.x == 0) atomicExch(p.err, 1);
-                    mbar_wait(bar, phase);
-                    late = true;
-                    break;
-                }
-            } else {
-                const float2* src = p.in + ((long long)kk * p.n0 + i0) * G::SLAB;
-                for (int e = threadIdx.x; e < G::SLAB / 2; e += kTailThreads) cp_async16(S + 2 * e, src + 2 * e);
-                cp_async_commit();
-                cp_async_wait0();
-                __syncthreads();
+    for (int s = 0; s < nk; ++s) {
+        const int kk = k0 + s;
+        if constexpr (TMA) {
+            // the slab's line groups: nbox box copies {4, 1, boxg, 1} at (0, i0, b boxg, kk)
+            const unsigned bar = smem_u32(&s_bar);
+            if (threadIdx.x == 0) {
+                const unsigned bytes = (unsigned)(p.nbox * p.boxg * 32);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                             :: "r"(bar), "r"(bytes) : "memory");
+                for (int b = 0; b < p.nbox; ++b)
+                    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+                                 :: "r"(smem_u32(S + b * p.boxg * 4)), "l"(&tmap), "r"(0), "r"(i0),
+                                    "r"(b * p.boxg), "r"(kk), "r"(bar)
+                                 : "memory");
             }
-            // axis 1: columns (P2 / 2 of them in groups of 32, then the last one, P2 / 2)
-            for (int task = warp; task < G::NT1; task += kTailWarps) {
-                const int main_tasks = G::NT1 - 1;
-                const int col = task < main_tasks ? (task >> 3) * 32 + (task & 7) + 8 * li : P2 / 2;
-                const bool cv = task < main_tasks || li == 0;
-                float2 v[R1a];
-#pragma unroll
-                for (int m = 0; m < R1a; ++m) v[m] = cv ? S[(t + 8 * m) * H2 + col] : make_float2(0.f, 0.f);
-                reg_fft<P1, 1>(v, TW1, xl, t);
-                if (cv) {
-#pragma unroll
-                    for (int m = 0; m < R1a / 2; ++m) S[(t + 8 * m) * H2 + col] = v[m];
-                }
-            }
+            if (!mbar_wait(bar, (unsigned)(s & 1))) s_late = 1;
             __syncthreads();
-            // axis 2: real inverse of rows cA (real part) and cB (imaginary part)
-            if (has2) {
-                const float2* ra = S + cA * H2;
-                const float2* rb = S + cB * H2;
-                float2 v[R1b];
+            if (s_late) {
+                // the copies did not land in time: flag it, wait once more for them, stop
+                if (threadIdx.x == 0) atomicExch(p.err, 1);
+                mbar_wait(bar, (unsigned)(s & 1));
+                break;
+            }
+        } else {
+            const float2* src = p.in + ((long long)kk * p.n0 + i0) * G::SLAB;
+            for (int e = threadIdx.x; e < G::SLAB / 2; e += kTailThreads) cp_async16(S + 2 * e, src + 2 * e);
+            cp_async_commit();
+            cp_async_wait0();
+            __syncthreads();
+        }
+        // axis 1: columns (P2 / 2 of them in groups of 32, then the last one, P2 / 2)
+        for (int task = warp; task < G::NT1; task += kTailWarps) {
+            const int main_tasks = G::NT1 - 1;
+            const int col = task < main_tasks ? (task >> 3) * 32 + (task & 7) + 8 * li : P2 / 2;
+            const bool cv = task < main_tasks || li == 0;
+            float2 v[R1a];
 #pragma unroll
-                for (int m = 0; m < R1b; ++m) {
-                    const int j = t + 8 * m;
-                    const bool lo2 = 2 * j <= P2;
-                    const int k = lo2 ? j : P2 - j;
-                    const float2 a = ra[k], b = rb[k];
-                    v[m] = lo2 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
-                }
-                reg_fft<P2, 1>(v, TW2, xl, t);
+            for (int m = 0; m < R1a; ++m) v[m] = cv ? S[(t + 8 * m) * H2 + col] : make_float2(0.f, 0.f);
+            reg_fft<P1, 1>(v, TW1, xl, t);
+            if (cv) {
 #pragma unroll
-                for (int m = 0; m < MH; ++m) {
-                    const int i2 = t + 8 * m;
-                    if (i2 < p.n2) {
+                for (int m = 0; m < R1a / 2; ++m) S[(t + 8 * m) * H2 + col] = v[m];
+            }
+        }
+        __syncthreads();
+        // axis 2: real inverse of rows cA (real part) and cB (imaginary part)
+        if (has2) {
+            const float2* ra = S + cA * H2;
+            const float2* rb = S + cB * H2;
+            float2 v[R1b];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int row = h ? cB : cA;
-                            if (row < p.n1) {
-                                const float val = (h ? v[m].y : v[m].x) * p.scale;
-                                if (p.eta_out)
-                                    p.eta_out[(long long)kk * p.V + ((long long)i0 * p.n1 + row) * p.n2 + i2] = val;
-                                saw_nan = saw_nan || val != val;
-                                if (val > mx[h][m]) {
-                                    mx[h][m] = val;
-                                    ak[h][m] = kk;
-                                }
+            for (int m = 0; m < R1b; ++m) {
+                const int j = t + 8 * m;
+                const bool lo = 2 * j <= P2;
+                const int k = lo ? j : P2 - j;
+                const float2 a = ra[k], b = rb[k];
+                v[m] = lo ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, b.x - a.y);
+            }
+            reg_fft<P2, 1>(v, TW2, xl, t);
+#pragma unroll
+            for (int m = 0; m < MH; ++m) {
+                const int i2 = t + 8 * m;
+                if (i2 < p.n2) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = h ? cB : cA;
+                        if (row < p.n1) {
+                            const float val = (h ? v[m].y : v[m].x) * p.scale;
+                            if (p.eta_out)
+                                p.eta_out[(long long)kk * p.V + ((long long)i0 * p.n1 + row) * p.n2 + i2] = val;
+                            saw_nan = saw_nan || val != val;
+                            if (val > mx[h][m]) {
+                                mx[h][m] = val;
+                                ak[h][m] = kk;
                             }
                         }
                     }
                 }
             }
-            // the slab is reloaded for the next kernel: order this kernel's shared-memory
-            // accesses before the copy engine's writes
-            if constexpr (TMA) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncthreads();
         }
-        // merge the piece's maxima into the per-voxel keys
-        if (has2) {
+        // the slab is reloaded for the next kernel: order this kernel's shared-memory
+        // accesses before the copy engine's writes
+        if constexpr (TMA) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+    }
+
+    unsigned long long best = 0ull;
+    if (has2 && nk > 0) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = h ? cB : cA;
-                if (row >= p.n1) continue;
+        for (int h = 0; h < 2; ++h) {
+            const int row = h ? cB : cA;
+            if (row >= p.n1) continue;
 #pragma unroll
-                for (int m = 0; m < MH; ++m) {
-                    const int i2 = t + 8 * m;
-                    if (i2 < p.n2) {
-                        const long long o = ((long long)i0 * p.n1 + row) * p.n2 + i2;
-                        const unsigned long long key = candidate_key(mx[h][m], (unsigned long long)ak[h][m] * p.V + o);
-                        if (p.vox_key) atomicMax(p.vox_key + o, key);
-                        if (key > best) best = key;
-                    }
+            for (int m = 0; m < MH; ++m) {
+                const int i2 = t + 8 * m;
+                if (i2 < p.n2) {
+                    const long long o = ((long long)i0 * p.n1 + row) * p.n2 + i2;
+                    const unsigned long long key = candidate_key(mx[h][m], (unsigned long long)ak[h][m] * p.V + o);
+                    if (p.vox_key) atomicMax(p.vox_key + o, key);
+                    if (key > best) best = key;
                 }
             }
         }
@@ -376,35 +361,45 @@ bool cert_tail_supported(int P1, int P2, int n1, int n2) {
 }
 
 template <int P1, int P2, bool TMA>
-static sfw_status run_tail(CertTailPass p, const CUtensorMap& tm, cudaStream_t st) {
+static sfw_status run_tail(CertTailPass p, const CUtensorMap& tm, int groups, cudaStream_t st) {
     using G = TailGeom<P1, P2>;
     const size_t smem = G::smem(TMA ? G::cap(p.boxg, p.nbox) : G::cap(0, 0));
     auto kern = k_cert_tail<P1, P2, TMA>;
     SFW_TRY(prepare(kern, smem));
-    // one CTA per resident slot (computed once per device and geometry), at most one per item
     int dev = 0;
     SFW_CUDA(cudaGetDevice(&dev));
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, size_t>, int> slots_of;
-    const auto key = std::make_tuple(dev, P1, P2, (int)TMA, smem);
-    int slots = 0;
-    {
+    static std::map<std::tuple<int, int, int, int, int, int>, int> chosen;  // (dev, P1, P2, TMA, n0, K) -> groups
+    const auto key = std::make_tuple(dev, P1, P2, (int)TMA, p.n0, p.ktotal);
+    if (groups <= 0) {
         std::lock_guard<std::mutex> lk(mu);
-        auto it = slots_of.find(key);
-        if (it != slots_of.end()) slots = it->second;
+        auto it = chosen.find(key);
+        if (it != chosen.end()) groups = it->second;
     }
-    if (slots <= 0) {
+    if (groups <= 0) {
+        // kernels per CTA: the fewest rounds of resident CTAs, then the most kernels per CTA
         int sms = 1, per = 1;
         SFW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         SFW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTailThreads, smem));
-        slots = (per > 0 ? per : 1) * sms;
+        const long long slots = (long long)(per > 0 ? per : 1) * sms;
+        long long best_cost = -1;
+        for (int ns = 1; ns <= p.ktotal; ++ns) {
+            const long long g = (p.ktotal + ns - 1) / ns;
+            const long long rounds = (p.n0 * g + slots - 1) / slots;
+            const long long cost = rounds * ns;
+            if (best_cost < 0 || cost <= best_cost) {
+                best_cost = cost;
+                groups = (int)g;
+            }
+        }
         std::lock_guard<std::mutex> lk(mu);
-        slots_of[key] = slots;
+        chosen[key] = groups;
     }
-    const long long items = (long long)p.n0 * p.ktotal;
-    const int nblocks = (int)(items < slots ? items : slots);
-    p.ntiles = nblocks;
-    SFW_LAUNCH(st, "k_cert_tail", (kern<<<nblocks, kTailThreads, smem, st>>>(p, tm)));
+    p.nspec = (p.ktotal + groups - 1) / groups;
+    groups = (p.ktotal + p.nspec - 1) / p.nspec;
+    p.ntiles = p.n0 * groups;
+    const dim3 grid((unsigned)p.n0, (unsigned)groups);
+    SFW_LAUNCH(st, "k_cert_tail", (kern<<<grid, kTailThreads, smem, st>>>(p, tm)));
     return launch_check("k_cert_tail");
 }
 
@@ -430,7 +425,7 @@ bool make_tail_tmap(const void* in, int n0, long long ngroups, int K, int boxg, 
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-sfw_status launch_cert_tail(const CertTailPass& p0, const void* tmap, cudaStream_t st) {
+sfw_status launch_cert_tail(const CertTailPass& p0, const void* tmap, int groups, cudaStream_t st) {
     CertTailPass p = p0;
     if (!cert_tail_supported(p.P1, p.P2, p.n1, p.n2) || p.H2 != p.P2 / 2 + 1)
         return fail(SFW_ERR_SHAPE, "fused certificate tail: unsupported lengths %d x %d", p.P1, p.P2);
@@ -443,7 +438,7 @@ sfw_status launch_cert_tail(const CertTailPass& p0, const void* tmap, cudaStream
     CUtensorMap tm;
     if (tmap) memcpy(&tm, tmap, sizeof(tm));
     else memset(&tm, 0, sizeof(tm));
-#define SFW_TAIL(A, B) return tmap ? run_tail<A, B, true>(p, tm, st) : run_tail<A, B, false>(p, tm, st)
+#define SFW_TAIL(A, B) return tmap ? run_tail<A, B, true>(p, tm, groups, st) : run_tail<A, B, false>(p, tm, groups, st)
     if (p.P1 == 64 && p.P2 == 64) SFW_TAIL(64, 64);
     if (p.P1 == 64) SFW_TAIL(64, 128);
     if (p.P2 == 64) SFW_TAIL(128, 64);

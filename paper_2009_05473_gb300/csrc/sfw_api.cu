@@ -1390,7 +1390,7 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
         t.nbox = p->tail_nbox;
         t.err = p->tail_err;
         LaunchTag lt__(kCertTailTag);
-        SFW_TRY(launch_cert_tail(t, p->tail_tma ? p->tail_tmap : nullptr, st));
+        SFW_TRY(launch_cert_tail(t, p->tail_tma ? p->tail_tmap : nullptr, 0, st));
     } else {
         {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
             C2CPass q;

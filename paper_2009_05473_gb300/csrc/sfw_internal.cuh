@@ -188,18 +188,17 @@ struct C2RPass {
     int64_t* best_idx;
 };
 
-// Certificate tail fused in one pass (lengths P1, P2 in {64, 128}): the (i0, k) items
-// are split evenly over the resident CTAs; per item the slab in[k][i0] (P1 x H2
-// complex) -> inverse along axis 1 (keep n1 rows) -> real inverse along axis 2 (keep
-// n2) -> running max / argmax over the CTA's kernels of that slab, candidate keys as
-// in C2RPass.
+// Certificate tail fused in one pass (lengths P1 in {64, 128}, P2 in {64, 128, 256}):
+// per (i0, kernel group) CTA and kernel k, the slab in[k][i0] (P1 x H2 complex,
+// contiguous) -> inverse along axis 1 (keep n1 rows) -> real inverse along axis 2
+// (keep n2) -> running max / argmax over the group, candidate keys as in C2RPass.
 struct CertTailPass {
     const float2* in;           // (K, n0, P1, H2) complex; with a tensor map, line-group-major
                                 // [k][l / 4][i0][l mod 4], l = p1 H2 + h2 (read by TMA)
     int boxg, nbox;             // TMA: line groups per box copy, box copies per slab
     int* err;                   // TMA: set to 1 if a slab's copies did not complete in time
     int n0, n1, n2, P1, P2, H2;
-    int ktotal;                 // kernels
+    int ktotal, nspec;          // kernels; kernels per CTA (grid.y = groups)
     const float2* tw1;          // twiddles of P1 (register factorisation)
     const float2* tw2;          // twiddles of P2
     float scale;                // 1 / lambda
@@ -216,7 +215,7 @@ struct CertTailPass {
 bool cert_tail_supported(int P1, int P2, int n1, int n2);
 // tmap: NULL (contiguous slabs, cp.async) or the 4-D tensor map of make_tail_tmap
 // (line-group-major slabs, TMA box copies), an opaque 128-byte CUtensorMap.
-sfw_status launch_cert_tail(const CertTailPass& p, const void* tmap, cudaStream_t st);
+sfw_status launch_cert_tail(const CertTailPass& p, const void* tmap, int groups, cudaStream_t st);
 // Encode the tensor map {4, n0, P1 H2 / 4, K} (8-byte elements) of the line-group-major
 // intermediate at in, boxes {4, 1, boxg, 1}; false if the driver entry point is missing.
 bool make_tail_tmap(const void* in, int n0, long long ngroups, int K, int boxg, void* tmap_out);
