@@ -64,6 +64,27 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max_s: float) -> float:
+    """Units all ranks processed (each rank the same work: replicas) over the slowest rank's time."""
+    return world * units_per_rank / t_max_s
+
+
+def replica_volume(workload: str, rank: int):
+    """The volume a rank solves: every replica its own seeded synthetic volume (seed = rank)."""
+    return sfw_inputs.WORKLOADS[workload](seed=rank)
+
+
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -232,7 +253,7 @@ def run_ours(args):
         dist.barrier()
 
     # each replica solves its own synthetic volume (seed = rank): replicas only
-    vol = sfw_inputs.WORKLOADS[args.workload](seed=rank)
+    vol = replica_volume(args.workload, rank)
     plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
     V, K = vol.V, plan.K
     dev = torch.device("cuda", local_rank)
@@ -318,14 +339,9 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
     t_ms = float(np.sum(step_ms))
     gpu_launches = kernels_per_step * args.steps
-    if world > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_ms
+    t_max = max_over_ranks(t_ms, dev)
     cands = V * K
-    value = world * args.steps * cands / (t_max / 1e3)
+    value = whole_job_rate(args.steps * cands, world, t_max / 1e3)
 
     # roofline of the dominant kernel, timed inside the timed region
     tag = dom_tag
@@ -363,11 +379,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if i >= 3:
             e2e_t += time.perf_counter() - t0
-    e2e_value = world * args.e2e_steps * cands / e2e_t if world == 1 else None
-    if world > 1:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_value = world * args.e2e_steps * cands / float(tt.item())
+    e2e_value = whole_job_rate(args.e2e_steps * cands, world, max_over_ranks(e2e_t, dev))
 
     # the sliding step's loss + gradient alone (the evaluation BFGS repeats in step 4 of
     # Algorithm 1): its own graph, replayed with the L2 flushed in between
@@ -393,7 +405,7 @@ def run_ours(args):
         e1.record()
         e1.synchronize()
         s_ms += e0.elapsed_time(e1)
-    slide_evals_per_s = world * n_slide / (s_ms / 1e3)
+    slide_evals_per_s = whole_job_rate(n_slide, world, max_over_ranks(s_ms, dev) / 1e3)
     del sgraph
 
     # outer iterations of Algorithms 1 and 2 on the GPU path (configurations 1 and 2)
@@ -425,7 +437,7 @@ def run_ours(args):
                        "atoms": vol.N, "kernels": K, "candidates_per_step": cands,
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                        "timing": "CUDA graph replay per step, CUDA events per step"},
-            "steps_per_s": world * args.steps / (t_max / 1e3),
+            "steps_per_s": whole_job_rate(args.steps, world, t_max / 1e3),
             "slide_evals_per_s": slide_evals_per_s,
             "sfw_outer": outer,
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
