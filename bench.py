@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-solver", action="store_true",
                     help="skip the outer SFW/BSFW iteration rates (GPU solves on 32^3 and 64^3)")
     ap.add_argument("--seeds", type=int, default=5, help="fig2_sfw_vs_bsfw: seeds per atom count")
+    ap.add_argument("--clock-log", default=os.path.join(ROOT, "bench_logs"),
+                    help="directory for the raw nvidia-smi clock samples (clocks_rank<i>.csv)")
     return ap.parse_args()
 
 
@@ -94,10 +96,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -319,7 +321,7 @@ def run_ours(args):
 
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local_rank) as clocks:
+    with ClockSampler(local_rank, args.clock_log) as clocks:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -583,7 +585,7 @@ def run_batch(args):
     steps = min(args.steps, 200)
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    with ClockSampler(local_rank) as clocks:
+    with ClockSampler(local_rank, args.clock_log) as clocks:
         for i in range(steps):
             flush.fill_(float(i))
             ev_s[i].record()

@@ -77,3 +77,21 @@ def test_traffic_record_matches_sources_or_is_ignored(tag):
         assert got == rec["bytes_per_launch"][tag]
     else:
         assert got is None
+
+
+def test_clock_summary_parses_samples_and_reasons(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0, str(tmp_path))
+    assert c.path == str(tmp_path / "clocks_rank0.csv")
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2040, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1100.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    c.proc = object()          # as if nvidia-smi had run
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.proc = None
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
