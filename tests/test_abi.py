@@ -61,3 +61,22 @@ def test_host_argument_checks_need_no_gpu(built):
     with pytest.raises(_abi.SfwError):
         _abi.sfw_slide_loss_grad(0, 0, _abi.Atoms(), 1.0, 0, 0, 0, 0)
     assert _abi.sfw_launch_count() == 0
+
+
+def test_no_cpu_fallback():
+    """Without a GPU the product path refuses to run (there is no CPU path), and without the
+    built library the binding raises instead of computing anything."""
+    import numpy as np
+    import torch
+    import paper_2009_05473_gb300 as sfw
+    from paper_2009_05473_gb300 import _abi
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError, match="no CPU path"):
+            sfw.Plan((8, 8, 8), (1, 1, 1), np.full((3, 3, 3), 1.0 / 27, np.float32))
+    saved_path, saved_lib = _abi.LIB_PATH, _abi._lib
+    try:
+        _abi.LIB_PATH, _abi._lib = os.path.join(ROOT, "no_such_dir", "libsfw.so"), None
+        with pytest.raises(RuntimeError, match="libsfw.so not found"):
+            _abi.lib()
+    finally:
+        _abi.LIB_PATH, _abi._lib = saved_path, saved_lib
