@@ -104,3 +104,26 @@ def test_host_loop_matches_oracle_algorithm(oracle_mod, host_solver, boosted):
     # every outer iteration but the last added an atom whose certificate exceeded 1 + tau
     assert all(h["eta_max"] > 1.0 for h in out["history"][:-1])
     assert out["history"][-1]["eta_max"] <= 1.0 + 1e-4
+
+
+def test_lambda_path_host_logic(oracle_mod, host_solver):
+    """lambda_max is step 1 of Algorithm 1 on y at lambda = 1 (the oracle's own step 1 gives
+    the same value); above it the measure stays empty; along decreasing lambda each warm-started
+    solve ends with the certificate at most 1 + tau and a criterion of its own lambda."""
+    vol, y, _ = _case(oracle_mod)
+    plan = _OraclePlan(oracle_mod, vol)
+    yt = torch.tensor(y)
+    lmax = host_solver.lambda_max(plan, yt)
+    _, eta_ref, _ = oracle_mod.oracle._certificate_max(vol.n, vol.R, vol.psf, y, np.zeros((0, 5)), np.zeros(0), 1.0,
+                                                plan.kernels, True)
+    assert abs(lmax - eta_ref) <= 1e-6 * eta_ref
+    path = host_solver.lambda_path(plan, yt, fractions=(1.01, 0.3, 0.15), boosted=False)
+    assert [p["fraction"] for p in path] == [1.01, 0.3, 0.15]
+    assert path[0]["w"].size == 0
+    assert path[1]["w"].size >= 1 and path[2]["w"].size >= path[1]["w"].size
+    for p in path:
+        assert p["history"][-1]["eta_max"] <= 1.0 + 1e-4
+        th = p["thetas"]
+        C = oracle_mod.criterion(vol.n, vol.R, vol.psf, y, th[:, :3], th[:, 3], th[:, 4], p["w"], p["lambda"],
+                                 fft=True)
+        assert abs(p["C"] - C) <= 1e-9 * max(1.0, abs(C))
