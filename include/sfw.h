@@ -268,7 +268,7 @@ sfw_status sfw_step(sfw_plan* plan, const float* y, const sfw_atoms* atoms, doub
  * replays); sfw_profile_stop ends recording (collecting once if collect was
  * never called) and writes a JSON object {"tag": [launches, total_ms], ...}
  * into json (host, len bytes, NUL-terminated).  Tags name the pass of the hot
- * path (e.g. "cert_axis0", "blur_c2r", "k_atom_grad").  SFW_ERR_ARG if json
+ * path (e.g. "cert_axis0", "blur_tail", "k_atom_grad").  SFW_ERR_ARG if json
  * is too small or launches were dropped (pool full). */
 sfw_status sfw_profile_start(int max_launches, const char* only_tag);
 sfw_status sfw_profile_collect(void);
