@@ -95,3 +95,18 @@ def test_clock_summary_parses_samples_and_reasons(tmp_path):
     assert s["reasons"] == ["sw_power_cap"]
     c.proc = None
     assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_reference_arm_bounds_many_steps():
+    """With more steps than whole oracle steps fit in the time budget, each step is a sample
+    of grid candidates evaluated by the oracle's direct sums, and the run stays bounded."""
+    import time
+    t0 = time.perf_counter()
+    p = _run({"SFW_REF_BUDGET_S": "2"}, "--impl", "reference", "--workload", "vol32_iso9_n3_k3",
+             "--steps", "400", "--warmup", "3")
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert time.perf_counter() - t0 < 60
+    rec = json.loads([l for l in p.stdout.splitlines() if l.startswith("{")][0])
+    assert rec["steps"] == 400 and rec["value"] > 0
+    assert rec["config"]["candidates_per_step"] >= 1
+    assert "direct sums" in rec["cpu_baseline"]["sample"]
