@@ -1690,19 +1690,6 @@ void append_payloads(const std::vector<const RecOp*>& ops, std::vector<unsigned 
     }
 }
 
-size_t payload_size(OpKind k) {
-    switch (k) {
-        case OP_R2C: return sizeof(R2CPass);
-        case OP_C2C: return sizeof(C2CPass);
-        case OP_MUL: return sizeof(MulPass);
-        case OP_C2R: return sizeof(C2RPass);
-        case OP_RENDER: return sizeof(RenderOp);
-        case OP_GRAD: return sizeof(GradOp);
-        case OP_SLAB: return sizeof(SlabPass);
-        default: return 0;
-    }
-}
-
 }  // namespace
 
 struct sfw_batch {
