@@ -34,7 +34,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-from typing import Callable, Dict, List, Optional, Sequence, Tuple
+from typing import Callable, Dict, List, Sequence, Tuple
 
 import numpy as np
 import scipy.fft as sfft
