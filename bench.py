@@ -1,25 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the sliding Frank-Wolfe hot path on one GB300 per rank.
 
-One step = one SFW iteration's data-parallel hot path on the 64^3 workload
-(PSF sigma (1.5, 1.5, 3) on 15x15x31, N = 10 atoms, certificate grid of 5 sigma
-x 3 d = 15 kernels):
+Headline (default workload vol128_aniso_n30_k32, the 'precision' configuration: 128^3,
+PSF sigma (1.5, 1.5, 3) on 15x15x31, N = 30 atoms, grid 8 sigma x 4 d = 32 kernels,
+bf16 kernel-family table).  One step = one SFW iteration's data-parallel hot path:
   1. sliding-step loss and adjoint gradient at the current atoms (render on E,
      blur, residual + loss, transposed blur, per-atom adjoint sums);
-  2. grid certificate of the new residual over all voxels x 15 kernels, with
-     the fused device argmax (the seed of the next local ascent).
-Metric: eta-grid candidates/s = V K / step time.  Also reported: steps/s; the
-sliding step's loss + gradient evaluations/s (its own replayed graph); the outer
-iterations/s of Algorithms 1 and 2 on the GPU path for the 32^3 and 64^3
-configurations (`sfw_outer`, skipped with --no-solver).
-`--workload batch64_uneven`: 64 uneven volumes stepped as one batch.
-`--workload fig2_sfw_vs_bsfw`: SFW against BSFW (time to stop, final criterion) on
-64^3 volumes with 4/6/8 atoms, a synthetic analogue of the paper's Fig. 2.
+  2. grid certificate of the new residual over all voxels x 32 kernels on the bf16
+     table, the top-64 voxels re-scored in FP32 by direct sums (the seed of the
+     next local ascent).
+Metric: eta-grid candidates/s = V K / step time.  Also in the line:
+  vs_plain_fp32  the same step through the plain FP32 route (direct sums, no
+                 transform) and the speed-up, with the routes' certificate differences;
+  slide          sliding loss + gradient evaluations/s (its own replayed graph) on this
+                 volume and on the 256x256x64, N = 100 workload, against the plain route;
+  secondary      the 64^3 workload's sfw_step (certificate on a second stream);
+  sfw_outer      outer iterations/s of Algorithms 1 and 2 on the 32^3 and 64^3 volumes;
+  batch          the 64-volume uneven batch (grouped launches, one graph);
+  e2e            the headline through the public API with host buffers and copies;
+  roofline       the dominant kernel's algorithmic bytes / its event-timed duration;
+  cpu_baseline   the FP64 oracle on a bounded sample, on the host cores.
+`--workload batch64_uneven`: the batch alone.  `--workload fig2_sfw_vs_bsfw`: SFW
+against BSFW (time to stop, final criterion), a synthetic analogue of the paper's Fig. 2.
 
 The timed region replays a CUDA graph of the step; L2 (129 MB) is flushed by a
 256 MB write between steps, outside the per-step CUDA events.  The library
-records graph event nodes around each kernel, so every kernel's duration is
-measured inside the timed region (roofline of the dominant kernel).
+records graph event nodes around the dominant kernel, so its duration is
+measured inside the timed region.
 `--impl reference` times the FP64 CPU oracle on the same workload.
 """
 
@@ -40,7 +47,9 @@ sys.path.insert(0, ROOT)
 
 import sfw_inputs  # noqa: E402
 
-WORKLOAD = "vol64_aniso_n10_k15"
+WORKLOAD = "vol128_aniso_n30_k32"
+# workloads of the 'precision' configuration: bf16 kernel-family table, top-64 FP32 re-score
+PRECISION_WORKLOADS = ("vol128_aniso_n30_k32",)
 FLUSH_BYTES = 256 << 20
 
 
@@ -55,10 +64,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true",
                     help="skip the outer SFW/BSFW iteration rates (GPU solves on 32^3 and 64^3)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 (direct-sum) route")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 64^3 sfw_step line")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume uneven batch line")
     ap.add_argument("--seeds", type=int, default=5, help="fig2_sfw_vs_bsfw: seeds per atom count")
     ap.add_argument("--clock-log", default=os.path.join(ROOT, "bench_logs"),
                     help="directory for the raw nvidia-smi clock samples (clocks_rank<i>.csv)")
     return ap.parse_args()
+
+
+def metric_name(workload: str) -> str:
+    """The headline metric of a workload's step (both arms print the same name)."""
+    extra = " + top-64 FP32 re-score" if workload in PRECISION_WORKLOADS else ""
+    return f"eta-grid candidates/s (grid certificate + argmax{extra} + sliding loss/grad per step)"
 
 
 def dist_env():
@@ -194,9 +212,9 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(tag: str):
-    """DRAM bytes per launch of `tag` from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+def ncu_traffic(tag: str, workload: str = WORKLOAD):
+    """DRAM bytes per launch of `tag` on `workload` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
@@ -204,7 +222,7 @@ def ncu_traffic(tag: str):
         rec = json.load(open(path))
     except ValueError:
         return None
-    if rec.get("source_digest") != source_digest() or rec.get("workload") != WORKLOAD:
+    if rec.get("source_digest") != source_digest() or rec.get("workload") != workload:
         return None
     return rec.get("bytes_per_launch", {}).get(tag)
 
@@ -230,6 +248,13 @@ def observe_on_device(sfw, plan, vol, dev):
     return y, 0.05 * float(c0["best_val"].item())
 
 
+def current_estimate(sfw, vol, dev, seed):
+    """The iterate of a sliding step: every atom near, not at, the truth."""
+    rng = np.random.default_rng(seed)
+    return sfw.AtomSet.from_numpy(vol.m + rng.normal(0, 0.4, vol.m.shape), vol.sigma * 1.05,
+                                  np.clip(vol.d + 0.05, 1.3, 2.9), vol.w * 0.9, device=dev)
+
+
 def gpu_solve(sfw, plan, vol, dev, boosted):
     """Algorithm 1 (SFW) or 2 (BSFW) on the GPU path: outer iterations, seconds, criterion."""
     from paper_2009_05473_gb300 import solver
@@ -238,6 +263,113 @@ def gpu_solve(sfw, plan, vol, dev, boosted):
     iters = len(out["history"])
     return {"outer_iters": iters, "seconds": out["seconds"], "iters_per_s": iters / out["seconds"],
             "C": out["C"], "atoms": int(out["w"].size), "true_atoms": int(vol.N)}
+
+
+class StepRunner:
+    """One SFW iteration's data-parallel work on one plan, as a callable on the current stream:
+    the sliding step's loss and gradient at the current atoms (render, blur, residual + loss,
+    transposed blur, adjoint sums), then the grid certificate of that residual -- with the
+    top-64 voxels re-scored in FP32 on a bf16 plan (the 'precision' configuration), with the
+    fused grid argmax otherwise."""
+
+    def __init__(self, sfw, plan, y, est, lam, topk, dev):
+        import torch
+        self.plan, self.y, self.est, self.lam, self.topk = plan, y, est, lam, topk
+        self.sb = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
+                   "grad": torch.empty(6 * est.N, dtype=torch.float64, device=dev),
+                   "residual": torch.empty(plan.n, dtype=torch.float32, device=dev)}
+        self.cb = {"best_val": torch.empty(1, dtype=torch.float32, device=dev),
+                   "best_idx": torch.empty(1, dtype=torch.int64, device=dev)}
+        self.last = None
+
+    def __call__(self):
+        loss, grad, res = self.plan.slide_loss_grad(self.y, self.est, self.lam, want_residual=True, out=self.sb)
+        if self.topk:
+            self.last = self.plan.certificate_topk(res, self.lam, self.topk)
+        else:
+            self.last = self.plan.certificate(res, self.lam, want_max=False, out=self.cb)
+        return loss, grad
+
+
+def time_graph(sfw, fn, steps, warmup, flush, dev, profile_tag=None, clock_log=None, local_rank=0,
+               world=1):
+    """Capture fn into a CUDA graph and replay it `steps` times with the L2 flushed between
+    replays (outside the per-step events).  With profile_tag the library puts event-record nodes
+    around the kernels of that tag ("*": every kernel) into the graph, so every replay times
+    them; their per-tag totals over the timed replays are returned in "prof"."""
+    import torch
+    import torch.distributed as dist
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream(device=dev)
+    if profile_tag:
+        sfw._abi.sfw_profile_start(4096, None if profile_tag == "*" else profile_tag)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            fn()
+    torch.cuda.synchronize()
+    for i in range(3):
+        flush.fill_(float(i))
+        g.replay()
+    torch.cuda.synchronize()
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(local_rank, clock_log) if clock_log else None
+    clocks = None
+    if sampler:
+        sampler.__enter__()
+    try:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(float(i))            # evict L2 between steps (outside the step events)
+            ev_s[i].record()
+            g.replay()
+            ev_e[i].record()
+            ev_e[i].synchronize()
+            if profile_tag:
+                sfw._abi.sfw_profile_collect()   # the tagged kernels' durations in this replay
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        if world > 1:
+            dist.barrier()
+    finally:
+        if sampler:
+            sampler.__exit__(None, None, None)
+            clocks = sampler.summary()
+    prof = sfw._abi.sfw_profile_stop() if profile_tag else None
+    ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
+    del g
+    return {"ms_total": float(np.sum(ms)), "ms_median": float(np.median(ms)), "prof": prof,
+            "clocks": clocks, "wall_s": wall1 - wall0}
+
+
+def time_direct(fn, reps, dev):
+    """Median CUDA-event time (ms) of fn called directly (the plain FP32 route: long kernels)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def eta_rel_diff(a_plan, b_plan, res, lam):
+    """max |eta_a - eta_b| / max |eta_b| over the whole grid (two routes on the same residual)."""
+    ea = a_plan.certificate(res, lam, want_eta=True, want_max=False)["eta"]
+    eb = b_plan.certificate(res, lam, want_eta=True, want_max=False)["eta"]
+    return float((ea - eb).abs().max().item() / eb.abs().max().item())
 
 
 def run_ours(args):
@@ -253,164 +385,131 @@ def run_ours(args):
         sfw.build_library()
     if world > 1:
         dist.barrier()
-
-    # each replica solves its own synthetic volume (seed = rank): replicas only
-    vol = replica_volume(args.workload, rank)
-    plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
-    V, K = vol.V, plan.K
     dev = torch.device("cuda", local_rank)
-
-    # observation y = Phi mu* + noise made on the device by the library's own forward operator;
-    # lambda = 0.05 * max over the grid of Phi^T y  (first certificate max = 20)
-    y, lam = observe_on_device(sfw, plan, vol, dev)
-    # the current iterate of a sliding step: atoms near, not at, the truth
-    rng = np.random.default_rng(1000 + rank)
-    est = sfw.AtomSet.from_numpy(vol.m + rng.normal(0, 0.4, vol.m.shape), vol.sigma * 1.05,
-                                 np.clip(vol.d + 0.05, 1.3, 2.9), vol.w * 0.9, device=dev)
-
-    bufs = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
-            "grad": torch.empty(6 * vol.N, dtype=torch.float64, device=dev),
-            "residual": torch.empty(vol.n, dtype=torch.float32, device=dev),
-            "best_val": torch.empty(1, dtype=torch.float32, device=dev),
-            "best_idx": torch.empty(1, dtype=torch.int64, device=dev)}
-    # one SFW iteration's device work (sfw_step): residual + loss, then the back-projection
-    # and adjoint on this stream while the grid certificate runs on the auxiliary one
-    aux = torch.cuda.Stream(device=dev)
-
-    def step():
-        plan.step(y, est, lam, aux_stream=aux, out=bufs)
-
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    launches0 = sfw.launch_count()
 
-    # warm-up (also sets every kernel attribute before capture)
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-
-    def capture(only_tag):
-        """Capture one step into a graph; the library puts event-record nodes around every
-        kernel (or only around `only_tag`), so each replay times those kernels."""
-        g = torch.cuda.CUDAGraph()
-        sfw._abi.sfw_profile_start(256, only_tag)
-        with torch.cuda.stream(cap_stream):
-            with torch.cuda.graph(g, stream=cap_stream):
-                step()
-        torch.cuda.synchronize()
-        return g
-
-    cap_stream = torch.cuda.Stream(device=dev)
-    # per-kernel breakdown (separate profiled replays, not the timed region)
-    graph = capture(None)
-    for i in range(20):
-        flush.fill_(float(i))
-        graph.replay()
-        torch.cuda.synchronize()
-        if i >= 5:
-            sfw._abi.sfw_profile_collect()
-    breakdown = sfw._abi.sfw_profile_stop()
-    kernels_per_step = int(sum(v["launches"] for v in breakdown.values()) // 15)
-    dom_tag = max(breakdown.items(), key=lambda kv: kv[1]["ms"])[0]
-    del graph
-
-    # timed graph: event nodes only around the dominant kernel
-    graph = capture(dom_tag)
-    for i in range(3):
-        flush.fill_(float(i))
-        graph.replay()
-    torch.cuda.synchronize()
-
-    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local_rank, args.clock_log) as clocks:
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))            # evict L2 between steps (outside the step events)
-            ev_s[i].record()
-            graph.replay()
-            ev_e[i].record()
-            ev_e[i].synchronize()
-            sfw._abi.sfw_profile_collect()   # the dominant kernel's duration in this replay
-        torch.cuda.synchronize()
-        wall1 = time.perf_counter()
-        if world > 1:
-            dist.barrier()
-    prof = sfw._abi.sfw_profile_stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
-    t_ms = float(np.sum(step_ms))
-    gpu_launches = kernels_per_step * args.steps
-    t_max = max_over_ranks(t_ms, dev)
+    # ---- headline: each replica solves its own synthetic volume (seed = rank): replicas only
+    vol = replica_volume(args.workload, rank)
+    precision = "bf16" if args.workload in PRECISION_WORKLOADS else "fp32"
+    topk = 64 if precision == "bf16" else 0
+    plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, precision=precision)
+    V, K = vol.V, plan.K
+    y, lam = observe_on_device(sfw, plan, vol, dev)
+    est = current_estimate(sfw, vol, dev, 1000 + rank)
+    run = StepRunner(sfw, plan, y, est, lam, topk, dev)
+    # per-kernel breakdown from separately profiled replays, then the timed replays with event
+    # nodes around the dominant kernel only
+    bd = time_graph(sfw, run, 12, args.warmup, flush, dev, profile_tag="*")["prof"]
+    breakdown = {k: v["ms"] / 12 for k, v in sorted(bd.items(), key=lambda kv: -kv[1]["ms"])}
+    kernels_per_step = int(round(sum(v["launches"] for v in bd.values()) / 12))
+    dom_tag = next(iter(breakdown))
+    t = time_graph(sfw, run, args.steps, args.warmup, flush, dev, profile_tag=dom_tag,
+                   clock_log=args.clock_log, local_rank=local_rank, world=world)
+    t_max = max_over_ranks(t["ms_total"], dev)
     cands = V * K
     value = whole_job_rate(args.steps * cands, world, t_max / 1e3)
-
-    # roofline of the dominant kernel, timed inside the timed region
-    tag = dom_tag
-    rec = prof[tag]
+    rec = t["prof"][dom_tag]
     avg_s = rec["ms"] / rec["launches"] / 1e3
     peak, peak_kind = measured_peaks()
-    alg = algorithmic_bytes(tag, plan, vol)
+    alg = algorithmic_bytes(dom_tag, plan, vol)
     achieved = alg / avg_s / 1e9
-    traffic = ncu_traffic(tag)
 
-    # end to end through the public API with host buffers (pinned), copies inside the timing
+    # ---- end to end through the public API with host buffers (pinned), copies inside the timing
     y_host = y.cpu().pin_memory()
     p_host = {k: getattr(est, k).cpu().pin_memory() for k in ("m", "sigma", "d", "w")}
     y_dev = torch.empty_like(y)
     a_dev = sfw.AtomSet(*(torch.empty_like(getattr(est, k)) for k in ("m", "sigma", "d", "w")))
+    e2e_run = StepRunner(sfw, plan, y_dev, a_dev, lam, topk, dev)
     out_host = {"loss": torch.empty(1, dtype=torch.float64).pin_memory(),
                 "grad": torch.empty(6 * vol.N, dtype=torch.float64).pin_memory(),
-                "best_val": torch.empty(1, dtype=torch.float32).pin_memory(),
-                "best_idx": torch.empty(1, dtype=torch.int64).pin_memory()}
-    h2d = y_host.numel() * 4 + sum(t.numel() * 4 for t in p_host.values())
-    d2h = 8 + 8 * 6 * vol.N + 4 + 8
+                "a": torch.empty(5 if topk else 1, dtype=torch.float32).pin_memory(),
+                "b": torch.empty(1, dtype=torch.float64 if topk else torch.int64).pin_memory()}
+    h2d = y_host.numel() * 4 + sum(v.numel() * 4 for v in p_host.values())
+    d2h = 8 + 8 * 6 * vol.N + (5 * 4 + 8 if topk else 4 + 8)
     e2e_t = 0.0
-    for i in range(args.e2e_steps + 3):
+    n_e2e = min(args.e2e_steps, 3 * args.steps + 10)
+    for i in range(n_e2e + 3):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         y_dev.copy_(y_host, non_blocking=True)
         for k in ("m", "sigma", "d", "w"):
             getattr(a_dev, k).copy_(p_host[k], non_blocking=True)
-        o = plan.step(y_dev, a_dev, lam, aux_stream=aux, out=bufs)
-        out_host["loss"].copy_(o["loss"], non_blocking=True)
-        out_host["grad"].copy_(o["grad"], non_blocking=True)
-        out_host["best_val"].copy_(o["best_val"], non_blocking=True)
-        out_host["best_idx"].copy_(o["best_idx"], non_blocking=True)
+        loss, grad = e2e_run()
+        out_host["loss"].copy_(loss, non_blocking=True)
+        out_host["grad"].copy_(grad, non_blocking=True)
+        last = e2e_run.last
+        out_host["a"].copy_(last["best_theta"] if topk else last["best_val"], non_blocking=True)
+        out_host["b"].copy_(last["best_eta"] if topk else last["best_idx"], non_blocking=True)
         torch.cuda.synchronize()
         if i >= 3:
             e2e_t += time.perf_counter() - t0
-    e2e_value = whole_job_rate(args.e2e_steps * cands, world, max_over_ranks(e2e_t, dev))
+    e2e_value = whole_job_rate(n_e2e * cands, world, max_over_ranks(e2e_t, dev))
 
-    # the sliding step's loss + gradient alone (the evaluation BFGS repeats in step 4 of
-    # Algorithm 1): its own graph, replayed with the L2 flushed in between
-    sb = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
-          "grad": torch.empty(6 * vol.N, dtype=torch.float64, device=dev),
-          "residual": torch.empty(vol.n, dtype=torch.float32, device=dev)}
-    for _ in range(3):
-        plan.slide_loss_grad(y, est, lam, want_residual=True, out=sb)
-    torch.cuda.synchronize()
-    sgraph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(cap_stream):
-        with torch.cuda.graph(sgraph, stream=cap_stream):
-            plan.slide_loss_grad(y, est, lam, want_residual=True, out=sb)
-    torch.cuda.synchronize()
-    n_slide = 300
-    s_ms = 0.0
-    for i in range(n_slide):
-        flush.fill_(float(i))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        sgraph.replay()
-        e1.record()
-        e1.synchronize()
-        s_ms += e0.elapsed_time(e1)
-    slide_evals_per_s = whole_job_rate(n_slide, world, max_over_ranks(s_ms, dev) / 1e3)
-    del sgraph
+    # ---- the plain FP32 route (direct sums) on the same step, and the routes' differences
+    plain = None
+    if not args.no_plain:
+        pplan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, route="direct")
+        prun = StepRunner(sfw, pplan, y, est, lam, topk, dev)
+        p_ms = time_direct(prun, 2, dev)
+        f32 = plan if precision == "fp32" else sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
+        res = run.sb["residual"]
+        run()
+        torch.cuda.synchronize()
+        plain = {"route": "direct (FP32 direct sums over the PSF taps and the unit-atom boxes)",
+                 "ms_per_step": p_ms, "value": whole_job_rate(cands, world, max_over_ranks(p_ms, dev) / 1e3),
+                 "unit": "candidates/s",
+                 "eta_rel_diff_plain_vs_fft_fp32": eta_rel_diff(pplan, f32, res, lam)}
+        if precision == "bf16":
+            plain["eta_rel_diff_bf16_vs_fft_fp32"] = eta_rel_diff(plan, f32, res, lam)
+            f32.close()
+        plain["speedup"] = value / plain["value"]
+        pplan.close()
 
-    # outer iterations of Algorithms 1 and 2 on the GPU path (configurations 1 and 2)
+    # ---- sliding loss + gradient alone (step 4 of Algorithm 1 repeats it): this volume, and
+    # the 256 x 256 x 64, N = 100 'differentiation' workload, FFT against the plain route
+    slide = {}
+    for wl in (args.workload, "vol256x256x64_n100"):
+        v = vol if wl == args.workload else sfw_inputs.WORKLOADS[wl](seed=rank)
+        sp = plan if wl == args.workload else sfw.Plan(v.n, v.R, v.psf)
+        yy = y if wl == args.workload else observe_slide(sfw, sp, v, dev)
+        ee = est if wl == args.workload else current_estimate(sfw, v, dev, 2000 + rank)
+        sb = {"loss": torch.empty(1, dtype=torch.float64, device=dev),
+              "grad": torch.empty(6 * v.N, dtype=torch.float64, device=dev)}
+        fn = (lambda sp=sp, yy=yy, ee=ee, sb=sb: sp.slide_loss_grad(yy, ee, lam, out=sb))
+        ts = time_graph(sfw, fn, 100, 3, flush, dev)
+        rate = whole_job_rate(100, world, max_over_ranks(ts["ms_total"], dev) / 1e3)
+        entry = {"evals_per_s": rate, "ms": ts["ms_total"] / 100, "atoms": int(v.N), "volume": list(v.n)}
+        if not args.no_plain:
+            dp = sfw.Plan(v.n, v.R, v.psf, route="direct")
+            d_ms = time_direct(lambda dp=dp, yy=yy, ee=ee, sb=sb: dp.slide_loss_grad(yy, ee, lam, out=sb), 3, dev)
+            entry["plain_fp32_evals_per_s"] = whole_job_rate(1, world, max_over_ranks(d_ms, dev) / 1e3)
+            entry["speedup_vs_plain_fp32"] = rate / entry["plain_fp32_evals_per_s"]
+            dp.close()
+        if sp is not plan:
+            sp.close()
+        slide[wl] = entry
+
+    # ---- the 64^3 workload (configuration 2): sfw_step with the certificate on a second stream
+    secondary = None
+    if args.workload != "vol64_aniso_n10_k15" and not args.no_secondary:
+        v64 = sfw_inputs.vol64_aniso_n10(seed=rank)
+        p64 = sfw.Plan(v64.n, v64.R, v64.psf, v64.grid_sigmas, v64.grid_ds)
+        y64, lam64 = observe_on_device(sfw, p64, v64, dev)
+        e64 = current_estimate(sfw, v64, dev, 1000 + rank)
+        aux = torch.cuda.Stream(device=dev)
+        bufs = {}
+        p64.step(y64, e64, lam64, aux_stream=aux, out=bufs)
+        fn = (lambda: p64.step(y64, e64, lam64, aux_stream=aux, out=bufs))
+        ts = time_graph(sfw, fn, 200, 3, flush, dev)
+        ms = max_over_ranks(ts["ms_total"], dev) / 200
+        secondary = {"workload": "vol64_aniso_n10_k15", "ms_per_step": ms,
+                     "candidates_per_s": whole_job_rate(v64.V * p64.K, world, ms / 1e3),
+                     "step": "sfw_step: sliding loss/grad + grid certificate argmax (certificate on a second stream)"}
+        p64.close()
+
+    # ---- outer iterations of Algorithms 1 and 2 on the GPU path (configurations 1 and 2)
     outer = None
     if rank == 0 and world == 1 and not args.no_solver:
         outer = {}
@@ -423,7 +522,7 @@ def run_ours(args):
     line = None
     if rank == 0:
         line = {
-            "metric": "eta-grid candidates/s (grid certificate + argmax + sliding loss/grad per step)",
+            "metric": metric_name(args.workload),
             "value": value,
             "unit": "candidates/s",
             "n_gpus": world,
@@ -433,37 +532,52 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
+            "dtype": "bf16" if precision == "bf16" else "f32",
             "data": "synthetic (seeded; Gaussian PSF stands in for the paper's TDM PSF)",
             "config": {"workload": args.workload, "volume": list(vol.n), "psf_support": [2 * r + 1 for r in vol.R],
                        "atoms": vol.N, "kernels": K, "candidates_per_step": cands,
+                       "table": f"{precision} on P_cert {list(plan.info['P_cert'])}",
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                        "timing": "CUDA graph replay per step, CUDA events per step"},
             "steps_per_s": whole_job_rate(args.steps, world, t_max / 1e3),
-            "slide_evals_per_s": slide_evals_per_s,
+            "vs_plain_fp32": plain,
+            "slide": slide,
+            "secondary": secondary,
             "sfw_outer": outer,
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": gpu_launches,
+            "gpu_launches": kernels_per_step * args.steps,
             "kernels_per_step": kernels_per_step,
-            "roofline": {"bound": "hbm", "kernel": tag, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "roofline": {"bound": "hbm", "kernel": dom_tag, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic(dom_tag, args.workload),
                          "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
-            "kernels_ms_per_step": {k: v["ms"] / 15 for k, v in
-                                    sorted(breakdown.items(), key=lambda kv: -kv[1]["ms"])},
-            "clocks": clocks.summary(),
-            "wall_s_timed_region": wall1 - wall0,
+            "kernels_ms_per_step": breakdown,
+            "clocks": t["clocks"],
+            "wall_s_timed_region": t["wall_s"],
+            "library_launches_total": sfw.launch_count() - launches0,
         }
     plan.close()
     if world > 1:
         dist.barrier()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0 and not args.no_batch and world == 1:
+        line["batch"] = run_batch(args, embedded=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def observe_slide(sfw, plan, vol, dev):
+    """y = Phi mu* + noise for a plan without certificate grid."""
+    import torch
+    truth = sfw.AtomSet.from_numpy(vol.m, vol.sigma, vol.d, vol.w, device=dev)
+    y = plan.forward(truth)
+    y += vol.noise_frac * y.max() * torch.tensor(vol.noise, dtype=torch.float32, device=dev)
+    return y
 
 
 # ----------------------------------------------------------------------------- oracle timing
@@ -494,15 +608,26 @@ def _oracle_setup(workload):
     return oracle, vol, y, lam, m, s, d, w, kernels
 
 
+CPU_BASELINE_S = 20.0   # target CPU seconds of the bounded oracle sample
+
+
 def cpu_baseline(workload):
+    """The FP64 oracle on the host cores, on a bounded sample of one step: the sliding loss and
+    gradient plus the grid certificate (Fourier domain) over as many of the grid kernels as fit
+    in about CPU_BASELINE_S seconds; rate = candidates evaluated / time."""
     oracle, vol, y, lam, m, s, d, w, kernels = _oracle_setup(workload)
     t0 = time.perf_counter()
-    cands = oracle_step(vol, y, lam, m, s, d, w, kernels, oracle)
+    oracle_step(vol, y, lam, m, s, d, w, kernels, oracle, kernel_subset=[0])
+    t_one = time.perf_counter() - t0
+    per = max(1, min(len(kernels), int(CPU_BASELINE_S / max(t_one, 1e-3))))
+    t0 = time.perf_counter()
+    cands = oracle_step(vol, y, lam, m, s, d, w, kernels, oracle, kernel_subset=list(range(per)))
     t = time.perf_counter() - t0
     return {"value": cands / t, "unit": "candidates/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"one full step of the FP64 oracle on {workload} ({cands} candidates; "
-                       f"{t:.1f} s): direct-sum render/adjoint on {oracle.num_threads()} OpenMP "
-                       "threads, scipy.fft on all host threads for the blur and the grid certificate")}
+            "sample": (f"one FP64 oracle step on {workload}: sliding loss/grad + Fourier-domain grid "
+                       f"certificate over {per} of {len(kernels)} kernels ({cands} candidates, {t:.1f} s); "
+                       f"direct-sum render/adjoint on {oracle.num_threads()} OpenMP threads, scipy.fft on "
+                       "all host threads")}
 
 
 REF_BUDGET_S = float(os.environ.get("SFW_REF_BUDGET_S", "150"))   # warm-up + timed steps, seconds
@@ -569,7 +694,7 @@ def run_reference(args):
         cands += step(i)
     t = time.perf_counter() - t0
     value = cands / t
-    line = {"impl": "reference", "metric": "eta-grid candidates/s (grid certificate + argmax + sliding loss/grad per step)",
+    line = {"impl": "reference", "metric": metric_name(args.workload),
             "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
@@ -581,10 +706,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, embedded=False):
     """The uneven batch: 64 volumes from {48^3, 64^3, 96x96x64, 128^3}, N in U{5..40}, per-volume
     PSF widths, K = 15; one step = every volume's sliding loss/gradient and grid certificate
-    argmax through grouped persistent launches, replayed from one CUDA graph."""
+    argmax through grouped persistent launches, replayed from one CUDA graph.  Embedded in the
+    default run it returns its record (fewer timed steps) instead of printing a line."""
     import torch
     import paper_2009_05473_gb300 as sfw
     rank, local_rank, world = dist_env()
@@ -596,14 +722,8 @@ def run_batch(args):
     t_plan = time.perf_counter()
     for i, vol in enumerate(vols):
         plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds)
-        truth = sfw.AtomSet.from_numpy(vol.m, vol.sigma, vol.d, vol.w, device=dev)
-        y = plan.forward(truth)
-        y += vol.noise_frac * y.max() * torch.tensor(vol.noise, dtype=torch.float32, device=dev)
-        lam = 0.05 * float(plan.certificate(y, 1.0, want_max=False)["best_val"].item())
-        rng = np.random.default_rng(2000 + i)
-        est = sfw.AtomSet.from_numpy(vol.m + rng.normal(0, 0.4, vol.m.shape), vol.sigma * 1.05,
-                                     np.clip(vol.d + 0.05, 1.3, 2.9), vol.w * 0.9, device=dev)
-        plans.append(plan); ys.append(y); ests.append(est); lams.append(lam)
+        y, lam = observe_on_device(sfw, plan, vol, dev)
+        plans.append(plan); ys.append(y); ests.append(current_estimate(sfw, vol, dev, 2000 + i)); lams.append(lam)
     t_plan = time.perf_counter() - t_plan
     batch = sfw.Batch(plans, ys, ests, lams)
     cands = sum(v.V * p.K for v, p in zip(vols, plans))
@@ -612,45 +732,30 @@ def run_batch(args):
         batch.step()
     torch.cuda.synchronize()
     t_tune = time.perf_counter()
-    batch.autotune(os.path.join("/tmp", "sfw_batch64_autotune.json"))
+    os.makedirs(args.clock_log, exist_ok=True)
+    batch.autotune(os.path.join(args.clock_log, "batch64_autotune.json"))
     t_tune = time.perf_counter() - t_tune
-    cap = torch.cuda.Stream(device=dev)
-    graph = torch.cuda.CUDAGraph()
-    sfw._abi.sfw_profile_start(4096, None)
-    with torch.cuda.stream(cap):
-        with torch.cuda.graph(graph, stream=cap):
-            batch.step()
-    torch.cuda.synchronize()
-    for i in range(3):
-        flush.fill_(float(i))
-        graph.replay()
-    torch.cuda.synchronize()
-    steps = min(args.steps, 200)
-    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    with ClockSampler(local_rank, args.clock_log) as clocks:
-        for i in range(steps):
-            flush.fill_(float(i))
-            ev_s[i].record()
-            graph.replay()
-            ev_e[i].record()
-            ev_e[i].synchronize()
-            sfw._abi.sfw_profile_collect()
-    prof = sfw._abi.sfw_profile_stop()
-    t_ms = float(sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e)))
-    per_step = {k: v["ms"] / steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
-    line = {"metric": "eta-grid candidates/s (batched: certificate + argmax + sliding loss/grad of 64 volumes per step)",
-            "value": cands * steps / (t_ms / 1e3), "unit": "candidates/s", "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": "batch64_uneven", "volumes": len(vols), "candidates_per_step": cands,
-                       "atoms_total": int(sum(v.N for v in vols)), "kernels": 15,
-                       "grouped_launches_per_step": batch.launches_per_step,
-                       "l2": "flushed between steps (256 MB write)", "timing": "one CUDA graph per step"},
-            "plan_seconds": t_plan, "autotune_seconds": t_tune,
-            "kernels_ms_per_step_with_event_nodes": per_step,
-            "clocks": clocks.summary()}
-    print(json.dumps(line), flush=True)
+    steps = min(args.steps, 20 if embedded else 200)
+    t = time_graph(sfw, batch.step, steps, 3, flush, dev, clock_log=None if embedded else args.clock_log,
+                   local_rank=local_rank)
+    rec = {"metric": "eta-grid candidates/s (batched: certificate + argmax + sliding loss/grad of 64 volumes per step)",
+           "value": cands * steps / (t["ms_total"] / 1e3), "unit": "candidates/s", "n_gpus": 1, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": t["ms_total"] / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+           "config": {"workload": "batch64_uneven", "volumes": len(vols), "candidates_per_step": cands,
+                      "atoms_total": int(sum(v.N for v in vols)), "kernels": 15,
+                      "grouped_launches_per_step": batch.launches_per_step,
+                      "l2": "flushed between steps (256 MB write)", "timing": "one CUDA graph per step"},
+           "plan_seconds": t_plan, "autotune_seconds": t_tune}
+    if not embedded:
+        rec["clocks"] = t["clocks"]
+    batch.close()
+    for p in plans:
+        p.close()
+    if embedded:
+        return {k: rec[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "plan_seconds",
+                                    "autotune_seconds")}
+    print(json.dumps(rec), flush=True)
 
 
 def run_fig2(args):

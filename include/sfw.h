@@ -53,6 +53,15 @@ typedef enum {
 
 enum { SFW_PREC_FP32 = 0, SFW_PREC_BF16 = 1 };
 
+/* Algorithm of the convolutions (Eq. 3 and its transpose) and of the grid
+ * certificate (Eq. 5).  FFT: Fourier-domain products on padded grids (Section 2:
+ * "convolutions are made in Fourier domain"; the certificate against the
+ * kernel-family table).  DIRECT: plain FP32 direct sums over the PSF taps and
+ * over the unit atom's truncated box, one thread per output voxel (the
+ * straightforward GPU form, kept as the comparison path).  AUTO: FFT until
+ * sfw_autotune times both on the plan and keeps the faster one per operation. */
+enum { SFW_ROUTE_AUTO = 0, SFW_ROUTE_FFT = 1, SFW_ROUTE_DIRECT = 2 };
+
 /* Problem geometry, certificate grid and options of a plan (all HOST memory).
  *   n[3]      grid shape, each in [4, 1024]
  *   R[3]      PSF half-widths, each in [0, 64]
@@ -64,7 +73,10 @@ enum { SFW_PREC_FP32 = 0, SFW_PREC_BF16 = 1 };
  *             (bfloat16 table, FP32 arithmetic; see sfw_certificate_grid)
  *   eps       atom truncation level for rendering and the adjoint: an atom is
  *             evaluated only where exp(-(rho/sigma)^d/2) >= eps; 0 selects
- *             1e-9 */
+ *             1e-9
+ *   route     SFW_ROUTE_AUTO, SFW_ROUTE_FFT or SFW_ROUTE_DIRECT (above).  A
+ *             DIRECT plan builds no kernel-family table; an AUTO plan builds
+ *             what both routes need. */
 typedef struct {
     int n[3];
     int R[3];
@@ -75,6 +87,7 @@ typedef struct {
     const float* ds;
     int precision;
     float eps;
+    int route;
 } sfw_plan_desc;
 
 typedef struct sfw_plan sfw_plan;
@@ -83,11 +96,14 @@ typedef struct sfw_plan sfw_plan;
 typedef struct {
     int E[3];               /* extended grid n + 2R */
     int P_conv[3];          /* FFT grid of the blur, >= E, 2-3-5 smooth */
-    int P_cert[3];          /* FFT grid of the certificate, >= 2n - 1, 2-3-5 smooth */
+    int P_cert[3];          /* FFT grid of the certificate, >= n + h (h: support half-width of
+                               H * g_k, at most n - 1), 2-3-5 smooth; 0 on a DIRECT plan */
     int K;                  /* number of certificate kernels */
     int real_table;         /* 1 if the kernel-family spectra are real (even H) */
     size_t table_bytes;     /* device bytes of the kernel-family table */
     size_t workspace_bytes; /* device bytes of the plan workspace */
+    int route_blur;         /* SFW_ROUTE_FFT or SFW_ROUTE_DIRECT: convolutions in use */
+    int route_cert;         /* SFW_ROUTE_FFT or SFW_ROUTE_DIRECT: grid certificate in use */
 } sfw_plan_info;
 
 /* Atom set (DEVICE memory, FP32, structure of arrays).
@@ -111,6 +127,16 @@ typedef struct {
  * SFW_ERR_ALLOC, SFW_ERR_CUDA. */
 sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out);
 
+/* Route choice of an SFW_ROUTE_AUTO plan (FFT vs DIRECT, separately for the
+ * convolutions and for the grid certificate).  Times each route of each
+ * operation on the plan's own workspace (a zero residual, one warm-up and three
+ * timed runs, CUDA events on stream) and keeps the faster one.  With
+ * cache_path (host string, may be NULL) the choice is looked up in that text
+ * file first, keyed by the plan's shape, PSF support, grid and precision, and
+ * appended to it after timing.  Synchronous; not capturable.  Plans created
+ * with a fixed route keep it (SFW_OK, nothing timed). */
+sfw_status sfw_autotune(sfw_plan* plan, const char* cache_path, void* stream);
+
 /* Free a plan and its device memory (synchronises the device). NULL is a no-op. */
 sfw_status sfw_plan_destroy(sfw_plan* plan);
 
@@ -132,7 +158,9 @@ sfw_status sfw_forward(sfw_plan* plan, const sfw_atoms* atoms, float* y_out, voi
 /* Certificate of Eq. 5 on the grid (step 1 of Algorithms 1 and 2):
  *   eta_k(m) = (1/lambda) sum_{s in grid} r(s) (H * g_k)(s - m)
  *            = (1/lambda) <Phi G((m, sigma_k, d_k), 1), r>
- * for every voxel m and kernel k, by FFT correlation with the plan's table.
+ * for every voxel m and kernel k, by FFT correlation with the plan's table
+ * (route FFT) or as (1/lambda) sum_t g_k(t - m) b(t), b = Phi^T r on E, by
+ * direct sums (route DIRECT).
  *   residual  device, n0*n1*n2 floats (r = y - Phi mu; r = y for mu = 0)
  *   lambda    > 0
  *   eta_out   device K*n0*n1*n2 floats or NULL: eta in flat order k*V + lin(m)
@@ -184,29 +212,34 @@ sfw_status sfw_eta_points(sfw_plan* plan, const float* residual, double lambda, 
 
 /* Arg-maximum / top-k of a device float array (the grid maximum that seeds
  * step 1).
- *   values   device, count floats, count in [1, 2^40]
+ *   values   device, count floats, count in [1, 2^32 - 2] (the index of a
+ *            value travels in the low 32 bits of a 64-bit comparison key;
+ *            SFW_ERR_ARG outside that range)
  *   topk     1..64: the topk largest values, in decreasing order, ties ->
  *            lower index first
  *   val_out  device topk floats; idx_out device topk int64
  * A NaN anywhere makes idx_out[0] = -1 (checked on the device; the call does
- * not synchronise). */
+ * not synchronise).  The key scratch is a library-owned device buffer,
+ * allocated with cudaMalloc on first use and re-allocated (after a stream
+ * synchronisation) when a larger count or topk needs more. */
 sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_out,
                       int64_t* idx_out, void* stream);
 
 /* sfw_argmax without any device allocation.  (The paper has no counterpart:
  * this entry point exists for callers that cannot allocate.)
- * Same arguments, results and NaN reporting as sfw_argmax.  sfw_argmax
- * allocates its key scratch with cudaMalloc on first use; this variant uses a
- * 2 MiB static device array of the library instead and never calls cudaMalloc
- * or cudaFree -- for code running under a global-mode stream capture, for
- * applications whose device memory belongs to another allocator, and for loops
- * where a cudaFree would synchronise the device.
- * Limit: topk == 1 accepts any count; topk > 1 needs
+ * Same arguments, results and NaN reporting as sfw_argmax, same count range
+ * [1, 2^32 - 2].  sfw_argmax allocates its key scratch with cudaMalloc on
+ * first use; this variant uses a 2 MiB static device array of the library
+ * instead and never calls cudaMalloc, cudaFree or an allocating library
+ * routine -- for applications whose device memory belongs to another
+ * allocator or a fixed budget, and for loops where the cudaFree of a
+ * re-allocation would synchronise the device.
+ * Limit: topk == 1 takes any count in the range above; topk > 1 needs
  * ceil(count / 4096) * topk <= 131072 (e.g. count <= 8 388 608 for topk = 64),
  * else SFW_ERR_SHAPE.  The first call on each device looks up the array's
- * address (make it before any stream capture).  All calls share the array:
- * calls whose kernels overlap on the GPU race and must be ordered by the
- * caller. */
+ * address (make that first call before any stream capture).  All calls share
+ * the array: calls whose kernels overlap on the GPU race and must be ordered
+ * by the caller. */
 sfw_status sfw_argmax_noalloc(const float* values, int64_t count, int topk, float* val_out,
                               int64_t* idx_out, void* stream);
 
@@ -251,7 +284,7 @@ sfw_status sfw_slide_loss_grad(sfw_plan* plan, const float* y, const sfw_atoms* 
  * it (data may change in place), the call captures the step into a CUDA graph
  * of the plan (on two streams the plan owns; capturing runs nothing) and
  * launches it on stream; later identical calls only launch the graph.  A call
- * with other arguments drops the graph (after a device synchronisation).
+ * with other arguments drops the graph (after waiting for its last launch).
  * Calls made while stream is being captured by the caller, and calls while a
  * profile is recorded, launch their kernels directly. */
 sfw_status sfw_step(sfw_plan* plan, const float* y, const sfw_atoms* atoms, double lambda,

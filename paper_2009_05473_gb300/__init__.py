@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_topk,  # noqa: F401
                    sfw_eta_points, sfw_forward, sfw_gram,
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
-                   sfw_plan_check, sfw_slide_loss_grad, sfw_step, sfw_version)
+                   sfw_plan_check, sfw_autotune, sfw_slide_loss_grad, sfw_step, sfw_version)
 
 __all__ = ["Plan", "AtomSet", "Batch", "argmax", "launch_count", "SfwError", "build_library"]
 
@@ -89,7 +89,7 @@ class Plan:
 
     def __init__(self, n: Sequence[int], R: Sequence[int], psf, sigmas: Sequence[float] = (),
                  ds: Sequence[float] = (), precision: str = "fp32", eps: float = 0.0,
-                 device: Optional[int] = None):
+                 device: Optional[int] = None, route: str = "fft"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2009_05473_gb300 needs a CUDA GPU (no CPU path)")
@@ -112,15 +112,30 @@ class Plan:
         desc.ds = dd.ctypes.data_as(fp) if dd.size else ctypes.cast(None, fp)
         desc.precision = {"fp32": _abi.SFW_PREC_FP32, "bf16": _abi.SFW_PREC_BF16}[precision]
         desc.eps = float(eps)
+        desc.route = {"auto": _abi.SFW_ROUTE_AUTO, "fft": _abi.SFW_ROUTE_FFT,
+                      "direct": _abi.SFW_ROUTE_DIRECT}[route]
         self._keep = (psf, sig, dd)
         self.handle = sfw_plan_create(desc)
-        info = sfw_plan_query(self.handle)
-        self.info = {"E": tuple(info.E), "P_conv": tuple(info.P_conv), "P_cert": tuple(info.P_cert),
-                     "K": info.K, "real_table": bool(info.real_table),
-                     "table_bytes": int(info.table_bytes), "workspace_bytes": int(info.workspace_bytes)}
-        self.K = info.K
+        self._query()
+        self.K = self.info["K"]
         self.V = int(np.prod(self.n))
         self.precision = precision
+        self.route = route
+
+    def _query(self):
+        info = sfw_plan_query(self.handle)
+        names = {_abi.SFW_ROUTE_FFT: "fft", _abi.SFW_ROUTE_DIRECT: "direct", 0: None}
+        self.info = {"E": tuple(info.E), "P_conv": tuple(info.P_conv), "P_cert": tuple(info.P_cert),
+                     "K": info.K, "real_table": bool(info.real_table),
+                     "table_bytes": int(info.table_bytes), "workspace_bytes": int(info.workspace_bytes),
+                     "route_blur": names[info.route_blur], "route_cert": names[info.route_cert]}
+
+    def autotune(self, cache_path: Optional[str] = None, stream=None) -> dict:
+        """Pick FFT or DIRECT per operation for a route="auto" plan (libsfw ``sfw_autotune``);
+        returns the routes in use."""
+        sfw_autotune(self.handle, cache_path, _stream_ptr(stream))
+        self._query()
+        return {"blur": self.info["route_blur"], "cert": self.info["route_cert"]}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -18,9 +18,13 @@ STATUS_NAMES = {0: "SFW_OK", 1: "SFW_ERR_ARG", 2: "SFW_ERR_SHAPE", 3: "SFW_ERR_C
                 7: "SFW_ERR_UNSUPPORTED"}
 SFW_PREC_FP32 = 0
 SFW_PREC_BF16 = 1
+SFW_ROUTE_AUTO = 0
+SFW_ROUTE_FFT = 1
+SFW_ROUTE_DIRECT = 2
 
 # every symbol declared in include/sfw.h
-EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_forward",
+EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_autotune",
+           "sfw_forward",
            "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
            "sfw_slide_loss_grad", "sfw_step", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
            "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
@@ -39,13 +43,14 @@ class PlanDesc(ctypes.Structure):
                 ("psf", ctypes.POINTER(ctypes.c_float)), ("n_sigma", ctypes.c_int),
                 ("n_d", ctypes.c_int), ("sigmas", ctypes.POINTER(ctypes.c_float)),
                 ("ds", ctypes.POINTER(ctypes.c_float)), ("precision", ctypes.c_int),
-                ("eps", ctypes.c_float)]
+                ("eps", ctypes.c_float), ("route", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("E", ctypes.c_int * 3), ("P_conv", ctypes.c_int * 3), ("P_cert", ctypes.c_int * 3),
                 ("K", ctypes.c_int), ("real_table", ctypes.c_int), ("table_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("route_blur", ctypes.c_int),
+                ("route_cert", ctypes.c_int)]
 
 
 class Atoms(ctypes.Structure):
@@ -75,6 +80,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(vp)]
     L.sfw_plan_destroy.argtypes = [vp]
     L.sfw_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    L.sfw_autotune.argtypes = [vp, ctypes.c_char_p, vp]
     L.sfw_forward.argtypes = [vp, ctypes.POINTER(Atoms), vp, vp]
     L.sfw_certificate_grid.argtypes = [vp, vp, dbl, vp, vp, vp, vp, vp, vp]
     L.sfw_eta_points.argtypes = [vp, vp, dbl, i32, vp, vp, vp, vp]
@@ -94,7 +100,8 @@ def lib() -> ctypes.CDLL:
     L.sfw_batch_autotune.argtypes = [vp, ctypes.c_char_p, vp]
     L.sfw_profile_stop.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     L.sfw_profile_collect.argtypes = []
-    for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_forward",
+    for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_autotune",
+                 "sfw_forward",
                  "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
                  "sfw_slide_loss_grad", "sfw_step", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
            "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect",
@@ -131,6 +138,10 @@ def sfw_plan_query(plan: int) -> PlanInfo:
     info = PlanInfo()
     check(lib().sfw_plan_query(plan, ctypes.byref(info)), "sfw_plan_query")
     return info
+
+
+def sfw_autotune(plan: int, cache_path, stream: int) -> None:
+    check(lib().sfw_autotune(plan, cache_path.encode() if cache_path else None, stream), "sfw_autotune")
 
 
 def sfw_forward(plan: int, atoms: Atoms, y_out: int, stream: int) -> None:

@@ -3,20 +3,19 @@
 //
 // sfw_argmax keeps its key scratch in a buffer it allocates with cudaMalloc on
 // first use (and re-allocates when a larger top-k needs more).  Some callers
-// cannot let a library do that: code that runs while a stream is being
-// captured into a CUDA graph in the global capture mode (cudaMalloc/cudaFree
-// are refused there), applications whose device memory is entirely owned by
-// another allocator (a framework's caching pool that already reserved the
-// GPU), and latency-critical loops in which a cudaFree would synchronise the
-// whole device.  This variant takes its scratch from one file-scope static
-// __device__ array instead, so it never calls cudaMalloc, cudaFree or any
-// allocating library routine.
+// cannot let a library do that: applications whose device memory is entirely
+// owned by another allocator (a framework's caching pool or a fixed budget
+// that already reserved the GPU, so a foreign cudaMalloc fails or steals from
+// it), and latency-critical loops in which the cudaFree of a re-allocation
+// would synchronise the whole device.  This variant takes its scratch from one
+// file-scope static __device__ array instead, so it never calls cudaMalloc,
+// cudaFree or any allocating library routine.
 //
 // The array exists on every GPU that loads this library, from load until
 // process exit.  Host code cannot use the array's name as a device address, so
 // the first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it; make that first call before any
-// stream capture.  Every call shares the array: two calls whose kernels overlap
+// (with that device current) and caches it; make that first call on a device
+// before any stream capture.  Every call shares the array: two calls whose kernels overlap
 // on the GPU (other streams, other host threads) race on it and may return
 // wrong results, so order such calls.  The kernels write every scratch slot
 // before they read it, so nothing needs clearing between calls.
@@ -59,7 +58,7 @@ extern "C" sfw_status sfw_argmax_noalloc(const float* values, int64_t count, int
     using namespace sfw;
     clear_error();
     if (!values || !val_out || !idx_out) return fail(SFW_ERR_ARG, "pointers must be non-NULL");
-    if (count < 1 || count >= 0xffffffffll) return fail(SFW_ERR_ARG, "count must be in [1, 2^32 - 1)");
+    if (count < 1 || count >= 0xffffffffll) return fail(SFW_ERR_ARG, "count must be in [1, 2^32 - 2]");
     if (topk < 1 || topk > 64 || topk > count) return fail(SFW_ERR_ARG, "topk must be in [1, min(64, count)]");
     // top-1 uses at most 1024 keys; top-k needs ceil(count / 4096) * topk keys per half
     const long long blocks = (count + 4095) / 4096;

@@ -37,10 +37,12 @@ sfw_status launch_wrap_psf(const float* psf, const int R[3], const int P[3], flo
 }
 
 // kx holds K(x) for |x_a| <= n_a - 1 at index x + (n - 1) (dense (2n-1)^3).
-// out[p] = K(-x) with x_a = p_a (p_a <= n_a - 1) or p_a - P_a (p_a >= P_a - n_a + 1), else 0:
-// the correlation kernel placed for a circular convolution on P.
-__global__ void k_wrap_kernel(const float* kx, int n0, int n1, int n2, int P0, int P1, int P2,
-                              float* out) {
+// out[p] = K(-x) with x_a = p_a (p_a <= h_a) or p_a - P_a (p_a >= P_a - h_a), else 0:
+// the correlation kernel, kept on the box |x_a| <= h_a (h_a <= n_a - 1, outside which it
+// vanishes), placed for a circular convolution on P (P_a >= n_a + h_a: no wrap-around
+// reaches a grid displacement).
+__global__ void k_wrap_kernel(const float* kx, int n0, int n1, int n2, int h0, int h1, int h2, int P0,
+                              int P1, int P2, float* out) {
     const long long total = (long long)P0 * P1 * P2;
     const int D1 = 2 * n1 - 1, D2 = 2 * n2 - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -49,9 +51,9 @@ __global__ void k_wrap_kernel(const float* kx, int n0, int n1, int n2, int P0, i
         const long long r = i / P2;
         const int p1 = (int)(r % P1);
         const int p0 = (int)(r / P1);
-        const int x0 = p0 <= n0 - 1 ? p0 : (p0 >= P0 - n0 + 1 ? p0 - P0 : 1 << 30);
-        const int x1 = p1 <= n1 - 1 ? p1 : (p1 >= P1 - n1 + 1 ? p1 - P1 : 1 << 30);
-        const int x2 = p2 <= n2 - 1 ? p2 : (p2 >= P2 - n2 + 1 ? p2 - P2 : 1 << 30);
+        const int x0 = p0 <= h0 ? p0 : (p0 >= P0 - h0 ? p0 - P0 : 1 << 30);
+        const int x1 = p1 <= h1 ? p1 : (p1 >= P1 - h1 ? p1 - P1 : 1 << 30);
+        const int x2 = p2 <= h2 ? p2 : (p2 >= P2 - h2 ? p2 - P2 : 1 << 30);
         float v = 0.f;
         if (x0 != (1 << 30) && x1 != (1 << 30) && x2 != (1 << 30))
             v = kx[((long long)(-x0 + n0 - 1) * D1 + (-x1 + n1 - 1)) * D2 + (-x2 + n2 - 1)];
@@ -59,9 +61,13 @@ __global__ void k_wrap_kernel(const float* kx, int n0, int n1, int n2, int P0, i
     }
 }
 
-sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int P[3], float* out,
+sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int h[3], const int P[3], float* out,
                               cudaStream_t st) {
-    SFW_LAUNCH(st, "k_wrap_kernel", k_wrap_kernel<<<1024, 256, 0, st>>>(kx, n[0], n[1], n[2], P[0], P[1], P[2], out));
+    for (int a = 0; a < 3; ++a)
+        if (h[a] < 0 || h[a] > n[a] - 1 || P[a] < n[a] + h[a])
+            return fail(SFW_ERR_SHAPE, "kernel placement: h[%d]=%d, P=%d, n=%d", a, h[a], P[a], n[a]);
+    SFW_LAUNCH(st, "k_wrap_kernel", k_wrap_kernel<<<1024, 256, 0, st>>>(kx, n[0], n[1], n[2], h[0], h[1], h[2],
+                                                                      P[0], P[1], P[2], out));
     return launch_check("k_wrap_kernel");
 }
 

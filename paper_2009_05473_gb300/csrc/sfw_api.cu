@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sfw_internal.cuh"
@@ -80,9 +81,22 @@ void prof_accumulate(const char* tag, double ms) {
 LaunchTag::LaunchTag(const char* tag) : prev(t_tag) { t_tag = tag; }
 LaunchTag::~LaunchTag() { t_tag = prev; }
 
-// Events are recorded with cudaEventRecordExternal so that, inside a stream
-// capture, they become event-record nodes of the graph and time every replay.
+// Inside a stream capture the events are recorded with cudaEventRecordExternal, so
+// that they become event-record nodes of the graph and time every replay; outside a
+// capture they are plain event records (the external flag is refused there).
 bool prof_active() { return g_prof_on.load(std::memory_order_relaxed); }
+
+static void prof_record(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
 
 void prof_begin(cudaStream_t st, const char* name) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
@@ -95,13 +109,13 @@ void prof_begin(cudaStream_t st, const char* name) {
     if (!g_prof_only.empty() && g_prof_only != tag) return;
     ProfRec& r = g_prof[g_prof_used++];
     r.tag = tag;
-    cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
+    prof_record(r.a, st);
     t_open = &r;
 }
 
 void prof_end(cudaStream_t st) {
     if (!t_open) return;
-    cudaEventRecordWithFlags(t_open->b, st, cudaEventRecordExternal);
+    prof_record(t_open->b, st);
     t_open = nullptr;
 }
 
@@ -578,6 +592,7 @@ struct sfw_plan {
     int K;
     std::vector<float> sigmas, ds;  // per kernel k
     int Pc[3], H2c;
+    int hc[3];          // half-widths of the kernel family's support (K_k = 0 beyond, per axis)
     Factors facc[3];
     const float2* twc[3];
     void* table;        // K spectra of Pc0 rows x (Pc1 H2c) lines (layout: table_lines)
@@ -617,6 +632,7 @@ struct sfw_plan {
     float* unit_slot;             // one atom (m0, m1, m2, sigma, d, w = 1)
     int num_sms;
     cudaEvent_t ev_fork, ev_join;  // sfw_step: residual ready / certificate done
+    cudaEvent_t ev_graph;          // sfw_step: recorded after each launch of the cached graph
     cudaStream_t cap_own, aux_own; // sfw_step captures its graph on these (origin, branch)
     // certificate tail by TMA: tensor map of the line-group-major axis-0 output (opaque)
     alignas(64) unsigned char tail_tmap[128];
@@ -641,6 +657,16 @@ struct sfw_plan {
     long long red_scratch_len;
     size_t ws_bytes;
     std::vector<void*> allocations;
+    // routes: requested (AUTO, FFT, DIRECT) and in use (FFT or DIRECT) per operation
+    int route;
+    int route_blur, route_cert;
+    bool fft_cert;                 // the kernel-family table and the certificate FFT buffers exist
+    bool direct_ok;                // the direct-sum buffers exist
+    float* gtab;                   // unit atoms g_k on their boxes (direct certificate)
+    int2* gkern;                   // per k: (offset in gtab, half-width)
+    float* bE_cert;                // H^T r of the direct certificate (bE belongs to the gradient)
+    double* dir_parts;             // criterion partials of the direct blur
+    int dir_parts_len;
 };
 
 static sfw_status plan_alloc(sfw_plan* p, void** ptr, size_t bytes) {
@@ -673,7 +699,8 @@ static void plan_free(sfw_plan* p) {
     p->aux_own = p->cap_own = nullptr;
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
-    p->ev_fork = p->ev_join = nullptr;
+    if (p->ev_graph) cudaEventDestroy(p->ev_graph);
+    p->ev_fork = p->ev_join = p->ev_graph = nullptr;
     if (p->gram_cols) cudaFree(p->gram_cols);
     p->gram_cols = nullptr;
     for (void* q : p->allocations) cudaFree(q);
@@ -749,7 +776,7 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
             ep.scale = 1.f;
             ep.out = kx;
             if ((st_ret = blur_forward(g, fE, Hg, SPEC_C64, gA, gB, ep, st, nullptr, kTableTags))) break;
-            if ((st_ret = launch_wrap_kernel(kx, p->n, p->Pc, wrapped, st))) break;
+            if ((st_ret = launch_wrap_kernel(kx, p->n, p->hc, p->Pc, wrapped, st))) break;
             if ((st_ret = fft3_forward(p->Pc, p->facc, p->twc, wrapped, ftmp, full + (size_t)k * spec_elems,
                                        1.0f / (float)Pc_tot, st)))
                 break;
@@ -808,6 +835,137 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
     cudaStreamSynchronize(st);
     for (void* q : tmp) cudaFree(q);
     return st_ret;
+}
+
+// Buffers of the direct-sum route: the criterion partials and, with a certificate
+// grid, every unit atom g_k tabulated on the cube of its cut-off radius (rendered by the
+// atom kernel itself, so the truncation g >= eps is the rendering's) plus a
+// back-projection buffer of its own.  Boxes beyond 2^28 values in total leave the
+// direct certificate out of an AUTO plan (SFW_ERR_SHAPE for a DIRECT plan).
+static sfw_status build_direct(sfw_plan* p, cudaStream_t st) {
+    p->dir_parts_len = 8 * p->num_sms;
+    SFW_TRY(plan_alloc_t(p, &p->dir_parts, (size_t)p->dir_parts_len));
+    const int K = p->K;
+    if (K == 0) return SFW_OK;
+    int emax = p->E[0];
+    for (int a = 1; a < 3; ++a) emax = p->E[a] > emax ? p->E[a] : emax;
+    const double L = 2.0 * log(1.0 / (double)p->eps);
+    std::vector<int2> kern(K);
+    std::vector<float> hm(3 * (size_t)K), hs(K), hd(K), hw(K, 1.0f);
+    long long total = 0;
+    for (int k = 0; k < K; ++k) {
+        const double rho = (double)p->sigmas[k] * pow(L, 1.0 / (double)p->ds[k]);
+        int h = (int)ceil(rho) + 1;
+        if (h > emax - 1) h = emax - 1;
+        kern[k] = make_int2((int)total, h);
+        total += (long long)(2 * h + 1) * (2 * h + 1) * (2 * h + 1);
+        for (int a = 0; a < 3; ++a) hm[3 * k + a] = (float)h;
+        hs[k] = p->sigmas[k];
+        hd[k] = p->ds[k];
+    }
+    if (total > (1LL << 28)) {
+        if (p->route == SFW_ROUTE_DIRECT)
+            return fail(SFW_ERR_SHAPE, "direct certificate: unit-atom boxes need %lld values (> 2^28)", total);
+        return SFW_OK;
+    }
+    SFW_TRY(plan_alloc_t(p, &p->gtab, (size_t)total));
+    SFW_TRY(plan_alloc_t(p, &p->gkern, (size_t)K));
+    SFW_TRY(plan_alloc_t(p, &p->bE_cert, (size_t)p->VE));
+    SFW_CUDA(cudaMemcpy(p->gkern, kern.data(), sizeof(int2) * K, cudaMemcpyHostToDevice));
+    float* dev = nullptr;
+    cudaError_t e = cudaMalloc(&dev, sizeof(float) * 6 * (size_t)K);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SFW_ERR_ALLOC, "direct certificate: atom upload");
+    }
+    sfw_status s = SFW_OK;
+    do {
+        float* dm = dev;
+        float* dsg = dev + 3 * K;
+        float* dd = dev + 4 * K;
+        float* dw = dev + 5 * K;
+        if ((e = cudaMemcpy(dm, hm.data(), sizeof(float) * 3 * K, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(dsg, hs.data(), sizeof(float) * K, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(dd, hd.data(), sizeof(float) * K, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(dw, hw.data(), sizeof(float) * K, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            s = cuda_fail(e, "direct certificate: atom upload");
+            break;
+        }
+        const int R0[3] = {0, 0, 0};
+        for (int k = 0; k < K && s == SFW_OK; ++k) {
+            AtomsDev a;
+            a.N = 1;
+            a.m = dm + 3 * k;
+            a.sigma = dsg + k;
+            a.d = dd + k;
+            a.w = dw + k;
+            const int wd = 2 * kern[k].y + 1;
+            const int box[3] = {wd, wd, wd};
+            s = launch_render(a, box, R0, p->eps, p->gtab + kern[k].x, st);
+        }
+        if (s) break;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(e, "direct certificate tables");
+    } while (0);
+    cudaStreamSynchronize(st);
+    cudaFree(dev);
+    return s;
+}
+
+// Phi f_E on the grid by the plan's convolution route.
+static sfw_status plan_blur_store(sfw_plan* p, const float* fE, float* out, cudaStream_t st) {
+    if (p->route_blur == SFW_ROUTE_DIRECT) {
+        if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the FFT route only");
+        DirectBlur b;
+        memset(&b, 0, sizeof(b));
+        b.fE = fE;
+        b.H = p->psf;
+        for (int a = 0; a < 3; ++a) {
+            b.n[a] = p->n[a];
+            b.R[a] = p->R[a];
+        }
+        b.out = out;
+        b.num_sms = p->num_sms;
+        return launch_direct_blur(b, st);
+    }
+    C2RPass ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.mode = C2R_STORE;
+    ep.scale = 1.f;
+    ep.out = out;
+    return blur_forward(p->blur, fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, nullptr);
+}
+
+// b = Phi^T r on E by the plan's convolution route.
+static sfw_status plan_transpose(sfw_plan* p, const float* r, float* bE, cudaStream_t st) {
+    if (p->route_blur == SFW_ROUTE_DIRECT) {
+        if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the FFT route only");
+        return launch_direct_transpose(r, p->psf, p->n, p->R, bE, p->num_sms, st);
+    }
+    return blur_transpose(p->blur, r, p->Hspec, SPEC_C64, p->bufA, p->bufB, bE, st);
+}
+
+// Median of three timed runs of fn on st (after one untimed run), in ms; < 0 on error.
+template <typename F>
+static float time_route(F fn, cudaStream_t st) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        cudaGetLastError();
+        return -1.f;
+    }
+    float t[3] = {-1.f, -1.f, -1.f};
+    bool ok = fn() == SFW_OK;
+    for (int i = 0; i < 3 && ok; ++i) {
+        ok = cudaEventRecord(a, st) == cudaSuccess && fn() == SFW_OK && cudaEventRecord(b, st) == cudaSuccess &&
+             cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t[i], a, b) == cudaSuccess;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!ok) return -1.f;
+    if (t[0] > t[1]) std::swap(t[0], t[1]);
+    if (t[1] > t[2]) std::swap(t[1], t[2]);
+    if (t[0] > t[1]) std::swap(t[0], t[1]);
+    return t[1];
 }
 
 static sfw_status check_atoms(const sfw_atoms* a, bool need_nonempty) {
@@ -913,11 +1071,17 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
     if (desc->precision != SFW_PREC_FP32 && desc->precision != SFW_PREC_BF16)
         return fail(SFW_ERR_ARG, "unknown precision %d", desc->precision);
     if (!(desc->eps >= 0.f && desc->eps < 0.1f)) return fail(SFW_ERR_ARG, "eps outside [0, 0.1)");
+    if (desc->route != SFW_ROUTE_AUTO && desc->route != SFW_ROUTE_FFT && desc->route != SFW_ROUTE_DIRECT)
+        return fail(SFW_ERR_ARG, "unknown route %d", desc->route);
 
     sfw_plan* p = new (std::nothrow) sfw_plan();
     if (!p) return fail(SFW_ERR_ALLOC, "host allocation");
     p->eps = desc->eps > 0.f ? desc->eps : 1e-9f;
     p->precision = desc->precision;
+    p->route = desc->route;
+    p->route_blur = p->route_cert = desc->route == SFW_ROUTE_DIRECT ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
+    p->fft_cert = K > 0 && desc->route != SFW_ROUTE_DIRECT;
+    p->direct_ok = desc->route != SFW_ROUTE_FFT;
     for (int a = 0; a < 3; ++a) {
         p->n[a] = desc->n[a];
         p->R[a] = desc->R[a];
@@ -939,9 +1103,37 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
     sfw_status s = SFW_OK;
     do {
         if ((s = make_blur_geom(p->tw, p->n, p->R, &p->blur))) break;
-        if (K > 0) {
+        if (p->fft_cert) {
+            // Support of K_k = H * g_k: the rendered atom vanishes beyond its cut-off radius
+            // rho_k = sigma_k (2 ln(1/eps))^(1/d_k) and H beyond R, so K_k(x) = 0 once
+            // |x_a| > R_a + ceil(max_k rho_k).  A circular correlation on P_a >= n_a + h_a
+            // then equals the linear one at every grid displacement.
+            double rho = 0.0;
+            const double L = 2.0 * log(1.0 / (double)p->eps);
+            for (int k = 0; k < K; ++k) {
+                const double r = (double)p->sigmas[k] * pow(L, 1.0 / (double)p->ds[k]);
+                rho = r > rho ? r : rho;
+            }
             for (int a = 0; a < 3; ++a) {
-                p->Pc[a] = next_smooth_even(2 * p->n[a] - 1);
+                const double h = (double)p->R[a] + ceil(rho);
+                p->hc[a] = h >= (double)(p->n[a] - 1) ? p->n[a] - 1 : (int)h;
+                // the smallest 2-3-5 smooth length, unless a register-resident length (64, 128,
+                // 256) is within 25 % of it or a compile-time specialised one within 10 %
+                const int m = p->n[a] + p->hc[a];
+                const int sm = next_smooth_even(m);
+                int pick = sm;
+                const int reg[3] = {64, 128, 256};
+                const int spec[7] = {64, 80, 96, 128, 160, 192, 256};
+                int best_spec = 0;
+                for (int q = 0; q < 7 && !best_spec; ++q)
+                    if (spec[q] >= m) best_spec = spec[q];
+                if (best_spec && best_spec <= sm + sm / 10) pick = best_spec;
+                for (int q = 0; q < 3; ++q)
+                    if (reg[q] >= m && reg[q] <= sm + sm / 4) {
+                        pick = reg[q];
+                        break;
+                    }
+                p->Pc[a] = pick;
                 if (p->Pc[a] > kMaxLen) {
                     s = fail(SFW_ERR_SHAPE, "certificate FFT length %d > %d", p->Pc[a], kMaxLen);
                     break;
@@ -1023,12 +1215,13 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         if ((s = plan_alloc_t(p, &p->red_scratch, (size_t)p->red_scratch_len))) break;
         if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_graph, cudaEventDisableTiming) != cudaSuccess ||
             cudaStreamCreateWithFlags(&p->aux_own, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&p->cap_own, cudaStreamNonBlocking) != cudaSuccess) {
             s = cuda_fail(cudaGetLastError(), "plan events");
             break;
         }
-        if (K > 0) {
+        if (p->fft_cert) {
             const size_t a_el = (size_t)K * p->n[0] * p->n[1] * p->H2c;
             const size_t b_el = (size_t)p->n[0] * p->Pc[1] * p->H2c;
             const size_t c_el = (size_t)K * p->n[0] * p->Pc[1] * p->H2c;
@@ -1053,7 +1246,8 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         // H^ on the blur grid, scaled by 1/|P| (folds the inverse normalisation)
         if ((s = launch_wrap_psf(p->psf, p->R, g.P, p->fE, st))) break;
         if ((s = fft3_forward(g.P, g.fac, g.tw, p->fE, p->bufA, p->Hspec, 1.0f / (float)Ptot, st))) break;
-        if ((s = build_table(p, st))) break;
+        if (p->fft_cert && (s = build_table(p, st))) break;
+        if (p->direct_ok && (s = build_direct(p, st))) break;
         e = cudaDeviceSynchronize();
         if (e != cudaSuccess) s = cuda_fail(e, "plan create");
     } while (0);
@@ -1082,8 +1276,10 @@ sfw_status sfw_plan_query(const sfw_plan* p, sfw_plan_info* info) {
     for (int a = 0; a < 3; ++a) {
         info->E[a] = p->E[a];
         info->P_conv[a] = p->blur.P[a];
-        info->P_cert[a] = p->K ? p->Pc[a] : 0;
+        info->P_cert[a] = p->fft_cert ? p->Pc[a] : 0;
     }
+    info->route_blur = p->route_blur;
+    info->route_cert = p->K ? p->route_cert : 0;
     info->K = p->K;
     info->real_table = p->real_table;
     info->table_bytes = p->table_bytes;
@@ -1098,12 +1294,7 @@ sfw_status sfw_forward(sfw_plan* p, const sfw_atoms* atoms, float* y_out, void* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     AtomsDev a = to_dev(atoms);
     SFW_TRY(launch_render(a, p->E, p->R, p->eps, p->fE, st));
-    C2RPass ep;
-    memset(&ep, 0, sizeof(ep));
-    ep.mode = C2R_STORE;
-    ep.scale = 1.f;
-    ep.out = y_out;
-    return blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, nullptr);
+    return plan_blur_store(p, p->fE, y_out, st);
 }
 
 // Rendering, blur, residual r = y - Phi mu and the criterion C (Eq. 4), on st.
@@ -1111,6 +1302,28 @@ static sfw_status residual_and_loss(sfw_plan* p, const float* y, const sfw_atoms
                                     double* loss_out, float* r, cudaStream_t st) {
     AtomsDev a = to_dev(atoms);
     SFW_TRY(launch_render(a, p->E, p->R, p->eps, p->fE, st));
+    if (p->route_blur == SFW_ROUTE_DIRECT) {
+        if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the FFT route only");
+        DirectBlur b;
+        memset(&b, 0, sizeof(b));
+        b.fE = p->fE;
+        b.H = p->psf;
+        for (int q = 0; q < 3; ++q) {
+            b.n[q] = p->n[q];
+            b.R[q] = p->R[q];
+        }
+        b.out = r;
+        b.y = y;
+        b.partials = p->dir_parts;
+        b.partials_len = p->dir_parts_len;
+        b.counter = p->ctr + 0;
+        b.loss_out = loss_out;
+        b.w = atoms->w;
+        b.nw = atoms->N;
+        b.lambda = lambda;
+        b.num_sms = p->num_sms;
+        return launch_direct_blur(b, st);
+    }
     C2RPass ep;
     memset(&ep, 0, sizeof(ep));
     ep.mode = C2R_RESIDUAL;
@@ -1134,7 +1347,7 @@ static sfw_status residual_and_loss(sfw_plan* p, const float* y, const sfw_atoms
 static sfw_status loss_gradient(sfw_plan* p, const sfw_atoms* atoms, double lambda, const float* r,
                                 double* grad_out, cudaStream_t st) {
     AtomsDev a = to_dev(atoms);
-    SFW_TRY(blur_transpose(p->blur, r, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
+    SFW_TRY(plan_transpose(p, r, p->bE, st));
     return launch_atom_grad(a, p->E, p->R, p->eps, p->bE, lambda, p->grad_parts, grad_out,
                             p->adj_ctr, st);
 }
@@ -1222,6 +1435,7 @@ sfw_status sfw_step(sfw_plan* p, const float* y, const sfw_atoms* atoms, double 
     const bool same = p->step_seen && key == p->step_key;
     if (same && p->step_exec) {
         SFW_CUDA(cudaGraphLaunch(p->step_exec, st));
+        SFW_CUDA(cudaEventRecord(p->ev_graph, st));
         return SFW_OK;
     }
     if (same) {
@@ -1241,11 +1455,13 @@ sfw_status sfw_step(sfw_plan* p, const float* y, const sfw_atoms* atoms, double 
         if (ei != cudaSuccess) return cuda_fail(ei, "sfw_step graph instantiate");
         p->step_exec = ex;
         SFW_CUDA(cudaGraphLaunch(p->step_exec, st));
+        SFW_CUDA(cudaEventRecord(p->ev_graph, st));
         return SFW_OK;
     }
     if (p->step_exec) {
-        // the arguments changed: the cached graph is dropped once its launches are done
-        SFW_CUDA(cudaDeviceSynchronize());
+        // the arguments changed: the cached graph is dropped once its last launch is done
+        // (an event after each launch: no device-wide synchronisation)
+        SFW_CUDA(cudaEventSynchronize(p->ev_graph));
         cudaGraphExecDestroy(p->step_exec);
         p->step_exec = nullptr;
     }
@@ -1266,6 +1482,31 @@ sfw_status sfw_certificate_grid(sfw_plan* p, const float* residual, double lambd
 static sfw_status certificate_impl(sfw_plan* p, const float* residual, double lambda, float* eta_out,
                                    float* max_out, int32_t* argk_out, float* best_val,
                                    int64_t* best_idx, cudaStream_t st) {
+    if (p->route_cert == SFW_ROUTE_DIRECT) {
+        // b = Phi^T r on E, then eta_k(m) = (1/lambda) sum_t g_k(t - m) b(t) by direct sums
+        if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the FFT route only");
+        SFW_TRY(launch_direct_transpose(residual, p->psf, p->n, p->R, p->bE_cert, p->num_sms, st));
+        DirectCert c;
+        memset(&c, 0, sizeof(c));
+        c.bE = p->bE_cert;
+        c.gtab = p->gtab;
+        c.kern = p->gkern;
+        c.K = p->K;
+        for (int a = 0; a < 3; ++a) {
+            c.n[a] = p->n[a];
+            c.R[a] = p->R[a];
+        }
+        c.scale = (float)(1.0 / lambda);
+        c.eta_out = eta_out;
+        c.max_out = max_out;
+        c.argk_out = argk_out;
+        c.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+        c.counter = p->ctr + 1;
+        c.best_val = best_val;
+        c.best_idx = best_idx;
+        c.num_sms = p->num_sms;
+        return launch_direct_cert(c, st);
+    }
     const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
     const int P0 = p->Pc[0], P1 = p->Pc[1], P2 = p->Pc[2], H2 = p->H2c;
     const int K = p->K;
@@ -1485,12 +1726,7 @@ sfw_status sfw_gram(sfw_plan* p, const sfw_atoms* atoms, const float* y, double*
     for (int i = 0; i < N; ++i) {
         SFW_TRY(launch_unit_atom(a, i, p->unit_slot, st));
         SFW_TRY(launch_render(unit, p->E, p->R, p->eps, p->fE, st));
-        C2RPass ep;
-        memset(&ep, 0, sizeof(ep));
-        ep.mode = C2R_STORE;
-        ep.scale = 1.f;
-        ep.out = p->gram_cols + (size_t)i * (size_t)p->V;
-        SFW_TRY(blur_forward(p->blur, p->fE, p->Hspec, SPEC_C64, p->bufA, p->bufB, ep, st, nullptr));
+        SFW_TRY(plan_blur_store(p, p->fE, p->gram_cols + (size_t)i * (size_t)p->V, st));
     }
     return launch_gram(p->gram_cols, y, N, p->V, G_out, c_out, st);
 }
@@ -1511,7 +1747,7 @@ sfw_status sfw_certificate_topk(sfw_plan* p, const float* residual, double lambd
                         p->cand_idx, st));
     // 3. parameter rows (voxel position, sigma_k, d_k) and their FP32 re-score
     SFW_TRY(launch_candidate_theta(p->cand_idx, p->vargk, p->grid_sd, topk, p->n, p->cand_theta, st));
-    SFW_TRY(blur_transpose(p->blur, residual, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
+    SFW_TRY(plan_transpose(p, residual, p->bE, st));
     AtomsDev pts;
     pts.N = topk;
     pts.m = p->cand_theta;
@@ -1534,7 +1770,7 @@ sfw_status sfw_eta_points(sfw_plan* p, const float* residual, double lambda, int
     if (P < 1 || P > p->grad_parts_atoms) return fail(SFW_ERR_ARG, "P must be in [1, %d]", p->grad_parts_atoms);
     if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    SFW_TRY(blur_transpose(p->blur, residual, p->Hspec, SPEC_C64, p->bufA, p->bufB, p->bE, st));
+    SFW_TRY(plan_transpose(p, residual, p->bE, st));
     AtomsDev pts;
     pts.N = P;
     pts.m = theta;
@@ -1547,8 +1783,6 @@ sfw_status sfw_eta_points(sfw_plan* p, const float* residual, double lambda, int
                              grad_out, p->adj_ctr, st);
 }
 
-// Test hook (not part of the public header): copy an internal plan buffer to
-// host memory.  which: 0 = rendered atoms on E, 1 = H spectrum, 2 = back-projection on E.
 sfw_status sfw_plan_check(sfw_plan* p) {
     clear_error();
     if (!p) return fail(SFW_ERR_ARG, "plan is NULL");
@@ -1561,11 +1795,114 @@ sfw_status sfw_plan_check(sfw_plan* p) {
     return fail(SFW_ERR_TIMEOUT, "a certificate-tail CTA gave up waiting for its slab copies");
 }
 
+sfw_status sfw_autotune(sfw_plan* p, const char* cache_path, void* stream) {
+    clear_error();
+    if (!p) return fail(SFW_ERR_ARG, "plan is NULL");
+    if (p->route != SFW_ROUTE_AUTO) return SFW_OK;
+    if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "not while a batch records");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        SFW_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return fail(SFW_ERR_ARG, "sfw_autotune cannot be captured");
+    }
+    if (p->step_exec) {
+        // sfw_step's cached graph holds the launches of the routes in use: drop it
+        SFW_CUDA(cudaEventSynchronize(p->ev_graph));
+        cudaGraphExecDestroy(p->step_exec);
+        p->step_exec = nullptr;
+    }
+    p->step_seen = false;
+    // cache key: shape, PSF support, certificate grid, precision
+    std::string key;
+    {
+        char buf[96];
+        snprintf(buf, sizeof(buf), "n=%d,%d,%d R=%d,%d,%d prec=%d K=%d", p->n[0], p->n[1], p->n[2], p->R[0],
+                 p->R[1], p->R[2], p->precision, p->K);
+        key = buf;
+        for (int k = 0; k < p->K; ++k) {
+            snprintf(buf, sizeof(buf), " %.7g/%.7g", p->sigmas[k], p->ds[k]);
+            key += buf;
+        }
+    }
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "r");
+        if (f) {
+            char line[8192];
+            while (fgets(line, sizeof(line), f)) {
+                const size_t kl = key.size();
+                int rb = 0, rc = 0;
+                if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == '|' &&
+                    sscanf(line + kl + 1, "%d %d", &rb, &rc) == 2 &&
+                    (rb == SFW_ROUTE_FFT || (rb == SFW_ROUTE_DIRECT && p->direct_ok)) &&
+                    (rc == SFW_ROUTE_FFT ? p->fft_cert || p->K == 0 : rc == SFW_ROUTE_DIRECT && p->gtab)) {
+                    fclose(f);
+                    p->route_blur = rb;
+                    p->route_cert = rc;
+                    return SFW_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    // a zero residual and a zero atom field on the plan's own buffers
+    SFW_CUDA(cudaMemsetAsync(p->r, 0, sizeof(float) * (size_t)p->V, st));
+    SFW_CUDA(cudaMemsetAsync(p->fE, 0, sizeof(float) * (size_t)p->VE, st));
+    float t_blur[3] = {-1.f, -1.f, -1.f};   // indexed by route
+    for (int rt = SFW_ROUTE_FFT; rt <= SFW_ROUTE_DIRECT; ++rt) {
+        if (rt == SFW_ROUTE_DIRECT && !p->direct_ok) continue;
+        p->route_blur = rt;
+        // the convolutions of one sliding-step evaluation: Phi on the grid, Phi^T on E
+        t_blur[rt] = time_route([&]() -> sfw_status {
+            SFW_TRY(plan_blur_store(p, p->fE, p->r, st));
+            return plan_transpose(p, p->r, p->bE, st);
+        }, st);
+    }
+    p->route_blur = (t_blur[SFW_ROUTE_DIRECT] >= 0.f && t_blur[SFW_ROUTE_DIRECT] < t_blur[SFW_ROUTE_FFT])
+                        ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
+    if (p->K > 0) {
+        SFW_CUDA(cudaMemsetAsync(p->r, 0, sizeof(float) * (size_t)p->V, st));
+        float t_cert[3] = {-1.f, -1.f, -1.f};
+        for (int rt = SFW_ROUTE_FFT; rt <= SFW_ROUTE_DIRECT; ++rt) {
+            if (rt == SFW_ROUTE_FFT && !p->fft_cert) continue;
+            if (rt == SFW_ROUTE_DIRECT && !p->gtab) continue;
+            p->route_cert = rt;
+            t_cert[rt] = time_route([&]() -> sfw_status {
+                return certificate_impl(p, p->r, 1.0, nullptr, nullptr, nullptr, p->cand_val, p->cand_idx, st);
+            }, st);
+        }
+        const bool direct = t_cert[SFW_ROUTE_DIRECT] >= 0.f &&
+                            (t_cert[SFW_ROUTE_FFT] < 0.f || t_cert[SFW_ROUTE_DIRECT] < t_cert[SFW_ROUTE_FFT]);
+        p->route_cert = direct ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
+    }
+    SFW_CUDA(cudaStreamSynchronize(st));
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s|%d %d\n", key.c_str(), p->route_blur, p->route_cert);
+            fclose(f);
+        }
+    }
+    return SFW_OK;
+}
+
+// Test hook (not part of the public header): raise the plan's timeout flag from the host,
+// as a certificate-tail CTA whose bounded wait ran out would, so that the flag -> status
+// path of sfw_plan_check is exercised without any device wait running out.
+sfw_status sfw_test_raise_timeout_flag(sfw_plan* p) {
+    clear_error();
+    if (!p) return fail(SFW_ERR_ARG, "plan is NULL");
+    if (!p->tail_err) return fail(SFW_ERR_UNSUPPORTED, "plan has no certificate tail flag");
+    const int one = 1;
+    SFW_CUDA(cudaMemcpy(p->tail_err, &one, sizeof(int), cudaMemcpyHostToDevice));
+    return SFW_OK;
+}
+
 sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_out,
                       int64_t* idx_out, void* stream) {
     clear_error();
     if (!values || !val_out || !idx_out) return fail(SFW_ERR_ARG, "pointers must be non-NULL");
-    if (count < 1 || count >= 0xffffffffll) return fail(SFW_ERR_ARG, "count must be in [1, 2^32 - 1)");
+    if (count < 1 || count >= 0xffffffffll) return fail(SFW_ERR_ARG, "count must be in [1, 2^32 - 2]");
     if (topk < 1 || topk > 64 || topk > count) return fail(SFW_ERR_ARG, "topk must be in [1, min(64, count)]");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // scratch: a small per-device buffer owned by the library (grown on demand)
@@ -1772,6 +2109,8 @@ sfw_status sfw_batch_create(int count, sfw_plan* const* plans, const sfw_batch_v
         const sfw_batch_volume& bv = vols[v];
         if (!plans[v]) return fail(SFW_ERR_ARG, "plan %d is NULL", v);
         if (plans[v]->K == 0) return fail(SFW_ERR_ARG, "plan %d has no certificate grid", v);
+        if (plans[v]->route_blur != SFW_ROUTE_FFT || plans[v]->route_cert != SFW_ROUTE_FFT || !plans[v]->fft_cert)
+            return fail(SFW_ERR_UNSUPPORTED, "plan %d: batches run the FFT route only", v);
         if (bv.N < 1 || bv.N > 4096) return fail(SFW_ERR_ARG, "volume %d: atoms outside [1, 4096]", v);
         if (!bv.y || !bv.m || !bv.sigma || !bv.d || !bv.w || !bv.residual || !bv.grad || !bv.loss ||
             !bv.best_val || !bv.best_idx)

@@ -342,6 +342,45 @@ sfw_status launch_unit_atom(const AtomsDev& a, int i, float* slot, cudaStream_t 
 sfw_status launch_gram(const float* A, const float* y, int N, long long V, double* G, double* c,
                        cudaStream_t st);
 
+// ------------------------------------------------------------------ plain FP32 route (direct.cu)
+// Direct sums without transforms (the route the transform route is measured against).
+struct DirectBlur {
+    const float* fE;          // rendered atoms on E = n + 2R
+    const float* H;           // PSF (2R+1)^3, C order
+    int n[3], R[3];
+    float* out;               // store: H * f_E on the grid; residual: y - H * f_E (or NULL)
+    const float* y;           // NULL: store mode; else the observation (residual mode)
+    double* partials;         // residual: one double per block
+    int partials_len;
+    unsigned int* counter;    // residual: last-block counter, zero between calls
+    double* loss_out;         // residual: C = 1/2 sum r^2 + lambda sum w, or NULL
+    const float* w;
+    int nw;
+    double lambda;
+    int num_sms;
+};
+sfw_status launch_direct_blur(const DirectBlur& p, cudaStream_t st);
+// b_E = H^T r on the extended grid.
+sfw_status launch_direct_transpose(const float* r, const float* H, const int n[3], const int R[3],
+                                   float* bE, int num_sms, cudaStream_t st);
+struct DirectCert {
+    const float* bE;          // H^T r on E
+    const float* gtab;        // unit atoms g_k on their boxes (2h_k + 1)^3
+    const int2* kern;         // per k: (offset in gtab, h_k)
+    int K;
+    int n[3], R[3];
+    float scale;              // 1 / lambda
+    float* eta_out;           // K x V or NULL
+    float* max_out;           // V or NULL
+    int* argk_out;            // V or NULL
+    unsigned long long* best_key;  // one key, zero between calls, or NULL
+    unsigned int* counter;
+    float* best_val;
+    int64_t* best_idx;
+    int num_sms;
+};
+sfw_status launch_direct_cert(const DirectCert& p, cudaStream_t st);
+
 // ------------------------------------------------------------------ non-FFT ops as descriptors
 // (one launch each, or grouped over the volumes of a batch)
 
@@ -409,7 +448,7 @@ extern thread_local Recorder* g_recorder;
 // dst[p] = src box value with circular placement (see definitions in reduce.cu)
 sfw_status launch_wrap_psf(const float* psf, const int R[3], const int P[3], float* out,
                            cudaStream_t st);
-sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int P[3], float* out,
+sfw_status launch_wrap_kernel(const float* kx, const int n[3], const int h[3], const int P[3], float* out,
                               cudaStream_t st);
 sfw_status launch_argmax_keys(const float* v, long long count, unsigned long long* partial,
                               int nblocks, cudaStream_t st);

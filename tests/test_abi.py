@@ -60,6 +60,20 @@ def test_host_argument_checks_need_no_gpu(built):
     assert e.value.status == 1
     with pytest.raises(_abi.SfwError):
         _abi.sfw_slide_loss_grad(0, 0, _abi.Atoms(), 1.0, 0, 0, 0, 0)
+    # an unknown route is refused before any device work
+    import numpy as np
+    psf = np.full((3, 3, 3), 1.0 / 27, np.float32)
+    d = _abi.PlanDesc()
+    d.n[:] = [8, 8, 8]
+    d.R[:] = [1, 1, 1]
+    d.psf = psf.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    d.route = 9
+    with pytest.raises(_abi.SfwError) as e:
+        _abi.sfw_plan_create(d)
+    assert e.value.status == 1 and "route" in str(e.value)
+    with pytest.raises(_abi.SfwError) as e:
+        _abi.sfw_autotune(0, None, 0)                  # NULL plan
+    assert e.value.status == 1
     assert _abi.sfw_launch_count() == 0
 
 

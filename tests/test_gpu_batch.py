@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import sfw_inputs
+from parity_util import assert_argmax
 
 pytestmark = pytest.mark.gpu
 
@@ -99,3 +100,40 @@ def test_batch_equals_single_calls_and_graph_replay(sfw, oracle_mod, tmp_path):
     torch.cuda.synchronize()
     assert torch.equal(batch.loss, ref_loss)
     assert torch.equal(batch.best_idx, ref_idx)
+
+
+def test_batch_with_128_volume_and_bf16_plan(sfw, oracle_mod):
+    """The largest member of the uneven batch (128^3) and a bf16-table plan in one batch: every
+    volume equals its single calls (loss, gradient, residual bit-identical; grid argmax), and
+    the 128^3 volume matches the FP64 oracle (loss 1e-5, gradient 1e-4, grid argmax)."""
+    import torch
+    shapes = [(128, 128, 128), (64, 64, 64), (48, 48, 48)]
+    vols, plans, ys, atoms, lams = _make(sfw, oracle_mod, shapes)
+    vb = vols[1]
+    plans[1].close()
+    plans[1] = sfw.Plan(vb.n, vb.R, vb.psf, vb.grid_sigmas, vb.grid_ds, precision="bf16")
+    batch = sfw.Batch(plans, ys, atoms, lams)
+    batch.step()
+    torch.cuda.synchronize()
+    for v in range(len(plans)):
+        loss, grad, r = plans[v].slide_loss_grad(ys[v], atoms[v], lams[v], want_residual=True)
+        c = plans[v].certificate(r, lams[v], want_max=False)
+        assert batch.loss[v].item() == loss.item()
+        assert torch.equal(batch.grad[v], grad)
+        assert torch.equal(batch.residual[v], r)
+        assert batch.best_idx[v].item() == c["best_idx"].item()
+    v = 0
+    vol = vols[v]
+    a = atoms[v]
+    m, s, d, w = (x.double().cpu().numpy() for x in (a.m, a.sigma, a.d, a.w))
+    y = ys[v].double().cpu().numpy()
+    C, g, _ = oracle_mod.loss_and_grad(vol.n, vol.R, vol.psf, y, m, s, d, w, lams[v], fft=True)
+    assert abs(batch.loss[v].item() - C) <= 1e-5 * abs(C)
+    gg = batch.grad[v].cpu().numpy()
+    assert np.max(np.abs(gg - g)) <= 1e-4 * np.max(np.abs(g))
+    eta = oracle_mod.eta_grid_fft(vol.n, vol.R, vol.psf, batch.residual[v].double().cpu().numpy(), lams[v],
+                                  vol.grid_kernels())
+    assert_argmax(int(batch.best_idx[v].item()), eta, 1e-5 * np.max(np.abs(eta)))
+    batch.close()
+    for p in plans:
+        p.close()

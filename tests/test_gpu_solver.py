@@ -118,3 +118,16 @@ def test_lambda_path_vol32(sfw, oracle_mod):
     cold = solver.sfw(plan, yd, path[2]["lambda"])
     assert abs(cold["C"] - path[2]["C"]) <= 1e-4 * abs(cold["C"])
     assert lmax > 0
+    # against the FP64 oracle: lambda_max is step 1 of Algorithm 1 on the empty measure at
+    # lambda = 1 (grid maximum of Phi^T y, then the local ascent), and the path point at
+    # 0.3 lambda_max is the oracle's Algorithm 1 solution at that lambda
+    kernels = vol.grid_kernels()
+    from oracle import oracle as oracle_core
+    _, lmax_ref, _ = oracle_core._certificate_max(vol.n, vol.R, vol.psf, y, np.zeros((0, 5)), np.zeros(0), 1.0,
+                                                   kernels, True)
+    assert abs(lmax - lmax_ref) <= 1e-5 * lmax_ref
+    ref = oracle_mod.sfw(vol.n, vol.R, vol.psf, y, path[1]["lambda"], kernels, fft=True)
+    print(f"\n[lambda path 0.3 lambda_max] oracle atoms {ref['w'].size} C {ref['C']:.9g}; "
+          f"gpu (warm start) atoms {path[1]['w'].size} C {path[1]['C']:.9g}")
+    assert path[1]["w"].size == ref["w"].size
+    assert abs(path[1]["C"] - ref["C"]) <= 1e-4 * abs(ref["C"])

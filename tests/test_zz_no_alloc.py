@@ -1,8 +1,8 @@
 """sfw_argmax_noalloc: the arg-maximum / top-k for callers that cannot allocate device memory.
 
-Callers under a global-mode stream capture, callers whose device memory belongs to another
-allocator, and loops that must not let a cudaFree synchronise the device cannot use a routine
-that allocates its own scratch.  sfw_argmax_noalloc uses a static device array of the library
+Callers whose device memory belongs to another allocator or a fixed budget, and loops that must
+not let the cudaFree of a re-allocation synchronise the device, cannot use a routine that
+allocates its own scratch.  sfw_argmax_noalloc uses a static device array of the library
 instead.  This test calls it through the C ABI twice in a row (different sizes and top-k, so
 stale scratch contents from the first call would show up in the second) and checks each result
 against sfw_argmax, the entry point that allocates.  Results are index work: they must match
