@@ -165,6 +165,10 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- roofline model
 
+def _r16(x: int) -> int:
+    return (x + 15) // 16 * 16
+
+
 def algorithmic_bytes(tag: str, plan, vol) -> float:
     """Bytes a pass must read and write (its inputs and outputs, once), per launch."""
     n0, n1, n2 = vol.n
@@ -185,6 +189,11 @@ def algorithmic_bytes(tag: str, plan, vol) -> float:
         "cert_c2c_inv": K * n0 * Pc[1] * H2c * c8 + K * n0 * n1 * H2c * c8,
         "cert_c2r_max": K * n0 * n1 * H2c * c8 + V * 8,
         "cert_tail": K * n0 * Pc[1] * H2c * c8,
+        # tensor-core axis-0 stage: forward spectrum X (P0 x lines), the table as per-line bf16
+        # MMA operands (kernels and points padded to multiples of 16), K output spectra
+        "cert_x0fwd": n0 * Pc[1] * H2c * c8 + Pc[0] * Pc[1] * H2c * c8,
+        "cert_axis0_tc": (Pc[0] * Pc[1] * H2c * c8 + Pc[1] * H2c * _r16(K) * _r16(Pc[0]) * 2
+                          + K * n0 * Pc[1] * H2c * c8),
         "cert_head": V * 4 + n0 * Pc[1] * H2c * c8,
         "blur_r2c": VE * 4 + E[0] * E[1] * H2 * c8,
         "blur_c2c_fwd": E[0] * E[1] * H2 * c8 + E[0] * P[1] * H2 * c8,
@@ -394,6 +403,10 @@ def run_ours(args):
     precision = "bf16" if args.workload in PRECISION_WORKLOADS else "fp32"
     topk = 64 if precision == "bf16" else 0
     plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, precision=precision)
+    # engine choice by timing (bf16 plans: the certificate's axis-0 stage on the tensor cores or
+    # in the FFT arithmetic), cached beside the clock logs
+    os.makedirs(args.clock_log, exist_ok=True)
+    engines = plan.autotune(os.path.join(args.clock_log, "engines.txt"))
     V, K = vol.V, plan.K
     y, lam = observe_on_device(sfw, plan, vol, dev)
     est = current_estimate(sfw, vol, dev, 1000 + rank)
@@ -466,6 +479,19 @@ def run_ours(args):
             f32.close()
         plain["speedup"] = value / plain["value"]
         pplan.close()
+    # the bf16 certificate with its axis-0 stage on the tensor cores (the default engine of a
+    # bf16 plan), timed alone next to the engine in use
+    tc_line = None
+    if precision == "bf16":
+        tplan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, precision="bf16")
+        res = run.sb["residual"]
+        cb = {}
+        t_tc = time_direct(lambda: tplan.certificate(res, lam, want_max=False, out=cb), 5, dev)
+        t_use = time_direct(lambda: plan.certificate(res, lam, want_max=False, out=cb), 5, dev)
+        tc_line = {"engine_in_use": "tensor cores" if engines["tensor_cores"] else "fft",
+                   "certificate_ms_tensor_cores": t_tc, "certificate_ms_in_use": t_use,
+                   "available": bool(tplan.info["tensor_cores"])}
+        tplan.close()
 
     # ---- sliding loss + gradient alone (step 4 of Algorithm 1 repeats it): this volume, and
     # the 256 x 256 x 64, N = 100 'differentiation' workload, FFT against the plain route
@@ -537,10 +563,12 @@ def run_ours(args):
             "config": {"workload": args.workload, "volume": list(vol.n), "psf_support": [2 * r + 1 for r in vol.R],
                        "atoms": vol.N, "kernels": K, "candidates_per_step": cands,
                        "table": f"{precision} on P_cert {list(plan.info['P_cert'])}",
+                       "engines": engines,
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MB write)",
                        "timing": "CUDA graph replay per step, CUDA events per step"},
             "steps_per_s": whole_job_rate(args.steps, world, t_max / 1e3),
             "vs_plain_fp32": plain,
+            "tensor_cores": tc_line,
             "slide": slide,
             "secondary": secondary,
             "sfw_outer": outer,

@@ -70,7 +70,8 @@ enum { SFW_ROUTE_AUTO = 0, SFW_ROUTE_FFT = 1, SFW_ROUTE_DIRECT = 2 };
  *             certificate grid (step 1 of Algorithms 1 and 2): kernels
  *             k = i_sigma * n_d + i_d, sigma in [0.25, 16], d in [0.5, 4]
  *   precision SFW_PREC_FP32 (complex64 kernel-family table) or SFW_PREC_BF16
- *             (bfloat16 table, FP32 arithmetic; see sfw_certificate_grid)
+ *             (bfloat16 table; tensor-core axis-0 stage for real tables, see
+ *             sfw_certificate_grid)
  *   eps       atom truncation level for rendering and the adjoint: an atom is
  *             evaluated only where exp(-(rho/sigma)^d/2) >= eps; 0 selects
  *             1e-9
@@ -104,6 +105,9 @@ typedef struct {
     size_t workspace_bytes; /* device bytes of the plan workspace */
     int route_blur;         /* SFW_ROUTE_FFT or SFW_ROUTE_DIRECT: convolutions in use */
     int route_cert;         /* SFW_ROUTE_FFT or SFW_ROUTE_DIRECT: grid certificate in use */
+    int tensor_cores;       /* 1 if the certificate's axis-0 stage runs on the tensor cores:
+                               the default of SFW_PREC_BF16 plans with a real table, FFT
+                               route and K <= 128; sfw_autotune may switch it off */
 } sfw_plan_info;
 
 /* Atom set (DEVICE memory, FP32, structure of arrays).
@@ -127,14 +131,16 @@ typedef struct {
  * SFW_ERR_ALLOC, SFW_ERR_CUDA. */
 sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out);
 
-/* Route choice of an SFW_ROUTE_AUTO plan (FFT vs DIRECT, separately for the
- * convolutions and for the grid certificate).  Times each route of each
- * operation on the plan's own workspace (a zero residual, one warm-up and three
- * timed runs, CUDA events on stream) and keeps the faster one.  With
- * cache_path (host string, may be NULL) the choice is looked up in that text
- * file first, keyed by the plan's shape, PSF support, grid and precision, and
- * appended to it after timing.  Synchronous; not capturable.  Plans created
- * with a fixed route keep it (SFW_OK, nothing timed). */
+/* Engine choice by timing (no counterpart in the paper).  For an SFW_ROUTE_AUTO
+ * plan: FFT or DIRECT, separately for the convolutions and for the grid
+ * certificate.  For a plan whose certificate can run its axis-0 stage on the
+ * tensor cores (SFW_PREC_BF16, real table): tensor cores or the FFT
+ * arithmetic.  Each candidate is timed on the plan's own workspace (a zero
+ * residual, one warm-up and three timed runs, CUDA events on stream) and the
+ * faster one kept.  With cache_path (host string, may be NULL) the choice is
+ * looked up in that text file first, keyed by the plan's shape, PSF support,
+ * grid, precision and route, and appended to it after timing.  Synchronous;
+ * not capturable.  A plan with nothing to choose returns SFW_OK at once. */
 sfw_status sfw_autotune(sfw_plan* plan, const char* cache_path, void* stream);
 
 /* Free a plan and its device memory (synchronises the device). NULL is a no-op. */
@@ -144,9 +150,10 @@ sfw_status sfw_plan_destroy(sfw_plan* plan);
 sfw_status sfw_plan_query(const sfw_plan* plan, sfw_plan_info* info);
 
 /* Device-side health of a plan (no counterpart in the paper).  Kernels that
- * wait on the copy engine (the certificate tail's TMA slab copies) give up
- * after a bounded number of polls, leave their results unspecified and set a
- * flag of the plan instead of hanging.  This call synchronises the device,
+ * wait on the copy engine or the tensor cores (the certificate tail's TMA slab
+ * copies; the tensor-core axis-0 stage's bulk copies and MMA completions) give
+ * up after a bounded number of polls, leave their results unspecified and set
+ * a flag of the plan instead of hanging.  This call synchronises the device,
  * returns SFW_ERR_TIMEOUT if the flag is set (and clears it), else SFW_OK. */
 sfw_status sfw_plan_check(sfw_plan* plan);
 
@@ -172,7 +179,10 @@ sfw_status sfw_forward(sfw_plan* plan, const sfw_atoms* atoms, float* y_out, voi
  *             local ascent).  If any eta is NaN, best_idx = -1 and best_val =
  *             NaN (the call itself cannot see it: it does not synchronise).
  * With precision SFW_PREC_BF16 the table is read as bfloat16 (values carry
- * ~3 significant digits); sfw_eta_points re-evaluates candidates in FP32. */
+ * ~3 significant digits); with a real table (even PSF) the axis-0 stage of the
+ * correlation then runs on the tensor cores: bf16 operands (the table and the
+ * twiddled residual spectrum), FP32 accumulation.  sfw_eta_points re-evaluates
+ * candidates in FP32. */
 sfw_status sfw_certificate_grid(sfw_plan* plan, const float* residual, double lambda,
                                 float* eta_out, float* max_out, int32_t* argk_out,
                                 float* best_val, int64_t* best_idx, void* stream);

@@ -128,14 +128,17 @@ class Plan:
         self.info = {"E": tuple(info.E), "P_conv": tuple(info.P_conv), "P_cert": tuple(info.P_cert),
                      "K": info.K, "real_table": bool(info.real_table),
                      "table_bytes": int(info.table_bytes), "workspace_bytes": int(info.workspace_bytes),
-                     "route_blur": names[info.route_blur], "route_cert": names[info.route_cert]}
+                     "route_blur": names[info.route_blur], "route_cert": names[info.route_cert],
+                     "tensor_cores": bool(info.tensor_cores)}
 
     def autotune(self, cache_path: Optional[str] = None, stream=None) -> dict:
-        """Pick FFT or DIRECT per operation for a route="auto" plan (libsfw ``sfw_autotune``);
-        returns the routes in use."""
+        """Engine choice by timing (libsfw ``sfw_autotune``): FFT or DIRECT per operation for a
+        route="auto" plan, tensor cores or not for the axis-0 stage of a bf16 plan; returns the
+        choices in use."""
         sfw_autotune(self.handle, cache_path, _stream_ptr(stream))
         self._query()
-        return {"blur": self.info["route_blur"], "cert": self.info["route_cert"]}
+        return {"blur": self.info["route_blur"], "cert": self.info["route_cert"],
+                "tensor_cores": self.info["tensor_cores"]}
 
     def close(self):
         if getattr(self, "handle", None):

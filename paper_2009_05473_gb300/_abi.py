@@ -50,7 +50,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("E", ctypes.c_int * 3), ("P_conv", ctypes.c_int * 3), ("P_cert", ctypes.c_int * 3),
                 ("K", ctypes.c_int), ("real_table", ctypes.c_int), ("table_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("route_blur", ctypes.c_int),
-                ("route_cert", ctypes.c_int)]
+                ("route_cert", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Atoms(ctypes.Structure):

@@ -177,6 +177,8 @@ static const PassTags kTableTags = {"table_r2c", "table_c2c_fwd", "table_axis0",
                                     "table_head", "table_tail"};
 static const char* const kCertHeadTag = "cert_head";
 static const char* const kCertTailTag = "cert_tail";
+static const char* const kCertX0Tag = "cert_x0fwd";      // forward axis-0 spectrum (tensor-core path)
+static const char* const kCertTcTag = "cert_axis0_tc";   // axis-0 inverse on the tensor cores
 static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max",
                                    nullptr, nullptr};
 
@@ -665,6 +667,14 @@ struct sfw_plan {
     float* gtab;                   // unit atoms g_k on their boxes (direct certificate)
     int2* gkern;                   // per k: (offset in gtab, half-width)
     float* bE_cert;                // H^T r of the direct certificate (bE belongs to the gradient)
+    // tensor-core axis-0 pass (real bf16 tables): the table as per-line MMA operands and the
+    // forward axis-0 spectrum of the residual
+    bool tc_ready;                 // the tensor-core operands exist
+    bool tc;                       // the certificate's axis-0 stage runs on the tensor cores
+    __nv_bfloat16* tc_table;
+    __nv_bfloat16* tc_dft;         // the inverse DFT rows (A operands), per half of the n0 rows
+    int tc_Kp, tc_Np;
+    float2* cX;
     double* dir_parts;             // criterion partials of the direct blur
     int dir_parts_len;
 };
@@ -821,6 +831,22 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
             p->table_stride = spec_elems;
         }
         p->table_bytes = esz * (size_t)K * (size_t)p->table_stride;
+        if (p->precision == SFW_PREC_BF16 && p->real_table) {
+            // the tensor-core axis-0 pass: T_l per line as the MMA's B operand (Np kernels x Kp
+            // points, bf16); the plain bf16 table below stays for batches (recorded FFT passes)
+            const int Kp = (p->Pc[0] + 31) / 32 * 32, Np = (K + 15) / 16 * 16;
+            if (Np <= 128 && tc_smem_bytes(Kp, Np, p->Pc[0]) <= 227u * 1024u) {
+                p->tc_Kp = Kp;
+                p->tc_Np = Np;
+                if ((st_ret = plan_alloc_t(p, &p->tc_table, (size_t)nl * Np * Kp))) break;
+                if ((st_ret = plan_alloc_t(p, &p->cX, (size_t)nl * p->Pc[0]))) break;
+                if ((st_ret = launch_tc_table(full, spec_elems, K, p->Pc[0], nl, Np, Kp, p->tc_table, st))) break;
+                const size_t halves = (size_t)((p->n[0] + 63) / 64);
+                if ((st_ret = plan_alloc_t(p, &p->tc_dft, halves * 128 * 2 * (size_t)Kp))) break;
+                if ((st_ret = launch_tc_dft(p->n[0], p->Pc[0], Kp, p->tc_dft, st))) break;
+                p->tc_ready = p->tc = true;
+            }
+        }
         if ((st_ret = plan_alloc(p, &p->table, p->table_bytes))) break;
         if (cudaMemsetAsync(p->table, 0, p->table_bytes, st) != cudaSuccess) {
             st_ret = cuda_fail(cudaGetLastError(), "table clear");
@@ -1279,6 +1305,7 @@ sfw_status sfw_plan_query(const sfw_plan* p, sfw_plan_info* info) {
         info->P_cert[a] = p->fft_cert ? p->Pc[a] : 0;
     }
     info->route_blur = p->route_blur;
+    info->tensor_cores = p->tc ? 1 : 0;
     info->route_cert = p->K ? p->route_cert : 0;
     info->K = p->K;
     info->real_table = p->real_table;
@@ -1565,7 +1592,47 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
             }
         }
     }
-    {   // axis 0: forward once, then for each kernel k: times table_k, inverse -> (K, n0, P1, H2)
+    if (p->tc && !g_recorder) {
+        // axis 0 on the tensor cores: forward transform of the (n0, P1, H2) lines into X
+        // (P0, P1 H2), then U_k = W diag(X) T_k for all kernels as one bf16 GEMM per line
+        const long long nl = (long long)P1 * H2;
+        C2CPass f;
+        f.in = p->cB;
+        f.out = p->cX;
+        f.lin = ls(0, 1, nl, nl);
+        f.lout = ls(0, 1, nl, nl);
+        f.nlines = nl;
+        f.L = P0;
+        f.in_off = 0;
+        f.in_len = n0;
+        f.out_off = 0;
+        f.out_len = P0;
+        f.dir = -1;
+        f.scale = 1.f;
+        f.fac = p->facc[0];
+        f.tw = p->twc[0];
+        {
+            LaunchTag lt__(kCertX0Tag);
+            SFW_TRY(launch_c2c(f, st));
+        }
+        Axis0TcPass a;
+        memset(&a, 0, sizeof(a));
+        a.X = p->cX;
+        a.A = p->tc_dft;
+        a.Tb = p->tc_table;
+        a.out = p->cC;
+        a.lout = (slabs && p->tail_tma) ? ls(4LL * n0, 1, 4, 4) : ls(0, 1, nl, nl);
+        a.out_stride = (long long)n0 * nl;
+        a.nl = nl;
+        a.P0 = P0;
+        a.Kp = p->tc_Kp;
+        a.n0 = n0;
+        a.K = K;
+        a.Np = p->tc_Np;
+        a.err = p->tail_err;
+        LaunchTag lt__(kCertTcTag);
+        SFW_TRY(launch_axis0_tc(a, p->num_sms, st));
+    } else {   // axis 0: forward once, then for each kernel k: times table_k, inverse -> (K, n0, P1, H2)
         MulPass q;
         const long long nl = (long long)P1 * H2;
         q.in = p->cB;
@@ -1792,13 +1859,15 @@ sfw_status sfw_plan_check(sfw_plan* p) {
     SFW_CUDA(cudaMemcpy(&flag, p->tail_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (!flag) return SFW_OK;
     SFW_CUDA(cudaMemset(p->tail_err, 0, sizeof(int)));
-    return fail(SFW_ERR_TIMEOUT, "a certificate-tail CTA gave up waiting for its slab copies");
+    return fail(SFW_ERR_TIMEOUT, "a certificate kernel gave up a bounded wait (slab copies or tensor-core MMAs)");
 }
 
 sfw_status sfw_autotune(sfw_plan* p, const char* cache_path, void* stream) {
     clear_error();
     if (!p) return fail(SFW_ERR_ARG, "plan is NULL");
-    if (p->route != SFW_ROUTE_AUTO) return SFW_OK;
+    const bool tune_routes = p->route == SFW_ROUTE_AUTO;
+    const bool tune_tc = p->tc_ready;
+    if (!tune_routes && !tune_tc) return SFW_OK;
     if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "not while a batch records");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     {
@@ -1813,12 +1882,12 @@ sfw_status sfw_autotune(sfw_plan* p, const char* cache_path, void* stream) {
         p->step_exec = nullptr;
     }
     p->step_seen = false;
-    // cache key: shape, PSF support, certificate grid, precision
+    // cache key: shape, PSF support, certificate grid, precision, requested route
     std::string key;
     {
-        char buf[96];
-        snprintf(buf, sizeof(buf), "n=%d,%d,%d R=%d,%d,%d prec=%d K=%d", p->n[0], p->n[1], p->n[2], p->R[0],
-                 p->R[1], p->R[2], p->precision, p->K);
+        char buf[112];
+        snprintf(buf, sizeof(buf), "n=%d,%d,%d R=%d,%d,%d prec=%d route=%d K=%d", p->n[0], p->n[1], p->n[2],
+                 p->R[0], p->R[1], p->R[2], p->precision, p->route, p->K);
         key = buf;
         for (int k = 0; k < p->K; ++k) {
             snprintf(buf, sizeof(buf), " %.7g/%.7g", p->sigmas[k], p->ds[k]);
@@ -1831,14 +1900,16 @@ sfw_status sfw_autotune(sfw_plan* p, const char* cache_path, void* stream) {
             char line[8192];
             while (fgets(line, sizeof(line), f)) {
                 const size_t kl = key.size();
-                int rb = 0, rc = 0;
+                int rb = 0, rc = 0, tcu = 0;
                 if (strncmp(line, key.c_str(), kl) == 0 && line[kl] == '|' &&
-                    sscanf(line + kl + 1, "%d %d", &rb, &rc) == 2 &&
+                    sscanf(line + kl + 1, "%d %d %d", &rb, &rc, &tcu) == 3 &&
                     (rb == SFW_ROUTE_FFT || (rb == SFW_ROUTE_DIRECT && p->direct_ok)) &&
-                    (rc == SFW_ROUTE_FFT ? p->fft_cert || p->K == 0 : rc == SFW_ROUTE_DIRECT && p->gtab)) {
+                    (rc == SFW_ROUTE_FFT ? p->fft_cert || p->K == 0 : rc == SFW_ROUTE_DIRECT && p->gtab) &&
+                    (!tcu || p->tc_ready)) {
                     fclose(f);
                     p->route_blur = rb;
                     p->route_cert = rc;
+                    p->tc = tcu != 0;
                     return SFW_OK;
                 }
             }
@@ -1848,38 +1919,50 @@ sfw_status sfw_autotune(sfw_plan* p, const char* cache_path, void* stream) {
     // a zero residual and a zero atom field on the plan's own buffers
     SFW_CUDA(cudaMemsetAsync(p->r, 0, sizeof(float) * (size_t)p->V, st));
     SFW_CUDA(cudaMemsetAsync(p->fE, 0, sizeof(float) * (size_t)p->VE, st));
-    float t_blur[3] = {-1.f, -1.f, -1.f};   // indexed by route
-    for (int rt = SFW_ROUTE_FFT; rt <= SFW_ROUTE_DIRECT; ++rt) {
-        if (rt == SFW_ROUTE_DIRECT && !p->direct_ok) continue;
-        p->route_blur = rt;
-        // the convolutions of one sliding-step evaluation: Phi on the grid, Phi^T on E
-        t_blur[rt] = time_route([&]() -> sfw_status {
-            SFW_TRY(plan_blur_store(p, p->fE, p->r, st));
-            return plan_transpose(p, p->r, p->bE, st);
+    auto time_cert = [&]() {
+        return time_route([&]() -> sfw_status {
+            return certificate_impl(p, p->r, 1.0, nullptr, nullptr, nullptr, p->cand_val, p->cand_idx, st);
         }, st);
-    }
-    p->route_blur = (t_blur[SFW_ROUTE_DIRECT] >= 0.f && t_blur[SFW_ROUTE_DIRECT] < t_blur[SFW_ROUTE_FFT])
-                        ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
-    if (p->K > 0) {
-        SFW_CUDA(cudaMemsetAsync(p->r, 0, sizeof(float) * (size_t)p->V, st));
-        float t_cert[3] = {-1.f, -1.f, -1.f};
+    };
+    if (tune_routes) {
+        float t_blur[3] = {-1.f, -1.f, -1.f};   // indexed by route
         for (int rt = SFW_ROUTE_FFT; rt <= SFW_ROUTE_DIRECT; ++rt) {
-            if (rt == SFW_ROUTE_FFT && !p->fft_cert) continue;
-            if (rt == SFW_ROUTE_DIRECT && !p->gtab) continue;
-            p->route_cert = rt;
-            t_cert[rt] = time_route([&]() -> sfw_status {
-                return certificate_impl(p, p->r, 1.0, nullptr, nullptr, nullptr, p->cand_val, p->cand_idx, st);
+            if (rt == SFW_ROUTE_DIRECT && !p->direct_ok) continue;
+            p->route_blur = rt;
+            // the convolutions of one sliding-step evaluation: Phi on the grid, Phi^T on E
+            t_blur[rt] = time_route([&]() -> sfw_status {
+                SFW_TRY(plan_blur_store(p, p->fE, p->r, st));
+                return plan_transpose(p, p->r, p->bE, st);
             }, st);
         }
-        const bool direct = t_cert[SFW_ROUTE_DIRECT] >= 0.f &&
-                            (t_cert[SFW_ROUTE_FFT] < 0.f || t_cert[SFW_ROUTE_DIRECT] < t_cert[SFW_ROUTE_FFT]);
-        p->route_cert = direct ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
+        p->route_blur = (t_blur[SFW_ROUTE_DIRECT] >= 0.f && t_blur[SFW_ROUTE_DIRECT] < t_blur[SFW_ROUTE_FFT])
+                            ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
+        if (p->K > 0) {
+            float t_cert[3] = {-1.f, -1.f, -1.f};
+            for (int rt = SFW_ROUTE_FFT; rt <= SFW_ROUTE_DIRECT; ++rt) {
+                if (rt == SFW_ROUTE_FFT && !p->fft_cert) continue;
+                if (rt == SFW_ROUTE_DIRECT && !p->gtab) continue;
+                p->route_cert = rt;
+                t_cert[rt] = time_cert();
+            }
+            const bool direct = t_cert[SFW_ROUTE_DIRECT] >= 0.f &&
+                                (t_cert[SFW_ROUTE_FFT] < 0.f || t_cert[SFW_ROUTE_DIRECT] < t_cert[SFW_ROUTE_FFT]);
+            p->route_cert = direct ? SFW_ROUTE_DIRECT : SFW_ROUTE_FFT;
+        }
+    }
+    if (tune_tc && p->route_cert == SFW_ROUTE_FFT) {
+        // the certificate's axis-0 stage: tensor cores against the FP32-arithmetic transform
+        p->tc = false;
+        const float t_fft = time_cert();
+        p->tc = true;
+        const float t_tc = time_cert();
+        p->tc = t_tc >= 0.f && (t_fft < 0.f || t_tc < t_fft);
     }
     SFW_CUDA(cudaStreamSynchronize(st));
     if (cache_path) {
         FILE* f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s|%d %d\n", key.c_str(), p->route_blur, p->route_cert);
+            fprintf(f, "%s|%d %d %d\n", key.c_str(), p->route_blur, p->route_cert, p->tc ? 1 : 0);
             fclose(f);
         }
     }

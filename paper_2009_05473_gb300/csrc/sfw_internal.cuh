@@ -342,6 +342,29 @@ sfw_status launch_unit_atom(const AtomsDev& a, int i, float* slot, cudaStream_t 
 sfw_status launch_gram(const float* A, const float* y, int N, long long V, double* G, double* c,
                        cudaStream_t st);
 
+// ------------------------------------------------------------------ tensor cores (cert_tc.cu)
+// The certificate's axis-0 inverse for real bf16 tables on tcgen05: per line l,
+// U_k[i0, l] = sum_p0 e^{2 pi i i0 p0 / P0} X[p0, l] T_k[p0, l] for all kernels k at once.
+struct Axis0TcPass {
+    const float2* X;            // forward axis-0 spectra (P0, nl): X[p0 * nl + l]
+    const __nv_bfloat16* A;     // per half of the output rows: 128 x 2 Kp real form of the inverse DFT rows
+    const __nv_bfloat16* Tb;    // per line: T_l as the Np x Kp bf16 B operand in the MMA layout
+    float2* out;                // U_k[i0, l] at out + k * out_stride + line_offset(lout, l) + i0 * lout.Sj
+    LineSet lout;
+    long long out_stride;
+    long long nl;               // lines (P1 * H2)
+    int P0, Kp;                 // transform length, padded to a multiple of 16
+    int n0;                     // kept output rows
+    int K, Np;                  // kernels, padded to a multiple of 16 (<= 128)
+    int* err;                   // set if a bounded wait ran out
+};
+sfw_status launch_tc_table(const float2* full, long long spec_elems, int K, int P0, long long nl, int Np,
+                           int Kp, __nv_bfloat16* Tb, cudaStream_t st);
+sfw_status launch_axis0_tc(const Axis0TcPass& p, int num_sms, cudaStream_t st);
+// The A operands of launch_axis0_tc: ceil(n0 / 64) blocks of 128 x 2 Kp bf16.
+sfw_status launch_tc_dft(int n0, int P0, int Kp, __nv_bfloat16* A, cudaStream_t st);
+size_t tc_smem_bytes(int Kp, int Np, int P0);
+
 // ------------------------------------------------------------------ plain FP32 route (direct.cu)
 // Direct sums without transforms (the route the transform route is measured against).
 struct DirectBlur {

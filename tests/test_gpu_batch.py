@@ -121,7 +121,12 @@ def test_batch_with_128_volume_and_bf16_plan(sfw, oracle_mod):
         assert batch.loss[v].item() == loss.item()
         assert torch.equal(batch.grad[v], grad)
         assert torch.equal(batch.residual[v], r)
-        assert batch.best_idx[v].item() == c["best_idx"].item()
+        if plans[v].info["tensor_cores"]:
+            # a batch records the FFT passes on the bf16 table; a single call on a bf16 plan
+            # runs the axis-0 stage on the tensor cores: both carry bf16 rounding
+            assert abs(batch.best_val[v].item() - c["best_val"].item()) <= 1e-2 * abs(c["best_val"].item())
+        else:
+            assert batch.best_idx[v].item() == c["best_idx"].item()
     v = 0
     vol = vols[v]
     a = atoms[v]

@@ -169,7 +169,8 @@ def test_auto_route_autotune_and_cache(sfw, oracle_mod, torch_mod, tmp_path):
     ref = oracle_mod.eta_grid(n, R, vol.psf, y32.astype(np.float64), lam, kernels)
     assert _rel_inf(out["eta"].cpu().numpy(), ref) <= RTOL
     fixed = sfw.Plan(n, R, vol.psf, vol.grid_sigmas, vol.grid_ds, route="fft")
-    assert fixed.autotune(cache) == {"blur": "fft", "cert": "fft"}   # fixed routes stay
+    fr = fixed.autotune(cache)
+    assert (fr["blur"], fr["cert"], fr["tensor_cores"]) == ("fft", "fft", False)   # nothing to choose
     for p in (plan, again, fixed):
         p.close()
 

@@ -131,3 +131,4 @@ def test_lambda_path_vol32(sfw, oracle_mod):
           f"gpu (warm start) atoms {path[1]['w'].size} C {path[1]['C']:.9g}")
     assert path[1]["w"].size == ref["w"].size
     assert abs(path[1]["C"] - ref["C"]) <= 1e-4 * abs(ref["C"])
+
