@@ -87,74 +87,84 @@ sfw_status launch_tc_dft(int n0, int P0, int Kp, __nv_bfloat16* A, cudaStream_t 
 
 // ------------------------------------------------------------------ the axis-0 GEMM pass
 
-// Dynamic shared memory of the pass (byte offsets from a 1024-aligned base; every region a
-// multiple of 1024 bytes, as the 128-byte swizzle wants).
+// A tile is LT = 128 / Np lines x Np kernels = 128 columns (the N of every MMA); K runs over
+// blocks of 64 points p0, each block contributing a Re and an Im 64-column slice of K.
+__host__ __device__ inline int tc_tile_lines(int Np) { return 128 / Np; }
+
+// Dynamic shared memory (byte offsets from a 1024-aligned base; every region a multiple of
+// 1024 bytes, as the 128-byte swizzle wants):
+//   a      A, 128 rows x 2 Kp                       (resident)
+//   b[3]   B' of a block: Re and Im slices, 128 rows x 64 each (32 KB)
+//   xs[2]  X of a tile: LT lines x Kp points, FP32 complex (one tile ahead)
+// The table pieces go from global memory (L2) straight to registers: keeping them out of
+// shared memory leaves its bandwidth to the tensor core's operand reads.
 struct TcSmem {
-    uint32_t a, b[2], t[3], xs[2], total;
+    uint32_t a, b[3], xs[2], total;
 };
 
-__host__ __device__ inline TcSmem tc_smem_layout(int Kp, int Np, int LG) {
+__host__ __device__ inline TcSmem tc_smem_layout(int Kp, int Np) {
     TcSmem s;
-    const uint32_t K2 = 2u * (uint32_t)Kp;
-    const uint32_t abytes = 128u * K2 * 2u, bbytes = (uint32_t)Np * K2 * 2u;
-    const uint32_t tbytes = (uint32_t)Np * (uint32_t)Kp * 2u, xbytes = (uint32_t)Kp * (uint32_t)LG * 8u;
+    const uint32_t abytes = 128u * 2u * (uint32_t)Kp * 2u;
+    const uint32_t bbytes = 2u * 128u * 64u * 2u;
+    const uint32_t xbytes = ((uint32_t)tc_tile_lines(Np) * (uint32_t)Kp * 8u + 1023u) & ~1023u;
     s.a = 0;
-    s.b[0] = abytes;
-    s.b[1] = abytes + bbytes;
-    for (int i = 0; i < 3; ++i) s.t[i] = abytes + 2 * bbytes + (uint32_t)i * tbytes;
-    s.xs[0] = abytes + 2 * bbytes + 3 * tbytes;
+    for (int i = 0; i < 3; ++i) s.b[i] = abytes + (uint32_t)i * bbytes;
+    s.xs[0] = abytes + 3u * bbytes;
     s.xs[1] = s.xs[0] + xbytes;
     s.total = s.xs[1] + xbytes + 1024u;   // + alignment slack of the base
     return s;
 }
 
-constexpr int kTcWorkers = 128;                 // warps 0-3: B' and the epilogue (one TMEM lane quadrant each)
-constexpr int kTcThreadsWs = kTcWorkers + 32;   // + warp 4: table copies and the MMAs
+constexpr int kTcFormWarps = 8;                   // warps 0-7: B' of every block
+constexpr int kTcEpiWarps = 4;                    // warps 8-11: results (TMEM lane quadrant = warp % 4)
+constexpr int kTcThreadsWs = 32 * (kTcFormWarps + kTcEpiWarps + 1);   // + warp 12: the MMAs
+constexpr int kTcFormThreads = 32 * kTcFormWarps;
 
-__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
+__device__ __forceinline__ void form_sync() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
 
-// One CTA per (half of the output rows, share of the line groups).  A = the real form of W's
-// 64 rows of the half (prepared at plan creation, one bulk copy):
+// One CTA per (half of the output rows, share of the tiles).  A = the real form of W's 64
+// rows of the half (prepared at plan creation, one bulk copy):
 //     row 2j   (Re U[i0]):  [ Re W[i0, :] | -Im W[i0, :] ]
 //     row 2j+1 (Im U[i0]):  [ Im W[i0, :] |  Re W[i0, :] ]      (K = 2 Kp)
-// and per line B' = [ T_l (.) Re X_l | T_l (.) Im X_l ] (Np kernels x 2 Kp).  D = A B'^T =
-// [Re U_k; Im U_k] for the line in tensor memory, LG lines side by side per buffer.
-// Warp roles: warps 0-3 build B' from the table block (three bulk-copy stages, refilled as
-// soon as a line's B' is built) and the staged X lines (copied one line group ahead), and
-// write each line group's results; one lane of warp 4 issues the table copies and the MMAs.
-// Hand-offs go through mbarriers: b_full (B' built, 4 warp arrivals), done (MMAs of a line
-// finished, tcgen05.commit), t_full (table block landed), acc_full / acc_empty (a group's
-// results ready / read).  Every wait is bounded; a wait that runs out sets p.err.
-template <int LG>
+// For every tile and block of 64 points, B'_re = T (.) Re X and B'_im = T (.) Im X (128
+// columns = LT lines x Np kernels); D (+)= A_re-block B'_re^T + A_im-block B'_im^T, so that
+// after the last block D = [Re U_k; Im U_k] for the tile's lines, in tensor memory.
+// Warp roles: warps 0-7 build B' (three stages; the table chunks read from global memory into
+// registers ahead of the stage wait, X staged a tile ahead); warps 8-11 write the results of a
+// tile while the next one accumulates (two tensor-memory buffers); one lane of warp 12 issues
+// the MMAs.  Hand-offs go through mbarriers: b_full (B' built, 8 arrivals), done (MMAs of a
+// block finished, tcgen05.commit), acc_full / acc_empty (a tile's results ready / read, 4
+// arrivals).  Every wait is bounded; a wait that runs out sets p.err.
+template <int LT>
 __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     extern __shared__ unsigned char tc_smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int Kp = p.Kp, Np = p.Np, P0 = p.P0, K2 = 2 * p.Kp;
-    const TcSmem L = tc_smem_layout(Kp, Np, LG);
-    __shared__ __align__(8) unsigned long long s_tfull[3], s_bfull[2], s_done[2], s_accf[2], s_acce[2], s_abar;
+    const int Kp = p.Kp, Np = p.Np, P0 = p.P0;
+    const int nb = Kp / 64;
+    const TcSmem L = tc_smem_layout(Kp, Np);
+    __shared__ __align__(8) unsigned long long s_bfull[3], s_done[3], s_accf[2], s_acce[2], s_abar;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t tbytes = (uint32_t)Np * (uint32_t)Kp * 2u;
-    const uint32_t idesc = tc::idesc_bf16_f32(128, Np);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, 128);
     const int halves = (p.n0 + 63) / 64;
     const int h = blockIdx.x % halves;
     const long long G = gridDim.x / halves;          // CTAs per half (the grid is a multiple)
     const long long gi = blockIdx.x / halves;
-    const long long ngroups = (p.nl + LG - 1) / LG;
-    const long long my_groups = gi < ngroups ? (ngroups - 1 - gi) / G + 1 : 0;
-    const long long my_lines = my_groups * LG;
-    auto line_of = [&](long long t) -> long long { return (gi + (t / LG) * G) * LG + (t % LG); };
-    auto tbar = [&](long long t) { return tc::smem_addr(&s_tfull[t % 3]); };
+    const long long ntiles = (p.nl + LT - 1) / LT;
+    const long long my_tiles = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
+    const long long my_blocks = my_tiles * nb;
+    auto tile_l0 = [&](long long u) -> long long { return (gi + u * G) * LT; };
 
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) tc::mbar_init(tc::smem_addr(&s_tfull[i]), 1);
-        for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(tc::smem_addr(&s_bfull[i]), 4);
+        for (int i = 0; i < 3; ++i) {
+            tc::mbar_init(tc::smem_addr(&s_bfull[i]), kTcFormWarps);
             tc::mbar_init(tc::smem_addr(&s_done[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             tc::mbar_init(tc::smem_addr(&s_accf[i]), 1);
-            tc::mbar_init(tc::smem_addr(&s_acce[i]), 4);
+            tc::mbar_init(tc::smem_addr(&s_acce[i]), kTcEpiWarps);
         }
         tc::mbar_init(tc::smem_addr(&s_abar), 1);
         tc::mbar_init_fence();
@@ -166,89 +176,89 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
 
-    if (warp == 4) {
-        // ---------------- producer / MMA lane
+    if (warp == kTcFormWarps + kTcEpiWarps) {
+        // ---------------- MMA lane
         if (lane == 0) {
-            auto issue_table = [&](long long t) {
-                const long long l = min(line_of(t), p.nl - 1);   // padding lines reuse a real block
-                tc::mbar_expect_tx(tbar(t), tbytes);
-                tc::bulk_g2s(tc::smem_addr(base + L.t[t % 3]), p.Tb + (size_t)l * (size_t)Np * (size_t)Kp, tbytes,
-                             tbar(t));
-            };
-            const uint32_t abytes = 128u * (uint32_t)K2 * 2u;
+            const uint32_t abytes = 128u * 2u * (uint32_t)Kp * 2u;
             tc::mbar_expect_tx(tc::smem_addr(&s_abar), abytes);
-            tc::bulk_g2s(tc::smem_addr(base + L.a), p.A + (size_t)h * 128u * (size_t)K2, abytes,
+            tc::bulk_g2s(tc::smem_addr(base + L.a), p.A + (size_t)h * 128u * 2u * (size_t)Kp, abytes,
                          tc::smem_addr(&s_abar));
-            for (long long t = 0; t < 3 && t < my_lines; ++t) issue_table(t);
             if (!tc::mbar_wait(tc::smem_addr(&s_abar), 0)) s_abort = 1;
             const uint32_t a0 = tc::smem_addr(base + L.a);
-            for (long long t = 0; t < my_lines && !s_abort; ++t) {
-                const long long u = t / LG;
-                const int j = (int)(t % LG), s = (int)(t & 1), b = (int)(u & 1);
-                if (j == 0 && u >= 2 && !tc::mbar_wait(tc::smem_addr(&s_acce[b]), (uint32_t)((u - 2) >> 1) & 1u)) {
+            for (long long q = 0; q < my_blocks && !s_abort; ++q) {
+                const long long u = q / nb;
+                const int b = (int)(q % nb), s = (int)(q % 3), ub = (int)(u & 1);
+                if (b == 0 && u >= 2 && !tc::mbar_wait(tc::smem_addr(&s_acce[ub]), (uint32_t)((u - 2) >> 1) & 1u)) {
                     s_abort = 1;
                     break;
                 }
-                if (!tc::mbar_wait(tc::smem_addr(&s_bfull[s]), (uint32_t)(t >> 1) & 1u)) {
+                if (!tc::mbar_wait(tc::smem_addr(&s_bfull[s]), (uint32_t)(q / 3) & 1u)) {
                     s_abort = 1;
                     break;
                 }
-                // the workers have read the table block of line t: refill its stage
-                if (t + 3 < my_lines) issue_table(t + 3);
                 tc::fence_after_sync();
-                const uint32_t b0 = tc::smem_addr(base + L.b[s]);
-                const uint32_t d = tmem + (uint32_t)(b * 128 + j * Np);
-                for (int ks = 0; ks < K2 / 16; ++ks)
-                    tc::mma_bf16(d, tc::desc_kmajor_sw128(a0 + tc::sw128_slice(ks, 128)),
-                                 tc::desc_kmajor_sw128(b0 + tc::sw128_slice(ks, Np)), idesc, ks > 0 ? 1u : 0u);
+                const uint32_t d = tmem + (uint32_t)(ub * 128);
+                const uint32_t bre = tc::smem_addr(base + L.b[s]), bim = bre + 128u * 64u * 2u;
+                // A's 64-column atoms: Re block b at column atom b, Im block b at atom nb + b
+                const uint32_t are = a0 + (uint32_t)b * 16u * 1024u, aim = a0 + (uint32_t)(nb + b) * 16u * 1024u;
+                for (int ks = 0; ks < 4; ++ks)
+                    tc::mma_bf16(d, tc::desc_kmajor_sw128(are + (uint32_t)ks * 32u),
+                                 tc::desc_kmajor_sw128(bre + (uint32_t)ks * 32u), idesc, (b > 0 || ks > 0) ? 1u : 0u);
+                for (int ks = 0; ks < 4; ++ks)
+                    tc::mma_bf16(d, tc::desc_kmajor_sw128(aim + (uint32_t)ks * 32u),
+                                 tc::desc_kmajor_sw128(bim + (uint32_t)ks * 32u), idesc, 1u);
                 tc::mma_commit(tc::smem_addr(&s_done[s]));
-                if (j == LG - 1) tc::mma_commit(tc::smem_addr(&s_accf[b]));
+                if (b == nb - 1) tc::mma_commit(tc::smem_addr(&s_accf[ub]));
             }
         }
         __syncwarp();
-    } else {
-        // ---------------- workers: B' of every line, then each group's results
-        auto stage_x = [&](long long u) {   // X lines of group u, per line contiguous (zero past the end)
+    } else if (warp < kTcFormWarps) {
+        // ---------------- B' of every block: column c' = j Np + n (line j of the tile, kernel n)
+        auto stage_x = [&](long long u) {   // X lines of tile u, per line contiguous (zero past the end)
             float2* xs = reinterpret_cast<float2*>(base + L.xs[u & 1]);
-            const long long l0 = (gi + u * G) * LG;
-            for (int e = tid; e < Kp * LG; e += kTcWorkers) {
-                const int jl = e % LG, p0 = e / LG;
+            const long long l0 = tile_l0(u);
+            for (int e = tid; e < Kp * LT; e += kTcFormThreads) {
+                const int jl = e % LT, p0 = e / LT;
                 float2* dst = xs + jl * Kp + p0;
                 if (p0 < P0 && l0 + jl < p.nl) tc::cp_async8(dst, p.X + (long long)p0 * p.nl + l0 + jl);
                 else *dst = make_float2(0.f, 0.f);
             }
             tc::cp_async_commit();
         };
-        if (my_groups > 0) stage_x(0);
-        const int m = tid, i0 = h * 64 + (m >> 1), im = m & 1;
-        const bool live = i0 < p.n0;
-        constexpr int HALF = LG >= 2 ? LG / 2 : 1;
-        const int jw = (LG >= 2 && im) ? HALF : 0;
-        const bool writer = live && (LG >= 2 || !im);
-        float2* dst0 = p.out + (long long)i0 * p.lout.Sj;
-        for (long long u = 0; u < my_groups && !s_abort; ++u) {
-            const long long l0 = (gi + u * G) * LG;
-            const int nlg = (int)min((long long)LG, p.nl - l0);
-            const int b = (int)(u & 1);
+        if (my_tiles > 0) stage_x(0);
+        constexpr int PER = 128 * 8 / kTcFormThreads;     // items (16-byte chunks) per thread and block
+        for (long long u = 0; u < my_tiles && !s_abort; ++u) {
             tc::cp_async_wait_all();
-            workers_sync();
-            if (u + 1 < my_groups) stage_x(u + 1);
+            form_sync();
+            if (u + 1 < my_tiles) stage_x(u + 1);
             const float2* xs = reinterpret_cast<const float2*>(base + L.xs[u & 1]);
-            for (int j = 0; j < LG; ++j) {
-                const long long t = u * LG + j;
-                const int s = (int)(t & 1);
-                // B'[s] is free once the MMAs of line t - 2 are done; the table block of line t landed
-                if (t >= 2 && !tc::mbar_wait(tc::smem_addr(&s_done[s]), (uint32_t)((t - 2) >> 1) & 1u)) s_abort = 1;
-                if (!tc::mbar_wait(tbar(t), (uint32_t)(t / 3) & 1u)) s_abort = 1;
+            const long long l0 = tile_l0(u);
+            for (int b = 0; b < nb; ++b) {
+                const long long q = u * nb + b;
+                const int s = (int)(q % 3);
+                // this thread's table chunks of the block, from global memory (L2) into registers
+                uint4 tv[PER];
+#pragma unroll
+                for (int r = 0; r < PER; ++r) {
+                    const int e = tid + r * kTcFormThreads;
+                    const int col = e & 127, c = e >> 7;
+                    const int j = col / Np, n = col - j * Np;
+                    const long long l = min(l0 + j, p.nl - 1);   // padding lines read a real block
+                    const unsigned char* blk = reinterpret_cast<const unsigned char*>(p.Tb + (size_t)l * (size_t)Np * (size_t)Kp);
+                    tv[r] = __ldg(reinterpret_cast<const uint4*>(blk + tc::kmajor_offset(n, 64 * b + 8 * c, Np)));
+                }
+                // B'[s] is free once the MMAs of block q - 3 are done
+                if (q >= 3 && !tc::mbar_wait(tc::smem_addr(&s_done[s]), (uint32_t)((q - 3) / 3) & 1u)) s_abort = 1;
                 if (s_abort) break;
-                const unsigned char* Ts = base + L.t[t % 3];
-                unsigned char* Bs = base + L.b[s];
-                const float2* x = xs + j * Kp;
-                for (int e = tid; e < Np * (Kp / 8); e += kTcWorkers) {
-                    const int n = e % Np, c = e / Np;
-                    const uint4 tv = *reinterpret_cast<const uint4*>(Ts + tc::kmajor_offset(n, 8 * c, Np));
-                    const uint32_t tw[4] = {tv.x, tv.y, tv.z, tv.w};
-                    const float4* x4 = reinterpret_cast<const float4*>(x + 8 * c);
+                unsigned char* Bre = base + L.b[s];
+                unsigned char* Bim = Bre + 128u * 64u * 2u;
+#pragma unroll
+                for (int r = 0; r < PER; ++r) {
+                    const int e = tid + r * kTcFormThreads;
+                    const int col = e & 127, c = e >> 7;          // column of B', 8-point chunk of the block
+                    const int j = col / Np;
+                    const uint32_t tw[4] = {tv[r].x, tv[r].y, tv[r].z, tv[r].w};
+                    const float4* x4 = reinterpret_cast<const float4*>(xs + j * Kp + 64 * b + 8 * c);
                     uint32_t re[4], imv[4];
 #pragma unroll
                     for (int q2 = 0; q2 < 4; ++q2) {
@@ -257,56 +267,72 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                         re[q2] = tc::pack_bf16x2(t0 * xx.x, t1 * xx.z);
                         imv[q2] = tc::pack_bf16x2(t0 * xx.y, t1 * xx.w);
                     }
-                    *reinterpret_cast<uint4*>(Bs + tc::sw128_offset(n, 8 * c, Np)) = make_uint4(re[0], re[1], re[2], re[3]);
-                    *reinterpret_cast<uint4*>(Bs + tc::sw128_offset(n, 8 * c + Kp, Np)) =
-                        make_uint4(imv[0], imv[1], imv[2], imv[3]);
+                    const uint32_t off = tc::sw128_offset(col, 8 * c, 128);
+                    *reinterpret_cast<uint4*>(Bre + off) = make_uint4(re[0], re[1], re[2], re[3]);
+                    *reinterpret_cast<uint4*>(Bim + off) = make_uint4(imv[0], imv[1], imv[2], imv[3]);
                 }
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_addr(&s_bfull[s]));
             }
-            if (s_abort) break;
-            // the group's results
-            if (!tc::mbar_wait(tc::smem_addr(&s_accf[b]), (uint32_t)(u >> 1) & 1u)) {
+        }
+        tc::cp_async_wait_all();
+    } else {
+        // ---------------- results: thread = TMEM lane = output row (i0, Re or Im)
+        const int m = tid - kTcFormThreads;               // 0..127, lane quadrant = warp % 4
+        const int i0 = h * 64 + (m >> 1), im = m & 1;
+        const bool writer = i0 < p.n0 && (LT >= 2 || !im);
+        float2* dst0 = p.out + (long long)i0 * p.lout.Sj;
+        // lines per step: 4 (the even row writes the first two, the odd row the last two, as
+        // one 16-byte store each), 2 (one line each) or 1 (the even row only)
+        constexpr int STEP = LT >= 4 ? 4 : LT;
+        constexpr int MINE = STEP >= 2 ? STEP / 2 : 1;
+        for (long long u = 0; u < my_tiles && !s_abort; ++u) {
+            const int ub = (int)(u & 1);
+            if (!tc::mbar_wait(tc::smem_addr(&s_accf[ub]), (uint32_t)(u >> 1) & 1u)) {
                 s_abort = 1;
                 break;
             }
             tc::fence_after_sync();
-            long long off_line[HALF];
+            const long long l0 = tile_l0(u);
+            const int nlt = (int)min((long long)LT, p.nl - l0);
+            const uint32_t row_base = tmem + (uint32_t)(ub * 128) + ((uint32_t)((warp & 3) * 32) << 16);
+            for (int j0 = 0; j0 < LT; j0 += STEP) {
+                const int jm = j0 + ((STEP >= 2 && im) ? MINE : 0);   // first line this thread writes
+                const long long off = line_offset(p.lout, min(l0 + jm, p.nl - 1));
+                for (int cb = 0; cb < Np; cb += 16) {
+                    float v[STEP][16];
 #pragma unroll
-            for (int q2 = 0; q2 < HALF; ++q2) off_line[q2] = line_offset(p.lout, min(l0 + jw + q2, p.nl - 1));
-            const uint32_t row_base = tmem + (uint32_t)(b * 128) + ((uint32_t)(warp * 32) << 16);
-            for (int cb = 0; cb < Np; cb += 16) {
-                float v[LG][16];
+                    for (int jj = 0; jj < STEP; ++jj) tc::tmem_ld16_nowait(row_base + (uint32_t)((j0 + jj) * Np + cb), v[jj]);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                for (int jj = 0; jj < LG; ++jj) tc::tmem_ld16(row_base + (uint32_t)(jj * Np + cb), v[jj]);
+                    for (int kk = 0; kk < 16; ++kk) {
+                        float mine[MINE], other[MINE];
 #pragma unroll
-                for (int kk = 0; kk < 16; ++kk) {
-                    const int k = cb + kk;
-                    float mine[HALF], other[HALF];
-#pragma unroll
-                    for (int q2 = 0; q2 < HALF; ++q2) {
-                        // even sends its values of lines HALF + q2, odd its values of lines q2
-                        const float send = (LG >= 2) ? (im ? v[q2][kk] : v[HALF + q2][kk]) : v[0][kk];
-                        other[q2] = __shfl_xor_sync(0xffffffffu, send, 1);
-                        mine[q2] = (LG >= 2) ? (im ? v[HALF + q2][kk] : v[q2][kk]) : v[0][kk];
-                    }
-                    if (k >= p.K || !writer) continue;
-                    float2* dst = dst0 + (long long)k * p.out_stride;
-#pragma unroll
-                    for (int q2 = 0; q2 < HALF; ++q2) {
-                        if (jw + q2 < nlg) {
-                            const float2 z = im ? make_float2(other[q2], mine[q2]) : make_float2(mine[q2], other[q2]);
-                            dst[off_line[q2]] = z;
+                        for (int q2 = 0; q2 < MINE; ++q2) {
+                            // even sends its values of lines MINE + q2, odd its values of lines q2
+                            const float send = STEP >= 2 ? (im ? v[q2][kk] : v[MINE + q2][kk]) : v[0][kk];
+                            other[q2] = __shfl_xor_sync(0xffffffffu, send, 1);
+                            mine[q2] = STEP >= 2 ? (im ? v[MINE + q2][kk] : v[q2][kk]) : v[0][kk];
+                        }
+                        const int k = cb + kk;
+                        if (k >= p.K || !writer) continue;
+                        float2* dst = dst0 + (long long)k * p.out_stride + off;
+                        const float2 z0 = im ? make_float2(other[0], mine[0]) : make_float2(mine[0], other[0]);
+                        if constexpr (MINE == 2) {
+                            const float2 z1 = im ? make_float2(other[1], mine[1]) : make_float2(mine[1], other[1]);
+                            if (jm + 1 < nlt) *reinterpret_cast<float4*>(dst) = make_float4(z0.x, z0.y, z1.x, z1.y);
+                            else if (jm < nlt) *dst = z0;
+                        } else {
+                            if (jm < nlt) *dst = z0;
                         }
                     }
                 }
             }
             tc::fence_before_sync();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(tc::smem_addr(&s_acce[b]));
+            if (lane == 0) tc::mbar_arrive(tc::smem_addr(&s_acce[ub]));
         }
-        tc::cp_async_wait_all();
     }
     __syncthreads();
     if (s_abort) {
@@ -314,8 +340,7 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
         // finish (bounded) before the tensor memory is released
         if (tid == 0) {
             atomicExch(p.err, 1);
-            for (int i = 0; i < 3; ++i) tc::mbar_wait(tc::smem_addr(&s_tfull[i]), 0, 1 << 16);
-            for (int i = 0; i < 2; ++i) tc::mbar_wait(tc::smem_addr(&s_done[i]), 0, 1 << 16);
+            for (int i = 0; i < 3; ++i) tc::mbar_wait(tc::smem_addr(&s_done[i]), 0, 1 << 16);
             tc::mbar_wait(tc::smem_addr(&s_abar), 0, 1 << 16);
         }
         __syncthreads();
@@ -324,39 +349,40 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     if (warp == 0) tc::tmem_dealloc(tmem, kTcCols);
 }
 
-// Lines accumulated side by side in one tensor-memory buffer (LG * Np <= 128 columns).
-int tc_lines_per_group(int Np) { return Np <= 16 ? 8 : Np <= 32 ? 4 : Np <= 64 ? 2 : 1; }
-
 size_t tc_smem_bytes(int Kp, int Np, int P0) {
     (void)P0;
-    return tc_smem_layout(Kp, Np, tc_lines_per_group(Np)).total;
+    return tc_smem_layout(Kp, Np).total;
 }
 
-template <int LG>
+template <int LT>
 static sfw_status run_axis0_tc(const Axis0TcPass& p, int num_sms, cudaStream_t st) {
-    const size_t smem = tc_smem_layout(p.Kp, p.Np, LG).total;
+    const size_t smem = tc_smem_layout(p.Kp, p.Np).total;
     static int configured = 0;   // largest dynamic shared memory set so far
     if ((int)smem > configured) {
-        SFW_CUDA(cudaFuncSetAttribute(k_axis0_tc<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SFW_CUDA(cudaFuncSetAttribute(k_axis0_tc<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = (int)smem;
     }
-    // CTAs per half: the SMs shared evenly, at most one per line group
+    // CTAs per half: the SMs shared evenly, at most one per tile
     const int halves = (p.n0 + 63) / 64;
-    const long long ngroups = (p.nl + LG - 1) / LG;
+    const long long ntiles = (p.nl + LT - 1) / LT;
     long long per = num_sms / halves;
     if (per < 1) per = 1;
-    if (per > ngroups) per = ngroups;
+    if (per > ntiles) per = ntiles;
     const int grid = (int)(per * halves);
-    SFW_LAUNCH(st, "k_axis0_tc", k_axis0_tc<LG><<<grid, kTcThreadsWs, smem, st>>>(p));
+    SFW_LAUNCH(st, "k_axis0_tc", k_axis0_tc<LT><<<grid, kTcThreadsWs, smem, st>>>(p));
     return launch_check("k_axis0_tc");
 }
 
 sfw_status launch_axis0_tc(const Axis0TcPass& p, int num_sms, cudaStream_t st) {
-    if (p.Np < 16 || p.Np > 128 || p.Np % 16 || p.Kp % 32 || p.Kp < p.P0 || p.n0 < 1)
-        return fail(SFW_ERR_SHAPE, "axis-0 tensor-core pass: Np=%d Kp=%d P0=%d", p.Np, p.Kp, p.P0);
+    if ((p.Np != 16 && p.Np != 32 && p.Np != 64 && p.Np != 128) || p.K > p.Np || p.Kp % 64 || p.Kp < p.P0 ||
+        p.n0 < 1)
+        return fail(SFW_ERR_SHAPE, "axis-0 tensor-core pass: Np=%d K=%d Kp=%d P0=%d", p.Np, p.K, p.Kp, p.P0);
+    // results go out as 16-byte pairs of consecutive lines: even offsets, consecutive lines adjacent
+    if (p.lout.Sb != 1 || p.lout.Sa % 2 || p.lout.Sj % 2 || p.lout.B % 2 || p.out_stride % 2)
+        return fail(SFW_ERR_SHAPE, "axis-0 tensor-core pass: output layout");
     if (tc_smem_bytes(p.Kp, p.Np, p.P0) > 227u * 1024u)
         return fail(SFW_ERR_SHAPE, "axis-0 tensor-core pass: shared memory for P0=%d", p.P0);
-    switch (tc_lines_per_group(p.Np)) {
+    switch (tc_tile_lines(p.Np)) {
         case 8: return run_axis0_tc<8>(p, num_sms, st);
         case 4: return run_axis0_tc<4>(p, num_sms, st);
         case 2: return run_axis0_tc<2>(p, num_sms, st);

@@ -834,8 +834,9 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
         if (p->precision == SFW_PREC_BF16 && p->real_table) {
             // the tensor-core axis-0 pass: T_l per line as the MMA's B operand (Np kernels x Kp
             // points, bf16); the plain bf16 table below stays for batches (recorded FFT passes)
-            const int Kp = (p->Pc[0] + 31) / 32 * 32, Np = (K + 15) / 16 * 16;
-            if (Np <= 128 && tc_smem_bytes(Kp, Np, p->Pc[0]) <= 227u * 1024u) {
+            const int Kp = (p->Pc[0] + 63) / 64 * 64;
+            const int Np = K <= 16 ? 16 : K <= 32 ? 32 : K <= 64 ? 64 : 128;
+            if (K <= 128 && tc_smem_bytes(Kp, Np, p->Pc[0]) <= 227u * 1024u) {
                 p->tc_Kp = Kp;
                 p->tc_Np = Np;
                 if ((st_ret = plan_alloc_t(p, &p->tc_table, (size_t)nl * Np * Kp))) break;
