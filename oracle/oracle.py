@@ -46,7 +46,9 @@ _LIB_PATH = os.path.join(_BUILD, "libsfw_oracle.so")
 
 SIGMA_BOUNDS = (0.75, 4.0)
 D_BOUNDS = (1.25, 3.0)
-TAU = 1e-4
+# stopping test of Algorithms 1 and 2: stop once max eta <= 1 + TAU (the paper writes "> 1"
+# to continue and "< 1" to stop; the margin covers the rounding spread of a converged slide)
+TAU = 1e-3
 PRUNE_REL = 1e-10
 
 __all__ = [

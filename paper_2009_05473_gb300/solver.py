@@ -9,7 +9,7 @@ the k x k Gram matrix, the BFGS curvature updates and the line searches.
 
 Readings of what the paper leaves open (same as the library's design notes):
 the domain box D (m_a in [0, n_a - 1], sigma in [0.75, 4], d in [1.25, 3],
-w >= 0), the stopping test max eta <= 1 + tau (tau = 1e-4), pruning of weights
+w >= 0), the stopping test max eta <= 1 + tau (tau = 1e-3), pruning of weights
 <= 1e-10 max w, projected BFGS with Armijo backtracking, Lawson-Hanson NNLS.
 """
 
@@ -118,7 +118,7 @@ def box_bfgs(fg: Callable[[np.ndarray], Tuple[float, np.ndarray]], x0: np.ndarra
 class GPUSolver:
     """SFW / BSFW on one volume: y (device, FP32), PSF and certificate grid in `plan`."""
 
-    def __init__(self, plan: Plan, y: torch.Tensor, lam: float, tau: float = 1e-4,
+    def __init__(self, plan: Plan, y: torch.Tensor, lam: float, tau: float = 1e-3,
                  slide_gtol: float = 1e-6, ascent_gtol: float = 1e-7, topk: int = 0):
         self.plan, self.y, self.lam, self.tau = plan, y, float(lam), tau
         self.slide_gtol, self.ascent_gtol, self.topk = slide_gtol, ascent_gtol, topk

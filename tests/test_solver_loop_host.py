@@ -103,7 +103,7 @@ def test_host_loop_matches_oracle_algorithm(oracle_mod, host_solver, boosted):
         assert abs(out["C"] - ref["C"]) <= 1e-3 * abs(ref["C"])
     # every outer iteration but the last added an atom whose certificate exceeded 1 + tau
     assert all(h["eta_max"] > 1.0 for h in out["history"][:-1])
-    assert out["history"][-1]["eta_max"] <= 1.0 + 1e-4
+    assert out["history"][-1]["eta_max"] <= 1.0 + 1e-3
 
 
 def test_lambda_path_host_logic(oracle_mod, host_solver):
@@ -122,7 +122,7 @@ def test_lambda_path_host_logic(oracle_mod, host_solver):
     assert path[0]["w"].size == 0
     assert path[1]["w"].size >= 1 and path[2]["w"].size >= path[1]["w"].size
     for p in path:
-        assert p["history"][-1]["eta_max"] <= 1.0 + 1e-4
+        assert p["history"][-1]["eta_max"] <= 1.0 + 1e-3
         th = p["thetas"]
         C = oracle_mod.criterion(vol.n, vol.R, vol.psf, y, th[:, :3], th[:, 3], th[:, 4], p["w"], p["lambda"],
                                  fft=True)
