@@ -120,8 +120,6 @@ constexpr int kTcEpiWarps = 4;                    // warps 8-11: results (TMEM l
 constexpr int kTcThreadsWs = 32 * (kTcFormWarps + kTcEpiWarps + 1);   // + warp 12: the MMAs
 constexpr int kTcFormThreads = 32 * kTcFormWarps;
 
-__device__ __forceinline__ void form_sync() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
-
 // One CTA per (half of the output rows, share of the tiles).  A = the real form of W's 64
 // rows of the half (prepared at plan creation, one bulk copy):
 //     row 2j   (Re U[i0]):  [ Re W[i0, :] | -Im W[i0, :] ]
@@ -227,9 +225,10 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
         };
         if (my_tiles > 0) stage_x(0);
         constexpr int PER = 128 * 8 / kTcFormThreads;     // items (16-byte chunks) per thread and block
-        for (long long u = 0; u < my_tiles && !s_abort; ++u) {
+        for (long long u = 0; u < my_tiles; ++u) {
             tc::cp_async_wait_all();
-            form_sync();
+            // all formation threads stop together (a barrier with a missing thread never ends)
+            if (tc::bar_sync_or<1, kTcFormThreads>(s_abort != 0)) break;
             if (u + 1 < my_tiles) stage_x(u + 1);
             const float2* xs = reinterpret_cast<const float2*>(base + L.xs[u & 1]);
             const long long l0 = tile_l0(u);

@@ -133,6 +133,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int max
     }
     return false;
 }
+// Named barrier `id` over `count` threads that also returns, to every one of them, whether any
+// passed true: a decision all of them take together (e.g. to stop on an abort flag that other
+// warps may set at any moment).
+template <int id, int count>
+__device__ __forceinline__ bool bar_sync_or(bool v) {
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+                 " selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(r) : "r"((uint32_t)v), "n"(id), "n"(count) : "memory");
+    return r != 0;
+}
 // bytes (multiple of 16) from global src to shared dst (both 16-byte aligned); completes on bar.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
