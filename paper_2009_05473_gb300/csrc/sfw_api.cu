@@ -179,6 +179,7 @@ static const char* const kCertHeadTag = "cert_head";
 static const char* const kCertTailTag = "cert_tail";
 static const char* const kCertX0Tag = "cert_x0fwd";      // forward axis-0 spectrum (tensor-core path)
 static const char* const kCertTcTag = "cert_axis0_tc";   // axis-0 inverse on the tensor cores
+static const char* const kCertC2rTcTag = "cert_c2r_tc";  // axis-2 real inverse + max on the tensor cores
 static const PassTags kCertTags = {"cert_r2c", "cert_c2c_fwd", "cert_axis0", "cert_c2c_inv", "cert_c2r_max",
                                    nullptr, nullptr};
 
@@ -675,6 +676,8 @@ struct sfw_plan {
     __nv_bfloat16* tc_dft;         // the inverse DFT rows (A operands), per half of the n0 rows
     int tc_Kp, tc_Np;
     float2* cX;
+    __nv_bfloat16* tc_c2r_C;       // the real inverse along axis 2 on the tensor cores (per-axis tails)
+    int tc_c2r_Kc;
     double* dir_parts;             // criterion partials of the direct blur
     int dir_parts_len;
 };
@@ -846,6 +849,20 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
                 if ((st_ret = plan_alloc_t(p, &p->tc_dft, halves * 128 * 2 * (size_t)Kp))) break;
                 if ((st_ret = launch_tc_dft(p->n[0], p->Pc[0], Kp, p->tc_dft, st))) break;
                 p->tc_ready = p->tc = true;
+                // the tail's real inverse along axis 2 (per-axis tails only: the slab tails fuse
+                // axes 1 and 2 already)
+                const int Kc = (p->Pc[2] + (p->Pc[2] & 1) + 15) / 16 * 16;
+                if (!cert_tail_supported(p->Pc[1], p->Pc[2], p->n[1], p->n[2]) && p->n[2] <= 128 &&
+                    tc_c2r_smem_bytes(Kc) <= 226u * 1024u) {
+                    const size_t cbytes = (size_t)128 * (size_t)((Kc + 63) / 64 * 64) * 2;
+                    if ((st_ret = plan_alloc(p, (void**)&p->tc_c2r_C, cbytes))) break;
+                    if (cudaMemsetAsync(p->tc_c2r_C, 0, cbytes, st) != cudaSuccess) {
+                        st_ret = cuda_fail(cudaGetLastError(), "tensor-core tail matrix");
+                        break;
+                    }
+                    if ((st_ret = launch_tc_c2r_matrix(p->Pc[2], p->H2c, p->n[2], Kc, p->tc_c2r_C, st))) break;
+                    p->tc_c2r_Kc = Kc;
+                }
             }
         }
         if ((st_ret = plan_alloc(p, &p->table, p->table_bytes))) break;
@@ -1252,7 +1269,8 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
             const size_t a_el = (size_t)K * p->n[0] * p->n[1] * p->H2c;
             const size_t b_el = (size_t)p->n[0] * p->Pc[1] * p->H2c;
             const size_t c_el = (size_t)K * p->n[0] * p->Pc[1] * p->H2c;
-            if ((s = plan_alloc_t(p, &p->cA, a_el))) break;
+            // + 2 complex of slack: the tensor-core tail copies whole 16-byte units of it
+            if ((s = plan_alloc_t(p, &p->cA, a_el + 2))) break;
             if ((s = plan_alloc_t(p, &p->cB, b_el))) break;
             if ((s = plan_alloc_t(p, &p->cC, c_el))) break;
             if ((s = plan_alloc_t(p, &p->tail_err, 1))) break;
@@ -1721,6 +1739,35 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
                 LaunchTag lt__(kCertTags.inv1);
                 SFW_TRY(launch_c2c(q, st));
             }
+        }
+        if (p->tc && p->tc_c2r_C && !g_recorder) {
+            // real inverse along axis 2 and the max over k on the tensor cores
+            C2rTcPass c;
+            memset(&c, 0, sizeof(c));
+            c.spec = p->cA;
+            c.spec_stride = (long long)n0 * n1 * H2;
+            c.C = p->tc_c2r_C;
+            c.nlines = n0 * n1;
+            c.P2 = P2;
+            c.H2 = H2;
+            c.n2 = n2;
+            c.Kc = p->tc_c2r_Kc;
+            c.K = K;
+            c.scale = (float)(1.0 / lambda);
+            c.eta_out = eta_out;
+            c.V = p->V;
+            c.vox_key = want_vox ? p->vox_key : nullptr;
+            c.best_key = (best_val || best_idx) ? p->best_key : nullptr;
+            c.counter = p->ctr + 1;
+            c.best_val = best_val;
+            c.best_idx = best_idx;
+            c.err = p->tail_err;
+            {
+                LaunchTag lt__(kCertC2rTcTag);
+                SFW_TRY(launch_c2r_tc(c, p->num_sms, st));
+            }
+            if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
+            return SFW_OK;
         }
         C2RPass q;
         memset(&q, 0, sizeof(q));

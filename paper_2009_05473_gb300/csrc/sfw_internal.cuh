@@ -365,6 +365,30 @@ sfw_status launch_axis0_tc(const Axis0TcPass& p, int num_sms, cudaStream_t st);
 sfw_status launch_tc_dft(int n0, int P0, int Kp, __nv_bfloat16* A, cudaStream_t st);
 size_t tc_smem_bytes(int Kp, int Np, int P0);
 
+// The certificate's real inverse along axis 2 with the max over kernels, on tcgen05
+// (cert_tc_c2r.cu): per 128 lines (i0, i1) and kernel k, eta = A C^T with A the line's half
+// spectrum as P2 real numbers (bf16) and C the fixed inverse matrix (n2 <= 128 outputs).
+struct C2rTcPass {
+    const float2* spec;         // (K, nlines, H2) complex: line L of kernel k at spec + k spec_stride + L H2;
+                                // 16-byte aligned, readable 8 bytes past its end
+    long long spec_stride;
+    const __nv_bfloat16* C;     // 128 x Kc inverse matrix (launch_tc_c2r_matrix), 128-byte swizzled
+    int nlines, P2, H2, n2, Kc, K;   // Kc = P2 (+ 1 if odd) rounded up to 16
+    int kgroup;                 // kernels per CTA item (set by the launcher)
+    float scale;                // 1 / lambda
+    float* eta_out;             // K x V or NULL
+    long long V;
+    unsigned long long* vox_key;   // V per-voxel keys or NULL
+    unsigned long long* best_key;  // one key or NULL; zero between calls
+    unsigned int* counter;
+    float* best_val;
+    int64_t* best_idx;
+    int* err;                   // set if a bounded wait ran out
+};
+sfw_status launch_tc_c2r_matrix(int P2, int H2, int n2, int Kc, __nv_bfloat16* C, cudaStream_t st);
+sfw_status launch_c2r_tc(const C2rTcPass& p, int num_sms, cudaStream_t st);
+size_t tc_c2r_smem_bytes(int Kc);
+
 // ------------------------------------------------------------------ plain FP32 route (direct.cu)
 // Direct sums without transforms (the route the transform route is measured against).
 struct DirectBlur {

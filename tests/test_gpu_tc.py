@@ -58,11 +58,15 @@ def test_tensor_core_tile_matches_numpy(sfw, K, N, swz):
     assert np.max(np.abs(d - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
-# ragged output rows (n0 not a multiple of 64), kernel counts padded to 16, 32 and 48
+# ragged output rows (n0 not a multiple of 64), kernel counts padded to 16, 32 and 48; all of
+# them take the per-axis certificate tail, whose axis-2 inverse also runs on the tensor cores
 TC_CASES = [
     ((20, 24, 28), (2, 3, 4), (1.0, 2.0, 3.0), (1.5, 2.0, 2.5)),               # K = 9  -> 16
     ((70, 18, 22), (3, 2, 3), tuple(np.linspace(1, 3, 8)), (1.5, 2.0, 2.5, 3.0)),  # K = 32
     ((33, 40, 16), (2, 4, 2), tuple(np.linspace(1, 3, 10)), (1.5, 2.0, 2.5, 3.0)),  # K = 40 -> 48
+    # odd line count x odd half-spectrum length: every other kernel's spectra start off the
+    # 16-byte grid, and the last 128-line tile has empty quarters
+    ((21, 15, 18), (2, 2, 3), (1.0, 2.0, 3.0), (1.5, 2.5)),                     # K = 6 -> 16
 ]
 
 
@@ -81,7 +85,11 @@ def test_tensor_core_certificate_matches_oracle(sfw, oracle_mod, case):
     pf = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, precision="fp32")
     assert pb.info["tensor_cores"] and not pf.info["tensor_cores"]
     rd = torch.tensor(r, device="cuda")
+    sfw._abi.sfw_profile_start(256, None)
     ob = pb.certificate(rd, lam, want_eta=True)
+    tags = sfw._abi.sfw_profile_stop()
+    # both inverse stages of the certificate ran on the tensor cores
+    assert "cert_axis0_tc" in tags and "cert_c2r_tc" in tags, sorted(tags)
     eb = ob["eta"].cpu().numpy()
     ef = pf.certificate(rd, lam, want_eta=True)["eta"].cpu().numpy()
     ref = oracle_mod.eta_grid_fft(vol.n, vol.R, vol.psf, r.astype(np.float64), lam, kernels)
