@@ -1,19 +1,24 @@
-// The certificate's last stage on the tensor cores (bf16 operands, FP32 accumulation in
+// The certificate's last stage on the tensor cores (tf32 operands, FP32 accumulation in
 // tensor memory): the real inverse along axis 2 with the maximum over the kernels.
 //
 // After the axes 0 and 1 every line L = (i0, i1) of kernel k holds the half spectrum
 // V_k[L, h2], h2 < H2 = P2 / 2 + 1, of a real line, and Eq. 5's certificate is
 //     eta_k(i0, i1, i2) = (1 / lambda) sum_h2 c_h2 (Re V cos(2 pi h2 i2 / P2) - Im V sin(...))
-// (c_h2 = 1 at h2 = 0 and P2 / 2, else 2; the 1 / |P| of the inverse is in the table).  The
-// sine vanishes at h2 = 0 and h2 = P2 / 2, so a line needs P2 real numbers: column 0 = Re V[0],
-// column 1 = Re V[P2 / 2] (even P2), columns (2 h2, 2 h2 + 1) = (Re, Im) V[h2] otherwise.  Over
-// 128 lines and all n2 outputs this is one GEMM per kernel,
-//     D (128 lines x n2) = A (lines x Kc) . C^T (n2 x Kc),   Kc = P2 (+ 1 if odd) rounded to 16,
-// with C fixed per plan (built once, resident in shared memory) and A converted from the FP32
-// spectra.  A CTA takes a tile of 128 lines and a group of kernels; its epilogue warps keep
-// each output's running maximum and its kernel in registers, then fold them into the
-// per-voxel and grid-maximum candidate keys (value, then lowest flat index k V + lin(m)).
+// (c_h2 = 1 at h2 = 0 and P2 / 2, else 2; the 1 / |P| of the inverse is in the table).  Read as
+// 2 H2 real numbers (Re, Im interleaved, exactly as the spectra lie in memory), a line times
+// the fixed matrix C^T (2 H2 x n2; the coefficients of Im V[0] and Im V[P2 / 2] are sin 0 = 0)
+// gives its n2 outputs, so over 128 lines this is one GEMM per kernel,
+//     D (128 lines x n2) = A (128 x 2 H2) . C^T,
+// with A loaded by the tensor-memory accelerator straight from the FP32 spectra into the
+// swizzled operand layout and multiplied as tf32: no conversion pass.  A CTA takes a tile of
+// 128 lines and a group of kernels; its epilogue warps keep each output's running maximum and
+// its kernel in registers, then fold them into the per-voxel and grid-maximum candidate keys
+// (value, then lowest flat index k V + lin(m)).
 #include <math.h>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <mutex>
 
 #include "sfw_internal.cuh"
 #include "tc_sm100.cuh"
@@ -22,102 +27,101 @@ namespace sfw {
 
 constexpr int kC2rRows = 128;      // lines per tile (M)
 constexpr int kC2rN = 128;         // outputs per line (N), n2 <= 128
-constexpr int kC2rSub = 32;        // lines per staged quarter of a tile
-constexpr int kC2rFormWarps = 4;   // warps 0-3: A of every step; thread 0 also issues copies and MMAs
-constexpr int kC2rEpiWarps = 16;   // warps 4-19: four per tensor-memory lane quadrant
-constexpr int kC2rCols = kC2rN / (kC2rEpiWarps / 4);              // columns (outputs) per epilogue thread
-constexpr int kC2rThreads = 32 * (kC2rFormWarps + kC2rEpiWarps);
-constexpr int kC2rFormThreads = 32 * kC2rFormWarps;
+constexpr int kC2rChunk = 32;      // tf32 columns per 128-byte swizzle atom (one A stage)
+constexpr uint32_t kC2rAtom = kC2rRows * 128u;   // bytes of a 128-row x 32-column atom
+constexpr int kC2rEpiWarps = 16;   // warps 0-15: four per tensor-memory lane quadrant
+constexpr int kC2rCols = kC2rN / (kC2rEpiWarps / 4);             // columns (outputs) per epilogue thread
+constexpr int kC2rProdWarp = kC2rEpiWarps, kC2rMmaWarp = kC2rEpiWarps + 1;
+constexpr int kC2rThreads = 32 * (kC2rEpiWarps + 2);
+constexpr int kC2rMaxStages = 8;
 
-// Column c of a line's A row: the bin h2 and the part (0 = Re, 1 = Im) it holds, or -1.
-__host__ __device__ inline int c2r_col_bin(int c, int P2, int H2, int* part) {
-    *part = 0;
-    if (c == 0) return 0;
-    if (c == 1) return (P2 & 1) ? -1 : P2 / 2;
-    const int h2 = c >> 1;
-    *part = c & 1;
-    return (h2 < H2 && 2 * h2 != P2) ? h2 : -1;
-}
+// Columns of C (and of a line's A row): 2 h2 + part, part 0 = Re, 1 = Im; chunks of 32.
+int tc_c2r_chunks(int H2) { return (2 * H2 + kC2rChunk - 1) / kC2rChunk; }
 
-// C for the real inverse of length P2 keeping outputs i2 < n2: row i2, column of (h2, part) =
-// c_h2 (cos, -sin)(2 pi h2 i2 / P2), zero elsewhere; 128-byte swizzled, 128 rows.
-__global__ void k_tc_c2r_matrix(int P2, int H2, int n2, int Kc, __nv_bfloat16* __restrict__ C) {
-    const int total = kC2rN * Kc;
+// C^T's rows as the MMA's B operand: row i2 < n2, column 2 h2 + part = c_h2 (cos, -sin)
+// (2 pi h2 i2 / P2), zero elsewhere; FP32, atoms of 128 rows x 32 columns with the 128-byte
+// swizzle (16-byte unit u of row r at unit u ^ (r mod 8)).
+__global__ void k_tc_c2r_matrix(int P2, int H2, int n2, int nch, float* __restrict__ C) {
+    const int total = kC2rN * nch * kC2rChunk;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int i2 = i / Kc, c = i - i2 * Kc;
-        int part;
-        const int h2 = c2r_col_bin(c, P2, H2, &part);
+        const int i2 = i / (nch * kC2rChunk), c = i - i2 * nch * kC2rChunk;
+        const int h2 = c >> 1, part = c & 1;
         float v = 0.f;
-        if (i2 < n2 && h2 >= 0) {
+        if (i2 < n2 && h2 < H2) {
             const long long r = ((long long)h2 * i2) % P2;
             double sn, cs;
             sincospi(2.0 * (double)r / (double)P2, &sn, &cs);
             const double w = (h2 == 0 || 2 * h2 == P2) ? 1.0 : 2.0;
             v = (float)(part ? -w * sn : w * cs);
         }
-        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(C) + tc::sw128_offset(i2, c, kC2rN)) =
-            __float2bfloat16_rn(v);
+        const int cc = c & (kC2rChunk - 1);
+        const uint32_t off = (uint32_t)(c / kC2rChunk) * kC2rAtom + (uint32_t)(i2 >> 3) * 1024u +
+                             (uint32_t)(i2 & 7) * 128u + ((((uint32_t)cc >> 2) ^ (uint32_t)(i2 & 7)) << 4) +
+                             (uint32_t)(cc & 3) * 4u;
+        *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(C) + off) = v;
     }
 }
 
-sfw_status launch_tc_c2r_matrix(int P2, int H2, int n2, int Kc, __nv_bfloat16* C, cudaStream_t st) {
-    SFW_LAUNCH(st, "k_tc_c2r_matrix", k_tc_c2r_matrix<<<64, 256, 0, st>>>(P2, H2, n2, Kc, C));
+sfw_status launch_tc_c2r_matrix(int P2, int H2, int n2, float* C, cudaStream_t st) {
+    const int nch = tc_c2r_chunks(H2);
+    SFW_LAUNCH(st, "k_tc_c2r_matrix", k_tc_c2r_matrix<<<64, 256, 0, st>>>(P2, H2, n2, nch, C));
     return launch_check("k_tc_c2r_matrix");
 }
 
-// Dynamic shared memory: C (128 rows x Kca), two A stages (128 rows x Kca), two staging
-// buffers for the FP32 spectra of a quarter tile (32 lines); Kca = Kc rounded up to whole
-// 64-column atoms.  Since H2 <= Kc / 2 + 1, a quarter holds at most 32 (Kc / 2 + 1) complex
-// values (+ one of misalignment and one of rounding), 16-byte rounded.
-__host__ __device__ inline uint32_t c2r_region(int Kc) { return (uint32_t)kC2rRows * (uint32_t)((Kc + 63) / 64 * 64) * 2u; }
-__host__ __device__ inline uint32_t c2r_stage(int Kc) {
-    return ((uint32_t)kC2rSub * (uint32_t)(Kc / 2 + 1) * 8u + 16u + 1023u) & ~1023u;
+// Dynamic shared memory: C (nch atoms, resident), then a ring of A stages (one atom each).
+static int c2r_stages(int nch) {
+    const long long room = 226LL * 1024 - 1024 - (long long)nch * kC2rAtom;
+    const long long s = room / kC2rAtom;
+    return (int)(s > kC2rMaxStages ? kC2rMaxStages : s);
 }
-size_t tc_c2r_smem_bytes(int Kc) { return 3u * c2r_region(Kc) + 2u * c2r_stage(Kc) + 1024u; }
+size_t tc_c2r_smem_bytes(int H2) {
+    const int nch = tc_c2r_chunks(H2);
+    return (size_t)(nch + c2r_stages(nch)) * kC2rAtom + 1024u;
+}
+bool tc_c2r_fits(int H2) { return c2r_stages(tc_c2r_chunks(H2)) >= 2; }
 
-__device__ __forceinline__ void c2r_form_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
-
-// Where quarter q of step (item it, kernel k) lies: the complex values f0 .. f0 + nf of the
-// spectra; the bulk copy takes the 16-byte units [s, e) that hold them (lead = values before f0
-// in the copy).  e may pass the end of the spectra by 8 bytes: their buffer has that slack.
-struct C2rQuarter {
-    long long f0;
-    int rows, nf, lead, row0;
-    uint32_t bytes;
-};
-
-__device__ __forceinline__ C2rQuarter c2r_quarter(const C2rTcPass& p, long long it, int ngroups, int k, int q) {
-    C2rQuarter h;
-    const int L0 = (int)(it / ngroups) * kC2rRows + kC2rSub * q;
-    const int rows = max(0, min(kC2rSub, p.nlines - L0));
-    h.row0 = kC2rSub * q;
-    h.rows = rows;
-    h.f0 = (long long)k * p.spec_stride + (long long)L0 * p.H2;
-    h.nf = rows * p.H2;
-    const unsigned long long a0 = (unsigned long long)h.f0 * 8ull, a1 = a0 + (unsigned long long)h.nf * 8ull;
-    const unsigned long long s0 = a0 & ~15ull, e0 = (a1 + 15ull) & ~15ull;
-    h.lead = (int)((a0 - s0) >> 3);
-    h.bytes = h.nf > 0 ? (uint32_t)(e0 - s0) : 0u;
-    return h;
+// The spectra as FP32 numbers (Re, Im interleaved): x = 2 h2 + part (2 H2 of them, row pitch
+// 2 H2p), y = line, z = kernel; boxes of 32 x 128 x 1 with the 128-byte swizzle.
+bool make_c2r_tmap(const float2* spec, int H2, int H2p, long long nlines, int K, void* tmap_out) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    });
+    if (!encode || (H2p & 1) || H2p < H2 || nlines < 1 || K < 1 || (reinterpret_cast<uintptr_t>(spec) & 15u))
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * H2), (cuuint64_t)nlines, (cuuint64_t)K};
+    const cuuint64_t strides[2] = {(cuuint64_t)H2p * 8u, (cuuint64_t)nlines * (cuuint64_t)H2p * 8u};
+    const cuuint32_t box[3] = {(cuuint32_t)kC2rChunk, (cuuint32_t)kC2rRows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap* tm = static_cast<CUtensorMap*>(tmap_out);
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(spec), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // One CTA per (tile of 128 lines, group of kernels), persistent over such items; a step is one
-// (item, kernel).  Warps 0-3 turn the spectra of a step (bulk-copied in quarters of 32 lines,
-// two staging buffers) into A (two stages); their thread 0 issues the copies and, once A is
-// built, the 128 x 128 MMAs over Kc (two tensor-memory buffers).  Warps 4-19 fold each kernel's
-// D into the running maxima and, after the group's last kernel, into the candidate keys.
-// mbarriers: v_full (a quarter's spectra landed), done (MMAs of a step finished), acc_empty
-// (D read, 16 arrivals).  Every wait is bounded; a wait that runs out sets p.err.
-__global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p) {
+// (item, kernel) and consists of nch chunks of 32 columns.  One lane of warp 16 loads the
+// chunks of A (tensor-map boxes) into a ring of stages; one lane of warp 17 issues the
+// 128 x 128 x 8 tf32 MMAs of each chunk against the resident C (two tensor-memory buffers);
+// warps 0-15 fold each kernel's D into the running maxima and, after the group's last kernel,
+// into the candidate keys.  mbarriers: full / empty per stage (box landed / its MMAs done),
+// done (MMAs of a step finished), acc_empty (D read, 16 arrivals), C landed.  Every wait is
+// bounded; a wait that runs out sets p.err.
+__global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p, const __grid_constant__ CUtensorMap tm) {
     extern __shared__ unsigned char tc_smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
-    const uint32_t region = c2r_region(p.Kc), stage = c2r_stage(p.Kc);
-    unsigned char* Cs = base;   // C, resident
-    // A stage i at base + (1 + i) region, staging buffer i at base + 3 region + i stage
-    auto A_stage = [&](int i) { return base + (uint32_t)(1 + i) * region; };
-    auto V_stage = [&](int i) { return base + 3u * region + (uint32_t)i * stage; };
-    __shared__ __align__(8) unsigned long long s_vfull[2], s_done[2], s_acce[2], s_cbar;
+    const int nch = p.nch, S = p.stages;
+    unsigned char* Cs = base;                                   // C, resident: nch atoms
+    unsigned char* ring = base + (uint32_t)nch * kC2rAtom;      // A stages
+    __shared__ __align__(8) unsigned long long s_full[kC2rMaxStages], s_empty[kC2rMaxStages], s_done[2], s_acce[2],
+        s_cbar;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -125,8 +129,11 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p) {
     const int ngroups = (p.K + p.kgroup - 1) / p.kgroup;
     const long long items = (long long)ntiles * ngroups;
     if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(tc::smem_addr(&s_full[i]), 1);
+            tc::mbar_init(tc::smem_addr(&s_empty[i]), 1);
+        }
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(tc::smem_addr(&s_vfull[i]), 1);
             tc::mbar_init(tc::smem_addr(&s_done[i]), 1);
             tc::mbar_init(tc::smem_addr(&s_acce[i]), kC2rEpiWarps);
         }
@@ -134,11 +141,7 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p) {
         tc::mbar_init_fence();
         s_abort = 0;
     }
-    // A's padding columns (past Kc) stay zero in both stages
-    for (uint32_t e = (uint32_t)tid * 16u; e < 2u * region; e += kC2rThreads * 16u)
-        *reinterpret_cast<uint4*>(A_stage(0) + e) = make_uint4(0u, 0u, 0u, 0u);
-    if (warp == 0) tc::tmem_alloc(&s_tmem, 256);
-    tc::fence_async_smem();
+    if (warp == kC2rProdWarp) tc::tmem_alloc(&s_tmem, 256);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -151,132 +154,78 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p) {
     };
     unsigned long long best = 0ull;
 
-    if (warp < kC2rFormWarps) {
-        // ---------------- A of every step: row = line, the line's P2 real numbers (c2r_col_bin)
-        const unsigned char* spec_b = reinterpret_cast<const unsigned char*>(p.spec);
-        const int nyq = (p.P2 & 1) ? -1 : p.P2 / 2;
-        const int nyq_sl = nyq >= 0 ? nyq >> 5 : 0;
-        const uint32_t lane_chunk = (uint32_t)lane >> 2, lane_byte = 4u * (uint32_t)(lane & 3);
-        // quarter q of a step is staged in buffer q & 1, whose uses alternate phase parity
-        auto issue_quarter = [&](long long it, int k, int q) {
-            const C2rQuarter h = c2r_quarter(p, it, ngroups, k, q);
-            const uint32_t bar = tc::smem_addr(&s_vfull[q & 1]);
-            tc::mbar_expect_tx(bar, h.bytes);
-            if (h.bytes)
-                tc::bulk_g2s(tc::smem_addr(V_stage(q & 1)), spec_b + (((unsigned long long)h.f0 * 8ull) & ~15ull),
-                             h.bytes, bar);
-        };
-        // thread 0's cursor: the quarter whose copy goes out next, two ahead of the one read
-        long long nit = blockIdx.x;
-        int nk = 0, nk1 = 0, nq = 0;
-        auto advance = [&]() {
-            if (++nq == 4) {
-                nq = 0;
-                if (++nk >= nk1) {
-                    nit += gridDim.x;
-                    if (nit < items) item_k(nit, &nk, &nk1);
+    if (warp == kC2rProdWarp) {
+        // ---------------- producer: C once, then the chunks of every step into the ring
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];\n" :: "l"(&tm) : "memory");
+            const uint32_t cbytes = (uint32_t)nch * kC2rAtom;
+            tc::mbar_expect_tx(tc::smem_addr(&s_cbar), cbytes);
+            tc::bulk_g2s(tc::smem_addr(Cs), p.C, cbytes, tc::smem_addr(&s_cbar));
+            uint32_t g = 0;   // chunks issued
+            for (long long it = blockIdx.x; it < items && !s_abort; it += gridDim.x) {
+                int k0, k1;
+                item_k(it, &k0, &k1);
+                const int y = (int)(it / ngroups) * kC2rRows;
+                for (int k = k0; k < k1 && !s_abort; ++k) {
+                    for (int c = 0; c < nch; ++c, ++g) {
+                        const uint32_t slot = g % (uint32_t)S;
+                        // the stage is free once the MMAs of its previous chunk are done
+                        if (g >= (uint32_t)S &&
+                            !tc::mbar_wait(tc::smem_addr(&s_empty[slot]), ((g / (uint32_t)S) - 1u) & 1u)) {
+                            s_abort = 1;
+                            break;
+                        }
+                        tc::mbar_expect_tx(tc::smem_addr(&s_full[slot]), kC2rAtom);
+                        tc::tma_load_3d(tc::smem_addr(ring + slot * kC2rAtom), &tm, c * kC2rChunk, y, k,
+                                        tc::smem_addr(&s_full[slot]));
+                    }
                 }
-            }
-        };
-        if (tid == 0) {
-            tc::mbar_expect_tx(tc::smem_addr(&s_cbar), region);
-            tc::bulk_g2s(tc::smem_addr(Cs), p.C, region, tc::smem_addr(&s_cbar));
-            if (nit < items) {
-                item_k(nit, &nk, &nk1);
-                issue_quarter(nit, nk, 0);
-                issue_quarter(nit, nk, 1);
-                advance();
-                advance();
             }
         }
-        const uint32_t idesc = tc::idesc_bf16_f32(kC2rRows, kC2rN);
-        const uint32_t c0 = tc::smem_addr(Cs);
-        // an abort is only acted on through a barrier of the formation warps that tells all of
-        // them at once, so that they leave the loops together
-        bool stop = false;
-        uint32_t t = 0;
-        for (long long it = blockIdx.x; it < items && !stop; it += gridDim.x) {
-            int k0, k1;
-            item_k(it, &k0, &k1);
-            for (int k = k0; k < k1 && !stop; ++k, ++t) {
-                const int s = (int)(t & 1);
-                unsigned char* As = A_stage(s);
-                // A[s] is free once the MMAs of step t - 2 are done
-                bool ok = t < 2 || tc::mbar_wait(tc::smem_addr(&s_done[s]), ((t - 2) >> 1) & 1u);
-                for (int q = 0; q < 4; ++q) {
-                    ok = ok && tc::mbar_wait(tc::smem_addr(&s_vfull[q & 1]), (uint32_t)(q >> 1) & 1u);
-                    stop = tc::bar_sync_or<1, kC2rFormThreads>(!ok || s_abort != 0);
-                    if (stop) break;
-                    const C2rQuarter h = c2r_quarter(p, it, ngroups, k, q);
-                    const float2* vs = reinterpret_cast<const float2*>(V_stage(q & 1)) + h.lead;
-                    // warp w takes lines w, w + 4, ... (two per pass); lane l the bins l, l + 32,
-                    // l + 64, l + 96 (H2 <= Kc / 2 + 1 <= 97: the shared-memory bound keeps
-                    // Kc <= 192).  Lane 0 stores Re V[0] with Re V[P2 / 2] (columns 0, 1).
-#pragma unroll 1
-                    for (int r0 = warp; r0 < h.rows; r0 += 2 * kC2rFormWarps) {
-                        float2 z[2][4];
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int r = r0 + u * kC2rFormWarps;
-                            const float2* src = vs + r * p.H2 + lane;
-#pragma unroll
-                            for (int sl = 0; sl < 4; ++sl)
-                                z[u][sl] = (r < h.rows && lane + 32 * sl < p.H2) ? src[32 * sl] : make_float2(0.f, 0.f);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int r = r0 + u * kC2rFormWarps;
-                            if (r >= h.rows) break;
-                            const float zs = nyq_sl == 0 ? z[u][0].x : nyq_sl == 1 ? z[u][1].x
-                                           : nyq_sl == 2 ? z[u][2].x : z[u][3].x;
-                            const float zn = nyq >= 0 ? __shfl_sync(0xffffffffu, zs, nyq & 31) : 0.f;
-                            const int row = h.row0 + r;
-                            // 64-column atoms 16 KB apart (128 rows); the lane's swizzled chunk
-                            unsigned char* dst = As + (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u +
-                                                 ((lane_chunk ^ (uint32_t)(row & 7)) << 4) + lane_byte;
-#pragma unroll
-                            for (int sl = 0; sl < 4; ++sl) {
-                                const int h2 = lane + 32 * sl;
-                                const uint32_t w = tc::pack_bf16x2(z[u][sl].x, (sl == 0 && lane == 0) ? zn : z[u][sl].y);
-                                if (h2 < p.H2 && h2 != nyq)
-                                    *reinterpret_cast<uint32_t*>(dst + (uint32_t)sl * (uint32_t)(kC2rRows / 8) * 1024u) = w;
-                            }
-                        }
+        __syncwarp();
+    } else if (warp == kC2rMmaWarp) {
+        // ---------------- MMA lane
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32_f32(kC2rRows, kC2rN);
+            const uint32_t c0 = tc::smem_addr(Cs), r0 = tc::smem_addr(ring);
+            if (!tc::mbar_wait(tc::smem_addr(&s_cbar), 0)) s_abort = 1;
+            uint32_t g = 0, t = 0;
+            for (long long it = blockIdx.x; it < items && !s_abort; it += gridDim.x) {
+                int k0, k1;
+                item_k(it, &k0, &k1);
+                for (int k = k0; k < k1 && !s_abort; ++k, ++t) {
+                    const int s = (int)(t & 1);
+                    // D[s] is free once the epilogue has read step t - 2
+                    if (t >= 2 && !tc::mbar_wait(tc::smem_addr(&s_acce[s]), ((t - 2) >> 1) & 1u)) {
+                        s_abort = 1;
+                        break;
                     }
-                    tc::fence_async_smem();
-                    c2r_form_sync();
-                    // staging buffer q & 1 is read: the quarter two ahead goes out
-                    if (tid == 0 && nit < items) {
-                        issue_quarter(nit, nk, nq);
-                        advance();
-                    }
-                }
-                if (stop) break;
-                if (tid == 0) {
-                    // D[s] is free once the epilogue has read step t - 2; C has landed
-                    bool ok2 = t > 0 || tc::mbar_wait(tc::smem_addr(&s_cbar), 0);
-                    ok2 = ok2 && (t < 2 || tc::mbar_wait(tc::smem_addr(&s_acce[s]), ((t - 2) >> 1) & 1u));
-                    if (ok2) {
+                    const uint32_t d = tmem + (uint32_t)(s * kC2rN);
+                    for (int c = 0; c < nch; ++c, ++g) {
+                        const uint32_t slot = g % (uint32_t)S;
+                        if (!tc::mbar_wait(tc::smem_addr(&s_full[slot]), (g / (uint32_t)S) & 1u)) {
+                            s_abort = 1;
+                            break;
+                        }
                         tc::fence_after_sync();
-                        const uint32_t a0 = tc::smem_addr(As);
-                        const uint32_t d = tmem + (uint32_t)(s * kC2rN);
-                        for (int ks = 0; ks < p.Kc / 16; ++ks) {
-                            const uint32_t off = (uint32_t)(ks >> 2) * 16u * 1024u + (uint32_t)(ks & 3) * 32u;
-                            tc::mma_bf16(d, tc::desc_kmajor_sw128(a0 + off), tc::desc_kmajor_sw128(c0 + off), idesc,
-                                         ks > 0 ? 1u : 0u);
-                        }
-                        tc::mma_commit(tc::smem_addr(&s_done[s]));
-                    } else {
-                        s_abort = 1;   // the formation warps see it at their next barrier
+                        // K = 8 slices holding columns < 2 H2 (the rest of the last chunk is zero)
+                        const int nks = min(4, (2 * p.H2 - c * kC2rChunk + 7) / 8);
+                        const uint32_t a0 = r0 + slot * kC2rAtom, b0 = c0 + (uint32_t)c * kC2rAtom;
+                        for (int ks = 0; ks < nks; ++ks)
+                            tc::mma_tf32(d, tc::desc_kmajor_sw128(a0 + (uint32_t)ks * 32u),
+                                         tc::desc_kmajor_sw128(b0 + (uint32_t)ks * 32u), idesc,
+                                         (c > 0 || ks > 0) ? 1u : 0u);
+                        tc::mma_commit(tc::smem_addr(&s_empty[slot]));
                     }
+                    if (s_abort) break;
+                    tc::mma_commit(tc::smem_addr(&s_done[s]));
                 }
             }
         }
-        if (stop) s_abort = 1;
+        __syncwarp();
     } else {
         // ---------------- running maxima: TMEM lane = line, kC2rCols columns (outputs i2) per thread
-        const int ew = warp - kC2rFormWarps;            // 0..15
-        const int quad = warp & 3, part = ew >> 2;
+        const int quad = warp & 3, part = warp >> 2;
         const int cbase = kC2rCols * part;
         float mx[kC2rCols];
         uint32_t akp[kC2rCols / 4];   // the kernel of each maximum, one byte per column (K <= 256)
@@ -349,13 +298,13 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p) {
         if (tid == 0) {
             atomicExch(p.err, 1);
             for (int i = 0; i < 2; ++i) tc::mbar_wait(tc::smem_addr(&s_done[i]), 0, 1 << 16);
-            for (int i = 0; i < 2; ++i) tc::mbar_wait(tc::smem_addr(&s_vfull[i]), 0, 1 << 16);
+            for (int i = 0; i < S; ++i) tc::mbar_wait(tc::smem_addr(&s_full[i]), 0, 1 << 16);
             tc::mbar_wait(tc::smem_addr(&s_cbar), 0, 1 << 16);
         }
         __syncthreads();
     }
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (warp == kC2rProdWarp) tc::tmem_dealloc(tmem, 256);
     // the grid maximum: a key per warp, decoded by the CTA that finishes last
     if (p.best_key) {
         for (int off = 16; off > 0; off >>= 1) {
@@ -377,15 +326,14 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p) {
     }
 }
 
-sfw_status launch_c2r_tc(const C2rTcPass& p0, int num_sms, cudaStream_t st) {
+sfw_status launch_c2r_tc(const C2rTcPass& p0, const void* tmap, int num_sms, cudaStream_t st) {
     C2rTcPass p = p0;
-    if (p.n2 < 1 || p.n2 > kC2rN || p.Kc % 16 || p.Kc < p.P2 + (p.P2 & 1) || p.H2 != p.P2 / 2 + 1 || p.H2 > 128 ||
-        p.K < 1 || p.K > 256 || p.nlines < 1 || (reinterpret_cast<uintptr_t>(p.spec) & 15u) ||
-        (reinterpret_cast<uintptr_t>(p.C) & 15u))
-        return fail(SFW_ERR_SHAPE, "certificate tail on the tensor cores: n2=%d Kc=%d P2=%d H2=%d", p.n2, p.Kc, p.P2,
-                    p.H2);
-    const size_t smem = tc_c2r_smem_bytes(p.Kc);
-    if (smem > 226u * 1024u) return fail(SFW_ERR_SHAPE, "certificate tail on the tensor cores: shared memory");
+    if (!tmap || p.n2 < 1 || p.n2 > kC2rN || p.H2 != p.P2 / 2 + 1 || !tc_c2r_fits(p.H2) || p.K < 1 || p.K > 256 ||
+        p.nlines < 1 || (reinterpret_cast<uintptr_t>(p.C) & 15u))
+        return fail(SFW_ERR_SHAPE, "certificate tail on the tensor cores: n2=%d P2=%d H2=%d", p.n2, p.P2, p.H2);
+    p.nch = tc_c2r_chunks(p.H2);
+    p.stages = c2r_stages(p.nch);
+    const size_t smem = tc_c2r_smem_bytes(p.H2);
     // kernels per item: the fewest steps on the busiest CTA, then the fewest key merges; all
     // kernels in one item when per-voxel keys are wanted (stored once, without atomics)
     const long long ntiles = (p.nlines + kC2rRows - 1) / kC2rRows;
@@ -408,7 +356,8 @@ sfw_status launch_c2r_tc(const C2rTcPass& p0, int num_sms, cudaStream_t st) {
         SFW_CUDA(cudaFuncSetAttribute(k_c2r_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = (int)smem;
     }
-    SFW_LAUNCH(st, "k_c2r_tc", k_c2r_tc<<<grid, kC2rThreads, smem, st>>>(p));
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(tmap);
+    SFW_LAUNCH(st, "k_c2r_tc", k_c2r_tc<<<grid, kC2rThreads, smem, st>>>(p, *tm));
     return launch_check("k_c2r_tc");
 }
 

@@ -676,8 +676,12 @@ struct sfw_plan {
     __nv_bfloat16* tc_dft;         // the inverse DFT rows (A operands), per half of the n0 rows
     int tc_Kp, tc_Np;
     float2* cX;
-    __nv_bfloat16* tc_c2r_C;       // the real inverse along axis 2 on the tensor cores (per-axis tails)
-    int tc_c2r_Kc;
+    // the real inverse along axis 2 on the tensor cores (per-axis tails): its matrix and the
+    // tensor map of the spectra, whose lines then have the even pitch H2p
+    float* tc_c2r_C;
+    bool c2r_tma;
+    int H2p;
+    alignas(64) unsigned char c2r_tmap[128];
     double* dir_parts;             // criterion partials of the direct blur
     int dir_parts_len;
 };
@@ -851,17 +855,12 @@ static sfw_status build_table(sfw_plan* p, cudaStream_t st) {
                 p->tc_ready = p->tc = true;
                 // the tail's real inverse along axis 2 (per-axis tails only: the slab tails fuse
                 // axes 1 and 2 already)
-                const int Kc = (p->Pc[2] + (p->Pc[2] & 1) + 15) / 16 * 16;
                 if (!cert_tail_supported(p->Pc[1], p->Pc[2], p->n[1], p->n[2]) && p->n[2] <= 128 &&
-                    tc_c2r_smem_bytes(Kc) <= 226u * 1024u) {
-                    const size_t cbytes = (size_t)128 * (size_t)((Kc + 63) / 64 * 64) * 2;
+                    p->H2c == p->Pc[2] / 2 + 1 && tc_c2r_fits(p->H2c)) {
+                    const size_t cbytes = (size_t)tc_c2r_chunks(p->H2c) * 128 * 128;
                     if ((st_ret = plan_alloc(p, (void**)&p->tc_c2r_C, cbytes))) break;
-                    if (cudaMemsetAsync(p->tc_c2r_C, 0, cbytes, st) != cudaSuccess) {
-                        st_ret = cuda_fail(cudaGetLastError(), "tensor-core tail matrix");
-                        break;
-                    }
-                    if ((st_ret = launch_tc_c2r_matrix(p->Pc[2], p->H2c, p->n[2], Kc, p->tc_c2r_C, st))) break;
-                    p->tc_c2r_Kc = Kc;
+                    if ((st_ret = launch_tc_c2r_matrix(p->Pc[2], p->H2c, p->n[2], p->tc_c2r_C, st))) break;
+                    p->c2r_tma = make_c2r_tmap(p->cA, p->H2c, p->H2p, (long long)p->n[0] * p->n[1], K, p->c2r_tmap);
                 }
             }
         }
@@ -1266,11 +1265,13 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
             break;
         }
         if (p->fft_cert) {
-            const size_t a_el = (size_t)K * p->n[0] * p->n[1] * p->H2c;
+            // lines of H2p = H2 rounded up to even complex values (a pitch of whole 16-byte
+            // units, as the tensor-core tail's tensor map wants)
+            p->H2p = (p->H2c + 1) & ~1;
+            const size_t a_el = (size_t)K * p->n[0] * p->n[1] * p->H2p;
             const size_t b_el = (size_t)p->n[0] * p->Pc[1] * p->H2c;
             const size_t c_el = (size_t)K * p->n[0] * p->Pc[1] * p->H2c;
-            // + 2 complex of slack: the tensor-core tail copies whole 16-byte units of it
-            if ((s = plan_alloc_t(p, &p->cA, a_el + 2))) break;
+            if ((s = plan_alloc_t(p, &p->cA, a_el))) break;
             if ((s = plan_alloc_t(p, &p->cB, b_el))) break;
             if ((s = plan_alloc_t(p, &p->cC, c_el))) break;
             if ((s = plan_alloc_t(p, &p->tail_err, 1))) break;
@@ -1719,12 +1720,14 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
         LaunchTag lt__(kCertTailTag);
         SFW_TRY(launch_cert_tail(t, p->tail_tma ? p->tail_tmap : nullptr, 0, st));
     } else {
+        // the axis-2 stage on the tensor cores reads the spectra with the line pitch H2p
+        const bool tc_tail = p->tc && p->tc_c2r_C && p->c2r_tma && !g_recorder;
         {   // axis 1 inverse over all kernels: (K n0, P1, H2) -> (K n0, n1, H2)
             C2CPass q;
             q.in = p->cC;
             q.out = p->cA;
             q.lin = ls((long long)P1 * H2, 1, H2, H2);
-            q.lout = ls((long long)n1 * H2, 1, H2, H2);
+            q.lout = tc_tail ? ls((long long)n1 * p->H2p, 1, p->H2p, H2) : ls((long long)n1 * H2, 1, H2, H2);
             q.nlines = (long long)K * n0 * H2;
             q.L = P1;
             q.in_off = 0;
@@ -1740,18 +1743,15 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
                 SFW_TRY(launch_c2c(q, st));
             }
         }
-        if (p->tc && p->tc_c2r_C && !g_recorder) {
+        if (tc_tail) {
             // real inverse along axis 2 and the max over k on the tensor cores
             C2rTcPass c;
             memset(&c, 0, sizeof(c));
-            c.spec = p->cA;
-            c.spec_stride = (long long)n0 * n1 * H2;
             c.C = p->tc_c2r_C;
             c.nlines = n0 * n1;
             c.P2 = P2;
             c.H2 = H2;
             c.n2 = n2;
-            c.Kc = p->tc_c2r_Kc;
             c.K = K;
             c.scale = (float)(1.0 / lambda);
             c.eta_out = eta_out;
@@ -1764,7 +1764,7 @@ static sfw_status certificate_impl(sfw_plan* p, const float* residual, double la
             c.err = p->tail_err;
             {
                 LaunchTag lt__(kCertC2rTcTag);
-                SFW_TRY(launch_c2r_tc(c, p->num_sms, st));
+                SFW_TRY(launch_c2r_tc(c, p->c2r_tmap, p->num_sms, st));
             }
             if (want_vox) SFW_TRY(launch_vox_decode(p->vox_key, p->V, max_out, argk_out, st));
             return SFW_OK;

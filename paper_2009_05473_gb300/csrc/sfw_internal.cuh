@@ -366,15 +366,14 @@ sfw_status launch_tc_dft(int n0, int P0, int Kp, __nv_bfloat16* A, cudaStream_t 
 size_t tc_smem_bytes(int Kp, int Np, int P0);
 
 // The certificate's real inverse along axis 2 with the max over kernels, on tcgen05
-// (cert_tc_c2r.cu): per 128 lines (i0, i1) and kernel k, eta = A C^T with A the line's half
-// spectrum as P2 real numbers (bf16) and C the fixed inverse matrix (n2 <= 128 outputs).
+// (cert_tc_c2r.cu): per 128 lines (i0, i1) and kernel k, eta = A C^T with A the lines' half
+// spectra read as 2 H2 FP32 numbers (tf32 MMAs) and C the fixed inverse matrix (n2 <= 128).
+// The spectra come through the tensor map of make_c2r_tmap: (K, nlines, H2) complex, line pitch
+// H2p (even).
 struct C2rTcPass {
-    const float2* spec;         // (K, nlines, H2) complex: line L of kernel k at spec + k spec_stride + L H2;
-                                // 16-byte aligned, readable 8 bytes past its end
-    long long spec_stride;
-    const __nv_bfloat16* C;     // 128 x Kc inverse matrix (launch_tc_c2r_matrix), 128-byte swizzled
-    int nlines, P2, H2, n2, Kc, K;   // Kc = P2 (+ 1 if odd) rounded up to 16
-    int kgroup;                 // kernels per CTA item (set by the launcher)
+    const float* C;             // the inverse matrix (launch_tc_c2r_matrix): tc_c2r_chunks(H2) atoms
+    int nlines, P2, H2, n2, K;
+    int kgroup, nch, stages;    // set by the launcher
     float scale;                // 1 / lambda
     float* eta_out;             // K x V or NULL
     long long V;
@@ -385,9 +384,12 @@ struct C2rTcPass {
     int64_t* best_idx;
     int* err;                   // set if a bounded wait ran out
 };
-sfw_status launch_tc_c2r_matrix(int P2, int H2, int n2, int Kc, __nv_bfloat16* C, cudaStream_t st);
-sfw_status launch_c2r_tc(const C2rTcPass& p, int num_sms, cudaStream_t st);
-size_t tc_c2r_smem_bytes(int Kc);
+int tc_c2r_chunks(int H2);                       // 32-column atoms of 2 H2 columns
+bool tc_c2r_fits(int H2);                        // C and two A stages fit in shared memory
+size_t tc_c2r_smem_bytes(int H2);
+sfw_status launch_tc_c2r_matrix(int P2, int H2, int n2, float* C, cudaStream_t st);
+bool make_c2r_tmap(const float2* spec, int H2, int H2p, long long nlines, int K, void* tmap_out);
+sfw_status launch_c2r_tc(const C2rTcPass& p, const void* tmap, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------------------ plain FP32 route (direct.cu)
 // Direct sums without transforms (the route the transform route is measured against).

@@ -50,6 +50,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
 
+// Instruction descriptor of kind::tf32 (A and B FP32 in memory, read as tf32; both K-major)
+// with FP32 accumulation.
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
+    return (1u << 4)                          // D format: FP32
+           | (2u << 7)                        // A format: tf32
+           | (2u << 10)                       // B format: tf32
+           | ((uint32_t)(N >> 3) << 17)       // N / 8
+           | ((uint32_t)(M >> 4) << 24);      // M / 16
+}
+
 // Tensor memory: allocation and release by one whole warp; the address lands in *slot.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
@@ -66,6 +76,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
                                          uint32_t accumulate) {
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
+// D (+)= A B^T for one K = 8 slice of tf32 operands (32 bytes of a 128-byte row).
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
                  :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
 }
 // The mbarrier at bar receives one arrival once every earlier tcgen05 op of this thread is done.
@@ -143,6 +160,13 @@ __device__ __forceinline__ bool bar_sync_or(bool v) {
                  " selp.u32 %0, 1, 0, q;\n}\n"
                  : "=r"(r) : "r"((uint32_t)v), "n"(id), "n"(count) : "memory");
     return r != 0;
+}
+// A 3-D box of a tiled tensor map into shared memory (x in elements, a multiple of 16 bytes);
+// completes on bar with the box's bytes (out-of-range elements read as zero).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z, uint32_t bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];\n"
+                 :: "r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
 }
 // bytes (multiple of 16) from global src to shared dst (both 16-byte aligned); completes on bar.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
