@@ -194,6 +194,8 @@ def algorithmic_bytes(tag: str, plan, vol) -> float:
         "cert_x0fwd": n0 * Pc[1] * H2c * c8 + Pc[0] * Pc[1] * H2c * c8,
         "cert_axis0_tc": (Pc[0] * Pc[1] * H2c * c8 + Pc[1] * H2c * _r16(K) * _r16(Pc[0]) * 2
                           + K * n0 * Pc[1] * H2c * c8),
+        # tensor-core tail: the K axis-2 half spectra, read once as FP32, and the per-voxel keys
+        "cert_c2r_tc": K * n0 * n1 * H2c * c8 + V * 8,
         "cert_head": V * 4 + n0 * Pc[1] * H2c * c8,
         "blur_r2c": VE * 4 + E[0] * E[1] * H2 * c8,
         "blur_c2c_fwd": E[0] * E[1] * H2 * c8 + E[0] * P[1] * H2 * c8,

@@ -191,8 +191,239 @@ __global__ void k_topk_decode(const unsigned long long* keys, int k, float* val,
     }
 }
 
+// ---- top-k of many values by radix selection: the order keys (float_order_key) of the k-th
+// largest value t are found 12 + 12 + 8 bits at a time from histograms, then the values above t
+// and the lowest-index values equal to t are gathered and sorted.  The result equals the sort of
+// all candidate keys (value, then lowest index); a NaN anywhere makes every output NaN / -1.
+constexpr int kSelGrid = 256;          // blocks of the passes over the values (contiguous chunks)
+constexpr int kSelBins = 4096;
+// scratch layout (64-bit slots)
+constexpr long long kSelHist = 0;                      // kSelBins counters (32-bit)
+constexpr long long kSelState = kSelHist + kSelBins / 2;   // 32 counters (32-bit)
+constexpr long long kSelAbove = kSelState + 16;        // <= 64 keys above t
+constexpr long long kSelBlkCnt = kSelAbove + 64;       // ties kept per block
+constexpr long long kSelBlkTies = kSelBlkCnt + kSelGrid;   // <= 64 tie keys per block, in index order
+constexpr long long kSelOut = kSelBlkTies + (long long)kSelGrid * 64;
+constexpr long long kSelScratch = kSelOut + 64;
+// state words: prefix of t's order key fixed so far, count above the current bin range,
+// NaN seen, keys gathered above t, ties wanted (k - above)
+enum { kStPrefix = 0, kStAbove = 1, kStNan = 2, kStNa = 3, kStM = 4 };
+
+// level 0: bits 31..20 of every value's order key; level 1: bits 19..8 of those whose bits 31..20
+// equal the prefix; level 2: bits 7..0 of those whose bits 31..8 do
+__device__ __forceinline__ int sel_shift(int level) { return level == 0 ? 20 : level == 1 ? 8 : 0; }
+
+__global__ void __launch_bounds__(kRedThreads) k_sel_hist(const float* __restrict__ v, long long count, int level,
+                                                          unsigned long long* scratch) {
+    __shared__ unsigned int h[kSelBins];
+    unsigned int* gh = reinterpret_cast<unsigned int*>(scratch + kSelHist);
+    unsigned int* stw = reinterpret_cast<unsigned int*>(scratch + kSelState);
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+    const unsigned int prefix = stw[kStPrefix];
+    const int sh = sel_shift(level), hi = level == 0 ? 32 : sel_shift(level - 1);
+    const unsigned int mask = level == 2 ? 0xFFu : 0xFFFu;
+    bool nan = false;
+    // four loads in flight per thread
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < count; g0 += 4 * stride) {
+        float x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = g0 + j * stride < count ? v[g0 + j * stride] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (g0 + j * stride >= count) continue;
+            if (x[j] != x[j]) {
+                nan = true;
+                continue;
+            }
+            const unsigned int o = float_order_key(x[j]);
+            if (hi < 32 && (o >> hi) != (prefix >> hi)) continue;
+            atomicAdd(&h[(o >> sh) & mask], 1u);
+        }
+    }
+    if (nan) stw[kStNan] = 1u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&gh[i], h[i]);
+}
+
+// One block: the bin of the k-th largest key at this level (counting from the top, after the
+// keys already known to lie above), its bits into the prefix; the histogram is cleared.
+__global__ void __launch_bounds__(kRedThreads) k_sel_pick(int level, int k, unsigned long long* scratch) {
+    __shared__ unsigned int hs[kSelBins];
+    __shared__ unsigned int wsum[kRedThreads / 32];
+    __shared__ int s_found;
+    unsigned int* gh = reinterpret_cast<unsigned int*>(scratch + kSelHist);
+    unsigned int* stw = reinterpret_cast<unsigned int*>(scratch + kSelState);
+    const int nb = level == 2 ? 256 : kSelBins;
+    const int per = nb / kRedThreads;                  // bins per thread; thread 0 the top ones
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = t; i < kSelBins; i += blockDim.x) {
+        hs[i] = gh[i];
+        gh[i] = 0u;
+    }
+    if (t == 0) s_found = 0;
+    __syncthreads();
+    unsigned int part = 0;
+    for (int j = 0; j < per; ++j) part += hs[nb - 1 - (t * per + j)];
+    // inclusive scan over threads (from the top bins down)
+    unsigned int incl = part;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    for (int w = 0; w < warp; ++w) incl += wsum[w];
+    const unsigned int above = stw[kStAbove];
+    const unsigned int excl = incl - part;
+    if (above + excl < (unsigned int)k && above + incl >= (unsigned int)k) {
+        unsigned int acc = above + excl;
+        int bin = nb - 1 - t * per;
+        for (int j = 0; j < per; ++j) {
+            const int b = nb - 1 - (t * per + j);
+            if (acc + hs[b] >= (unsigned int)k) {
+                bin = b;
+                break;
+            }
+            acc += hs[b];
+        }
+        s_found = 1;
+        stw[kStPrefix] |= (unsigned int)bin << sel_shift(level);
+        stw[kStAbove] = acc;
+        if (level == 2) stw[kStM] = (unsigned int)k - acc;
+    }
+    __syncthreads();
+    // fewer than k values that are not NaN: leave the prefix (the output is NaN / -1 anyway)
+    if (t == 0 && !s_found && level == 2) stw[kStM] = 0u;
+}
+
+// The keys above t (at most k - 1, any order) and, per block, the first m keys equal to t in
+// index order (blocks take contiguous chunks).
+__global__ void __launch_bounds__(kRedThreads) k_sel_gather(const float* __restrict__ v, long long count,
+                                                            unsigned long long* scratch) {
+    __shared__ unsigned int warp_cnt[kRedThreads / 32];
+    __shared__ unsigned int s_taken;
+    unsigned int* stw = reinterpret_cast<unsigned int*>(scratch + kSelState);
+    const unsigned int tkey = stw[kStPrefix], m = stw[kStM];
+    unsigned long long* above = scratch + kSelAbove;
+    unsigned long long* ties = scratch + kSelBlkTies + (long long)blockIdx.x * 64;
+    const long long chunk = (count + gridDim.x - 1) / gridDim.x;
+    const long long b0 = (long long)blockIdx.x * chunk, b1 = min(count, b0 + chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_taken = 0;
+    __syncthreads();
+    constexpr int U = 4;
+    for (long long base = b0; base < b1; base += U * blockDim.x) {
+        float x[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const long long g = base + j * blockDim.x + threadIdx.x;
+            x[j] = g < b1 ? v[g] : __int_as_float(0x7fc00000);
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const long long g = base + j * blockDim.x + threadIdx.x;
+            bool tie = false;
+            unsigned long long key = 0ull;
+            if (x[j] == x[j]) {   // beyond the chunk: NaN, never taken
+                const unsigned int o = float_order_key(x[j]);
+                key = candidate_key(x[j], (unsigned long long)g);
+                if (o > tkey) {
+                    const unsigned int pos = atomicAdd(&stw[kStNa], 1u);
+                    if (pos < 64u) above[pos] = key;
+                }
+                tie = o == tkey;
+            }
+            // ties in index order (rank in the warp, then the warps before); skipped when this
+            // group of the block holds none
+            if (__syncthreads_or(tie)) {
+                const unsigned int bal = __ballot_sync(0xffffffffu, tie);
+                if (lane == 0) warp_cnt[warp] = __popc(bal);
+                __syncthreads();
+                unsigned int before = s_taken;
+                for (int w = 0; w < warp; ++w) before += warp_cnt[w];
+                const unsigned int r = before + __popc(bal & ((1u << lane) - 1u));
+                if (tie && r < m) ties[r] = key;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned int tot = 0;
+                    for (int w = 0; w < kRedThreads / 32; ++w) tot += warp_cnt[w];
+                    s_taken += tot;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (threadIdx.x == 0) scratch[kSelBlkCnt + blockIdx.x] = min(s_taken, m);
+}
+
+// One block: the keys above t, then ties block by block until k keys, sorted descending.
+__global__ void __launch_bounds__(64) k_sel_final(int k, int nblocks, unsigned long long* scratch) {
+    __shared__ unsigned long long s[64];
+    __shared__ unsigned int cnt[kSelGrid];
+    unsigned int* stw = reinterpret_cast<unsigned int*>(scratch + kSelState);
+    const int t = threadIdx.x;
+    const unsigned int na = min(stw[kStNa], 64u);
+    s[t] = (unsigned int)t < na ? scratch[kSelAbove + t] : 0ull;
+    for (int b = t; b < nblocks; b += 64) cnt[b] = (unsigned int)scratch[kSelBlkCnt + b];
+    __syncthreads();
+    if (t == 0) {
+        unsigned int n = na;
+        for (int b = 0; b < nblocks && n < (unsigned int)k; ++b)
+            for (unsigned int j = 0; j < cnt[b] && n < (unsigned int)k; ++j)
+                s[n++] = scratch[kSelBlkTies + (long long)b * 64 + j];
+    }
+    __syncthreads();
+    // bitonic sort of 64 keys, descending
+    for (int size = 2; size <= 64; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int partner = t ^ stride;
+            const unsigned long long a = s[t], b = s[partner];
+            __syncthreads();
+            if (partner > t) {
+                const bool desc = (t & size) == 0;
+                if ((a < b) == desc) {
+                    s[t] = b;
+                    s[partner] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    unsigned long long* out = scratch + kSelOut;
+    if (t < k) out[t] = (stw[kStNan] && t == 0) ? ~0ull : s[t];
+}
+
+static sfw_status launch_topk_select(const float* v, long long count, int topk, unsigned long long* scratch,
+                                     float* val_out, int64_t* idx_out, cudaStream_t st) {
+    SFW_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)(kSelBlkCnt + kSelGrid), st));
+    for (int level = 0; level < 3; ++level) {
+        SFW_LAUNCH(st, "k_sel_hist", k_sel_hist<<<4 * kSelGrid, kRedThreads, 0, st>>>(v, count, level, scratch));
+        SFW_TRY(launch_check("k_sel_hist"));
+        SFW_LAUNCH(st, "k_sel_pick", k_sel_pick<<<1, kRedThreads, 0, st>>>(level, topk, scratch));
+        SFW_TRY(launch_check("k_sel_pick"));
+    }
+    SFW_LAUNCH(st, "k_sel_gather", k_sel_gather<<<kSelGrid, kRedThreads, 0, st>>>(v, count, scratch));
+    SFW_TRY(launch_check("k_sel_gather"));
+    SFW_LAUNCH(st, "k_sel_final", k_sel_final<<<1, 64, 0, st>>>(topk, kSelGrid, scratch));
+    SFW_TRY(launch_check("k_sel_final"));
+    SFW_LAUNCH(st, "k_topk_decode", k_topk_decode<<<1, 64, 0, st>>>(scratch + kSelOut, topk, val_out, idx_out));
+    return launch_check("k_topk_decode");
+}
+
+long long topk_scratch_keys(long long count, int topk) {
+    const long long blocks = (count + kSortN - 1) / kSortN;
+    const long long sorts = 2 * (blocks * topk + 64);
+    return count > 65536 && sorts < kSelScratch ? kSelScratch : sorts;
+}
+
 sfw_status launch_topk(const float* v, long long count, int topk, unsigned long long* scratch,
                        long long scratch_len, float* val_out, int64_t* idx_out, cudaStream_t st) {
+    // many values: radix selection (a few passes over the values instead of block sorts)
+    if (count > 65536 && topk <= 64 && scratch_len >= kSelScratch)
+        return launch_topk_select(v, count, topk, scratch, val_out, idx_out, st);
     // ping-pong halves of scratch
     long long blocks = (count + kSortN - 1) / kSortN;
     long long half = scratch_len / 2;

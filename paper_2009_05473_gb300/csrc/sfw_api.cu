@@ -2042,8 +2042,7 @@ sfw_status sfw_argmax(const float* values, int64_t count, int topk, float* val_o
     static thread_local int scratch_dev = -1;
     int dev = 0;
     SFW_CUDA(cudaGetDevice(&dev));
-    const long long blocks = (count + 4095) / 4096;
-    const long long need = topk == 1 ? 1024 : 2 * (blocks * topk + 64);
+    const long long need = topk == 1 ? 1024 : topk_scratch_keys(count, topk);
     if (scratch_len < need || scratch_dev != dev) {
         if (scratch) {
             cudaStreamSynchronize(st);

@@ -503,6 +503,8 @@ sfw_status launch_argmax_keys(const float* v, long long count, unsigned long lon
                               int nblocks, cudaStream_t st);
 sfw_status launch_argmax_final(const unsigned long long* partial, int n, float* val, int64_t* idx,
                                cudaStream_t st);
+// Scratch keys launch_topk wants for `count` values (it falls back to block sorts with less).
+long long topk_scratch_keys(long long count, int topk);
 sfw_status launch_topk(const float* v, long long count, int topk, unsigned long long* scratch,
                        long long scratch_len, float* val_out, int64_t* idx_out, cudaStream_t st);
 sfw_status launch_spec_stats(const float2* s, long long count, float* stats /*2 floats*/,

@@ -154,6 +154,33 @@ def test_argmax_topk_bruteforce_with_ties(sfw, oracle_mod, torch_mod, count):
     np.testing.assert_array_equal(val.cpu().numpy(), v[order])
 
 
+@pytest.mark.parametrize("kind", ["levels", "equal", "negative"])
+def test_topk_many_values_with_massive_ties(sfw, torch_mod, kind):
+    """Top-k of 2^21 + 7 values (the radix-selection path): ties at the k-th value spread over
+    every block must resolve to the lowest indices, exactly as a sort of (value desc, index asc)."""
+    count = (1 << 21) + 7
+    rng = np.random.default_rng(11)
+    if kind == "levels":
+        v = rng.integers(0, 40, count).astype(np.float32)      # ~52k copies of every value
+    elif kind == "equal":
+        v = np.full(count, 3.5, np.float32)
+    else:
+        v = -rng.integers(1, 1000, count).astype(np.float32) / 7.0
+    dv = torch_mod.tensor(v, device="cuda")
+    for k in (2, 17, 64):
+        val, idx = sfw.argmax(dv, k)
+        order = np.lexsort((np.arange(count), -v.astype(np.float64)))[:k]
+        np.testing.assert_array_equal(idx.cpu().numpy(), order)
+        np.testing.assert_array_equal(val.cpu().numpy(), v[order])
+
+
+def test_topk_many_values_nan_is_reported(sfw, torch_mod):
+    v = torch_mod.randn(300_001, device="cuda")
+    v[250_000] = float("nan")
+    val, idx = sfw.argmax(v, 16)
+    assert int(idx[0].item()) == -1
+
+
 def test_argmax_nan_is_reported(sfw, torch_mod):
     v = torch_mod.zeros(1000, device="cuda")
     v[417] = float("nan")
