@@ -182,31 +182,49 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
             tc::bulk_g2s(tc::smem_addr(base + L.a), p.A + (size_t)h * 128u * 2u * (size_t)Kp, abytes,
                          tc::smem_addr(&s_abar));
             if (!tc::mbar_wait(tc::smem_addr(&s_abar), 0)) s_abort = 1;
-            const uint32_t a0 = tc::smem_addr(base + L.a);
-            for (long long q = 0; q < my_blocks && !s_abort; ++q) {
-                const long long u = q / nb;
-                const int b = (int)(q % nb), s = (int)(q % 3), ub = (int)(u & 1);
-                if (b == 0 && u >= 2 && !tc::mbar_wait(tc::smem_addr(&s_acce[ub]), (uint32_t)((u - 2) >> 1) & 1u)) {
+            // This one thread's instruction latency paces the MMAs: descriptors are built once
+            // and advanced by adding to their address field (16-byte units), the B' stage ring
+            // (3 stages) is tracked without divisions, a block's 8 MMAs are unrolled.
+            const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_addr(base + L.a));
+            // the B' stages lie 2 x 16 KB apart (Re and Im slices)
+            const uint64_t dB0 = tc::desc_kmajor_sw128(tc::smem_addr(base + L.b[0]));
+            constexpr uint64_t kAtom = (16u * 1024u) >> 4, kKStep = 32u >> 4, kImOff = (128u * 64u * 2u) >> 4;
+            constexpr uint64_t kStage = 2 * kImOff;
+            int s = 0;
+            uint32_t ph = 0;
+            for (long long u = 0; u < my_tiles && !s_abort; ++u) {
+                const int ub = (int)(u & 1);
+                // the tile's accumulator is free once the epilogue has read tile u - 2
+                if (u >= 2 && !tc::mbar_wait(tc::smem_addr(&s_acce[ub]), (uint32_t)((u - 2) >> 1) & 1u)) {
                     s_abort = 1;
                     break;
                 }
-                if (!tc::mbar_wait(tc::smem_addr(&s_bfull[s]), (uint32_t)(q / 3) & 1u)) {
-                    s_abort = 1;
-                    break;
-                }
-                tc::fence_after_sync();
                 const uint32_t d = tmem + (uint32_t)(ub * 128);
-                const uint32_t bre = tc::smem_addr(base + L.b[s]), bim = bre + 128u * 64u * 2u;
-                // A's 64-column atoms: Re block b at column atom b, Im block b at atom nb + b
-                const uint32_t are = a0 + (uint32_t)b * 16u * 1024u, aim = a0 + (uint32_t)(nb + b) * 16u * 1024u;
-                for (int ks = 0; ks < 4; ++ks)
-                    tc::mma_bf16(d, tc::desc_kmajor_sw128(are + (uint32_t)ks * 32u),
-                                 tc::desc_kmajor_sw128(bre + (uint32_t)ks * 32u), idesc, (b > 0 || ks > 0) ? 1u : 0u);
-                for (int ks = 0; ks < 4; ++ks)
-                    tc::mma_bf16(d, tc::desc_kmajor_sw128(aim + (uint32_t)ks * 32u),
-                                 tc::desc_kmajor_sw128(bim + (uint32_t)ks * 32u), idesc, 1u);
-                tc::mma_commit(tc::smem_addr(&s_done[s]));
-                if (b == nb - 1) tc::mma_commit(tc::smem_addr(&s_accf[ub]));
+                for (int b = 0; b < nb; ++b) {
+                    if (!tc::mbar_wait(tc::smem_addr(&s_bfull[s]), ph)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    // A's 64-column atoms: Re block b at column atom b, Im block b at atom nb + b
+                    const uint64_t are = dA0 + (uint64_t)b * kAtom, aim = dA0 + (uint64_t)(nb + b) * kAtom;
+                    const uint64_t bre = dB0 + (uint64_t)s * kStage, bim = bre + kImOff;
+                    tc::mma_bf16(d, are, bre, idesc, b > 0 ? 1u : 0u);
+                    tc::mma_bf16(d, are + kKStep, bre + kKStep, idesc, 1u);
+                    tc::mma_bf16(d, are + 2 * kKStep, bre + 2 * kKStep, idesc, 1u);
+                    tc::mma_bf16(d, are + 3 * kKStep, bre + 3 * kKStep, idesc, 1u);
+                    tc::mma_bf16(d, aim, bim, idesc, 1u);
+                    tc::mma_bf16(d, aim + kKStep, bim + kKStep, idesc, 1u);
+                    tc::mma_bf16(d, aim + 2 * kKStep, bim + 2 * kKStep, idesc, 1u);
+                    tc::mma_bf16(d, aim + 3 * kKStep, bim + 3 * kKStep, idesc, 1u);
+                    tc::mma_commit(tc::smem_addr(&s_done[s]));
+                    if (++s == 3) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (s_abort) break;
+                tc::mma_commit(tc::smem_addr(&s_accf[ub]));
             }
         }
         __syncwarp();
@@ -225,6 +243,8 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
         };
         if (my_tiles > 0) stage_x(0);
         constexpr int PER = 128 * 8 / kTcFormThreads;     // items (16-byte chunks) per thread and block
+        int s = 0;          // B' stage of the next block (ring of 3) and its use count
+        uint32_t uses = 0;
         for (long long u = 0; u < my_tiles; ++u) {
             tc::cp_async_wait_all();
             // all formation threads stop together (a barrier with a missing thread never ends)
@@ -233,8 +253,6 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
             const float2* xs = reinterpret_cast<const float2*>(base + L.xs[u & 1]);
             const long long l0 = tile_l0(u);
             for (int b = 0; b < nb; ++b) {
-                const long long q = u * nb + b;
-                const int s = (int)(q % 3);
                 // this thread's table chunks of the block, from global memory (L2) into registers
                 uint4 tv[PER];
 #pragma unroll
@@ -246,8 +264,8 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                     const unsigned char* blk = reinterpret_cast<const unsigned char*>(p.Tb + (size_t)l * (size_t)Np * (size_t)Kp);
                     tv[r] = __ldg(reinterpret_cast<const uint4*>(blk + tc::kmajor_offset(n, 64 * b + 8 * c, Np)));
                 }
-                // B'[s] is free once the MMAs of block q - 3 are done
-                if (q >= 3 && !tc::mbar_wait(tc::smem_addr(&s_done[s]), (uint32_t)((q - 3) / 3) & 1u)) s_abort = 1;
+                // B'[s] is free once the MMAs of its previous use (block q - 3) are done
+                if (uses > 0 && !tc::mbar_wait(tc::smem_addr(&s_done[s]), (uses - 1u) & 1u)) s_abort = 1;
                 if (s_abort) break;
                 unsigned char* Bre = base + L.b[s];
                 unsigned char* Bim = Bre + 128u * 64u * 2u;
@@ -273,6 +291,10 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_addr(&s_bfull[s]));
+                if (++s == 3) {
+                    s = 0;
+                    ++uses;
+                }
             }
         }
         tc::cp_async_wait_all();

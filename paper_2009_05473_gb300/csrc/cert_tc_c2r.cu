@@ -161,35 +161,46 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p, const __
             const uint32_t cbytes = (uint32_t)nch * kC2rAtom;
             tc::mbar_expect_tx(tc::smem_addr(&s_cbar), cbytes);
             tc::bulk_g2s(tc::smem_addr(Cs), p.C, cbytes, tc::smem_addr(&s_cbar));
-            uint32_t g = 0;   // chunks issued
+            // ring position of the next chunk; its use count's parity flips at every wrap
+            uint32_t slot = 0, ph = 0;
+            bool wrapped = false;
             for (long long it = blockIdx.x; it < items && !s_abort; it += gridDim.x) {
                 int k0, k1;
                 item_k(it, &k0, &k1);
                 const int y = (int)(it / ngroups) * kC2rRows;
                 for (int k = k0; k < k1 && !s_abort; ++k) {
-                    for (int c = 0; c < nch; ++c, ++g) {
-                        const uint32_t slot = g % (uint32_t)S;
+                    for (int c = 0; c < nch; ++c) {
                         // the stage is free once the MMAs of its previous chunk are done
-                        if (g >= (uint32_t)S &&
-                            !tc::mbar_wait(tc::smem_addr(&s_empty[slot]), ((g / (uint32_t)S) - 1u) & 1u)) {
+                        if (wrapped && !tc::mbar_wait(tc::smem_addr(&s_empty[slot]), ph ^ 1u)) {
                             s_abort = 1;
                             break;
                         }
                         tc::mbar_expect_tx(tc::smem_addr(&s_full[slot]), kC2rAtom);
                         tc::tma_load_3d(tc::smem_addr(ring + slot * kC2rAtom), &tm, c * kC2rChunk, y, k,
                                         tc::smem_addr(&s_full[slot]));
+                        if (++slot == (uint32_t)S) {
+                            slot = 0;
+                            ph ^= 1u;
+                            wrapped = true;
+                        }
                     }
                 }
             }
         }
         __syncwarp();
     } else if (warp == kC2rMmaWarp) {
-        // ---------------- MMA lane
+        // ---------------- MMA lane.  This one thread's instruction latency paces the MMAs: the
+        // descriptors are built once and advanced by adding to their address field (16-byte
+        // units), the ring position is tracked without divisions, a chunk's MMAs are unrolled.
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_tf32_f32(kC2rRows, kC2rN);
-            const uint32_t c0 = tc::smem_addr(Cs), r0 = tc::smem_addr(ring);
+            const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_addr(ring));
+            const uint64_t dB0 = tc::desc_kmajor_sw128(tc::smem_addr(Cs));
+            constexpr uint64_t kAtomStep = kC2rAtom >> 4, kKStep = 32u >> 4;   // atom, K = 8 slice
+            // K = 8 slices of the last chunk holding columns < 2 H2 (the rest is zero)
+            const int nks_last = min(4, (2 * p.H2 - (nch - 1) * kC2rChunk + 7) / 8);
             if (!tc::mbar_wait(tc::smem_addr(&s_cbar), 0)) s_abort = 1;
-            uint32_t g = 0, t = 0;
+            uint32_t slot = 0, ph = 0, t = 0;
             for (long long it = blockIdx.x; it < items && !s_abort; it += gridDim.x) {
                 int k0, k1;
                 item_k(it, &k0, &k1);
@@ -201,21 +212,29 @@ __global__ void __launch_bounds__(kC2rThreads, 1) k_c2r_tc(C2rTcPass p, const __
                         break;
                     }
                     const uint32_t d = tmem + (uint32_t)(s * kC2rN);
-                    for (int c = 0; c < nch; ++c, ++g) {
-                        const uint32_t slot = g % (uint32_t)S;
-                        if (!tc::mbar_wait(tc::smem_addr(&s_full[slot]), (g / (uint32_t)S) & 1u)) {
+                    for (int c = 0; c < nch; ++c) {
+                        if (!tc::mbar_wait(tc::smem_addr(&s_full[slot]), ph)) {
                             s_abort = 1;
                             break;
                         }
                         tc::fence_after_sync();
-                        // K = 8 slices holding columns < 2 H2 (the rest of the last chunk is zero)
-                        const int nks = min(4, (2 * p.H2 - c * kC2rChunk + 7) / 8);
-                        const uint32_t a0 = r0 + slot * kC2rAtom, b0 = c0 + (uint32_t)c * kC2rAtom;
-                        for (int ks = 0; ks < nks; ++ks)
-                            tc::mma_tf32(d, tc::desc_kmajor_sw128(a0 + (uint32_t)ks * 32u),
-                                         tc::desc_kmajor_sw128(b0 + (uint32_t)ks * 32u), idesc,
-                                         (c > 0 || ks > 0) ? 1u : 0u);
+                        const uint64_t a = dA0 + slot * kAtomStep, b = dB0 + (uint64_t)c * kAtomStep;
+                        const uint32_t acc0 = c > 0 ? 1u : 0u;
+                        if (c + 1 < nch) {
+                            tc::mma_tf32(d, a, b, idesc, acc0);
+                            tc::mma_tf32(d, a + kKStep, b + kKStep, idesc, 1u);
+                            tc::mma_tf32(d, a + 2 * kKStep, b + 2 * kKStep, idesc, 1u);
+                            tc::mma_tf32(d, a + 3 * kKStep, b + 3 * kKStep, idesc, 1u);
+                        } else {
+                            tc::mma_tf32(d, a, b, idesc, acc0);
+                            for (int ks = 1; ks < nks_last; ++ks)
+                                tc::mma_tf32(d, a + ks * kKStep, b + ks * kKStep, idesc, 1u);
+                        }
                         tc::mma_commit(tc::smem_addr(&s_empty[slot]));
+                        if (++slot == (uint32_t)S) {
+                            slot = 0;
+                            ph ^= 1u;
+                        }
                     }
                     if (s_abort) break;
                     tc::mma_commit(tc::smem_addr(&s_done[s]));
