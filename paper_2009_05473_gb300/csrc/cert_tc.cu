@@ -152,7 +152,6 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     const long long gi = blockIdx.x / halves;
     const long long ntiles = (p.nl + LT - 1) / LT;
     const long long my_tiles = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
-    const long long my_blocks = my_tiles * nb;
     auto tile_l0 = [&](long long u) -> long long { return (gi + u * G) * LT; };
 
     if (tid == 0) {
@@ -245,25 +244,32 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
         constexpr int PER = 128 * 8 / kTcFormThreads;     // items (16-byte chunks) per thread and block
         int s = 0;          // B' stage of the next block (ring of 3) and its use count
         uint32_t uses = 0;
+        const int lnp = __ffs(Np) - 1;                    // Np is a power of two
+        // this thread's table chunks of block b of tile u, from global memory into registers;
+        // the next block's are loaded while the current one is formed
+        auto load_t = [&](long long u, int b, uint4 (&tv)[PER]) {
+            const long long l0 = tile_l0(u);
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int e = tid + r * kTcFormThreads;
+                const int col = e & 127, c = e >> 7;
+                const int j = col >> lnp, n = col - (j << lnp);
+                const long long l = min(l0 + j, p.nl - 1);   // padding lines read a real block
+                const unsigned char* blk = reinterpret_cast<const unsigned char*>(p.Tb + (size_t)l * (size_t)Np * (size_t)Kp);
+                tv[r] = __ldg(reinterpret_cast<const uint4*>(blk + tc::kmajor_offset(n, 64 * b + 8 * c, Np)));
+            }
+        };
+        uint4 tv[PER], tvn[PER];
+        if (my_tiles > 0) load_t(0, 0, tv);
         for (long long u = 0; u < my_tiles; ++u) {
             tc::cp_async_wait_all();
             // all formation threads stop together (a barrier with a missing thread never ends)
             if (tc::bar_sync_or<1, kTcFormThreads>(s_abort != 0)) break;
             if (u + 1 < my_tiles) stage_x(u + 1);
             const float2* xs = reinterpret_cast<const float2*>(base + L.xs[u & 1]);
-            const long long l0 = tile_l0(u);
             for (int b = 0; b < nb; ++b) {
-                // this thread's table chunks of the block, from global memory (L2) into registers
-                uint4 tv[PER];
-#pragma unroll
-                for (int r = 0; r < PER; ++r) {
-                    const int e = tid + r * kTcFormThreads;
-                    const int col = e & 127, c = e >> 7;
-                    const int j = col / Np, n = col - j * Np;
-                    const long long l = min(l0 + j, p.nl - 1);   // padding lines read a real block
-                    const unsigned char* blk = reinterpret_cast<const unsigned char*>(p.Tb + (size_t)l * (size_t)Np * (size_t)Kp);
-                    tv[r] = __ldg(reinterpret_cast<const uint4*>(blk + tc::kmajor_offset(n, 64 * b + 8 * c, Np)));
-                }
+                if (b + 1 < nb) load_t(u, b + 1, tvn);
+                else if (u + 1 < my_tiles) load_t(u + 1, 0, tvn);
                 // B'[s] is free once the MMAs of its previous use (block q - 3) are done
                 if (uses > 0 && !tc::mbar_wait(tc::smem_addr(&s_done[s]), (uses - 1u) & 1u)) s_abort = 1;
                 if (s_abort) break;
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                 for (int r = 0; r < PER; ++r) {
                     const int e = tid + r * kTcFormThreads;
                     const int col = e & 127, c = e >> 7;          // column of B', 8-point chunk of the block
-                    const int j = col / Np;
+                    const int j = col >> lnp;
                     const uint32_t tw[4] = {tv[r].x, tv[r].y, tv[r].z, tv[r].w};
                     const float4* x4 = reinterpret_cast<const float4*>(xs + j * Kp + 64 * b + 8 * c);
                     uint32_t re[4], imv[4];
@@ -291,6 +297,8 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(tc::smem_addr(&s_bfull[s]));
+#pragma unroll
+                for (int r = 0; r < PER; ++r) tv[r] = tvn[r];
                 if (++s == 3) {
                     s = 0;
                     ++uses;
