@@ -126,6 +126,15 @@ class GPUSolver:
         self.lo1 = np.array([0.0, 0.0, 0.0, SIGMA_RANGE[0], D_RANGE[0]])
         self.hi1 = np.array([n[0] - 1.0, n[1] - 1.0, n[2] - 1.0, SIGMA_RANGE[1], D_RANGE[1]])
         self.stats = {"certificate": 0, "eta_points": 0, "slide_evals": 0, "gram": 0}
+        # wall time of each kind of library call, from its launch until its results are on the
+        # host (device work, launch overhead, atom uploads); the rest of a solve is host code
+        self.call_seconds = {"certificate": 0.0, "eta_points": 0.0, "slide": 0.0, "gram": 0.0}
+
+    def _timed(self, what: str, fn):
+        t = time.perf_counter()
+        out = fn()
+        self.call_seconds[what] += time.perf_counter() - t
+        return out
 
     # -- device calls --------------------------------------------------------------------
     def _atoms(self, thetas: np.ndarray, w: np.ndarray) -> AtomSet:
@@ -145,15 +154,20 @@ class GPUSolver:
         return float(loss.item())
 
     # -- step 1 --------------------------------------------------------------------------
-    def certificate_max(self, thetas, w):
+    def _grid_argmax(self, thetas, w):
         r = self.residual(thetas, w)
+        out = self.plan.certificate(r, self.lam, want_max=False)
+        return r, int(out["best_idx"].item())
+
+    def certificate_max(self, thetas, w):
         self.stats["certificate"] += 1
         if self.topk:
-            out = self.plan.certificate_topk(r, self.lam, self.topk)
-            theta0 = out["best_theta"].double().cpu().numpy()
+            def call():
+                r = self.residual(thetas, w)
+                return r, self.plan.certificate_topk(r, self.lam, self.topk)["best_theta"].double().cpu().numpy()
+            r, theta0 = self._timed("certificate", call)
         else:
-            out = self.plan.certificate(r, self.lam, want_max=False)
-            flat = int(out["best_idx"].item())
+            r, flat = self._timed("certificate", lambda: self._grid_argmax(thetas, w))
             if flat < 0:
                 raise FloatingPointError("certificate holds a NaN")
             k, lin = divmod(flat, self.plan.V)
@@ -162,8 +176,11 @@ class GPUSolver:
 
         def neg_eta(th):
             self.stats["eta_points"] += 1
-            e, g = self.plan.eta_points(r, self.lam, th[None, :])
-            return -float(e.item()), -g[0].cpu().numpy()
+
+            def call():
+                e, g = self.plan.eta_points(r, self.lam, th[None, :])
+                return -float(e.item()), -g[0].cpu().numpy()
+            return self._timed("eta_points", call)
 
         th, f, _ = box_bfgs(neg_eta, theta0, self.lo1, self.hi1, gtol=self.ascent_gtol)
         return th, -f, theta0
@@ -171,8 +188,12 @@ class GPUSolver:
     # -- step 3 --------------------------------------------------------------------------
     def lasso(self, thetas) -> np.ndarray:
         self.stats["gram"] += 1
-        G, c = self.plan.gram(self._atoms(thetas, np.ones(thetas.shape[0])), self.y)
-        return nonneg_quadratic_min(G.cpu().numpy(), c.cpu().numpy() - self.lam)
+
+        def call():
+            G, c = self.plan.gram(self._atoms(thetas, np.ones(thetas.shape[0])), self.y)
+            return G.cpu().numpy(), c.cpu().numpy()
+        G, c = self._timed("gram", call)
+        return nonneg_quadratic_min(G, c - self.lam)
 
     # -- step 4 / 2b ---------------------------------------------------------------------
     def slide(self, thetas, w, max_iter=300):
@@ -184,8 +205,11 @@ class GPUSolver:
         def fg(x):
             self.stats["slide_evals"] += 1
             th, ww = _unpack(x)
-            loss, grad, _ = self.plan.slide_loss_grad(self.y, self._atoms(th, ww), self.lam)
-            return float(loss.item()), grad.cpu().numpy()
+
+            def call():
+                loss, grad, _ = self.plan.slide_loss_grad(self.y, self._atoms(th, ww), self.lam)
+                return float(loss.item()), grad.cpu().numpy()
+            return self._timed("slide", call)
 
         x, _, _ = box_bfgs(fg, _pack(thetas, w), lo, hi, gtol=self.slide_gtol, max_iter=max_iter)
         return _unpack(x)
@@ -226,8 +250,12 @@ class GPUSolver:
                 log(rec)
             break
         torch.cuda.synchronize()
+        seconds = time.perf_counter() - t0
+        stats = dict(self.stats)
+        stats["call_seconds"] = dict(self.call_seconds)
+        stats["host_seconds"] = seconds - sum(self.call_seconds.values())
         return {"thetas": thetas, "w": w, "C": self.criterion(thetas, w), "history": hist,
-                "seconds": time.perf_counter() - t0, "stats": dict(self.stats)}
+                "seconds": seconds, "stats": stats}
 
 
 def _pack(thetas, w):

@@ -67,16 +67,19 @@ def test_algorithmic_bytes_formulas():
     assert ab("not_a_pass") == 0.0
 
 
-@pytest.mark.parametrize("tag", ["cert_axis0", "cert_tail"])
+@pytest.mark.parametrize("tag", ["cert_axis0_tc", "cert_c2r_tc", "cert_axis0"])
 def test_traffic_record_matches_sources_or_is_ignored(tag):
+    """The committed DRAM bytes are used only for their workload, while the kernel sources
+    still match the digest they were captured on, and only for the tags they cover."""
     sys.path.insert(0, ROOT)
     import bench
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    got = bench.ncu_traffic(tag)
-    if rec["source_digest"] == bench.source_digest():
+    got = bench.ncu_traffic(tag, rec["workload"])
+    if rec["source_digest"] == bench.source_digest() and tag in rec["bytes_per_launch"]:
         assert got == rec["bytes_per_launch"][tag]
     else:
         assert got is None
+    assert bench.ncu_traffic(tag, "another_workload") is None
 
 
 def test_clock_summary_parses_samples_and_reasons(tmp_path):
