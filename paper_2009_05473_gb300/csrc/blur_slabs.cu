@@ -358,13 +358,22 @@ static sfw_status run_slab(Single ks, Grouped kg, const SlabPass& p, size_t smem
     return launch_check("k_slab");
 }
 
+template <int LL1, int LL2>
+static sfw_status run_slab_len(const SlabPass& p, size_t smem, cudaStream_t st, GroupArgs* g) {
+    if (p.mode == SLAB_HEAD) return run_slab(k_slab_head<LL1, LL2>, k_slab_head_g<LL1, LL2>, p, smem, st, g);
+    if (p.mode == SLAB_STORE)
+        return run_slab(k_slab_tail<LL1, LL2, SLAB_STORE>, k_slab_tail_g<LL1, LL2, SLAB_STORE>, p, smem, st, g);
+    return run_slab(k_slab_tail<LL1, LL2, SLAB_RESIDUAL>, k_slab_tail_g<LL1, LL2, SLAB_RESIDUAL>, p, smem, st, g);
+}
+
 size_t slab_smem(const SlabPass& p) {
     const SlabLayout q = slab_layout(p);
     const size_t bytes = sizeof(float2) * q.total;
     return bytes <= (size_t)220 * 1024 ? bytes : 0;
 }
 
-bool slab_specialised(const SlabPass& p) { return p.P1 == 80 && p.P2 == 96; }
+// Compile-time lengths: the 64^3 blur grid (80 x 96 on axes 1-2) and the 128^3 one (144 x 160).
+bool slab_specialised(const SlabPass& p) { return (p.P1 == 80 && p.P2 == 96) || (p.P1 == 144 && p.P2 == 160); }
 
 sfw_status launch_slab(const SlabPass& p0, cudaStream_t st, GroupArgs* g) {
     SlabPass p = p0;
@@ -381,15 +390,9 @@ sfw_status launch_slab(const SlabPass& p0, cudaStream_t st, GroupArgs* g) {
         SFW_TRY(twiddle_table(p.P2, mr2, &p.tw2));
         if (g_recorder) return g_recorder->add(p);
     }
-    const bool spec = slab_specialised(p);
-    if (p.mode == SLAB_HEAD)
-        return spec ? run_slab(k_slab_head<80, 96>, k_slab_head_g<80, 96>, p, smem, st, g)
-                    : run_slab(k_slab_head<0, 0>, k_slab_head_g<0, 0>, p, smem, st, g);
-    if (p.mode == SLAB_STORE)
-        return spec ? run_slab(k_slab_tail<80, 96, SLAB_STORE>, k_slab_tail_g<80, 96, SLAB_STORE>, p, smem, st, g)
-                    : run_slab(k_slab_tail<0, 0, SLAB_STORE>, k_slab_tail_g<0, 0, SLAB_STORE>, p, smem, st, g);
-    return spec ? run_slab(k_slab_tail<80, 96, SLAB_RESIDUAL>, k_slab_tail_g<80, 96, SLAB_RESIDUAL>, p, smem, st, g)
-                : run_slab(k_slab_tail<0, 0, SLAB_RESIDUAL>, k_slab_tail_g<0, 0, SLAB_RESIDUAL>, p, smem, st, g);
+    if (p.P1 == 80 && p.P2 == 96) return run_slab_len<80, 96>(p, smem, st, g);
+    if (p.P1 == 144 && p.P2 == 160) return run_slab_len<144, 160>(p, smem, st, g);
+    return run_slab_len<0, 0>(p, smem, st, g);
 }
 
 }  // namespace sfw

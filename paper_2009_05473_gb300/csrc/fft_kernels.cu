@@ -145,7 +145,7 @@ static sfw_status fit_factors(int L, int W, Factors* fac, const float2** tw, boo
 // ------------------------------------------------------------------ length dispatch
 
 // Lengths with compile-time specialisations (fft_len_*.cu); others run generic code.
-#define SFW_FFT_LENGTHS(X) X(64) X(80) X(96) X(128) X(160) X(192) X(256)
+#define SFW_FFT_LENGTHS(X) X(64) X(80) X(96) X(128) X(144) X(160) X(192) X(256)
 SFW_FFT_DECLARE(0)
 #define SFW_DECL(LL) SFW_FFT_DECLARE(LL)
 SFW_FFT_LENGTHS(SFW_DECL)

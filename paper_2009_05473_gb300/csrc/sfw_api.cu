@@ -2104,7 +2104,9 @@ std::string variant_key(const RecOp& o) {
             break;
         }
         case OP_SLAB:
-            snprintf(b, sizeof(b), "slab/%d/%d", o.slab.mode, slab_specialised(o.slab) ? 1 : 0);
+            // compile-time lengths are part of the variant; runtime-length slabs group together
+            snprintf(b, sizeof(b), "slab/%d/%d/%d", o.slab.mode, slab_specialised(o.slab) ? o.slab.P1 : 0,
+                     slab_specialised(o.slab) ? o.slab.P2 : 0);
             break;
         default:
             snprintf(b, sizeof(b), "op/%d", (int)o.kind);
