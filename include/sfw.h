@@ -301,6 +301,30 @@ sfw_status sfw_step(sfw_plan* plan, const float* y, const sfw_atoms* atoms, doub
                     double* loss_out, double* grad_out, float* residual_out, float* best_val,
                     int64_t* best_idx, void* stream, void* aux_stream);
 
+/* The same iteration with the precision configuration's seed: the sliding
+ * loss and gradient (Eq. 4; step 4 of Algorithm 1) and, for the same residual,
+ * the grid certificate's top-k voxels re-scored in FP32 (sfw_certificate_topk:
+ * the seed of step 1's local ascent).  One back-projection b = Phi^T r serves
+ * both the adjoint sums of the gradient and the re-score.
+ *   y, atoms, lambda (> 0), loss_out, grad_out (non-NULL), residual_out (or
+ *   NULL)  as for sfw_slide_loss_grad
+ *   topk, cand_theta, cand_grid, cand_eta, best_theta, best_eta  as for
+ *             sfw_certificate_topk
+ *   stream, aux_stream  as for sfw_step: given aux_stream, the grid
+ *             certificate and the top-k selection run on it once the residual
+ *             is ready, while the back-projection and the adjoint sums run on
+ *             stream; the re-score follows on aux_stream once those are done
+ *             (it shares their partial-sum scratch), and stream waits for it.
+ *             Three events of the plan order the branches: overlapping calls
+ *             on one plan are the caller's race.  Works under stream capture.
+ * Results equal those of sfw_slide_loss_grad followed by
+ * sfw_certificate_topk.  SFW_ERR_ARG on bad arguments or a plan without
+ * certificate grid; no graph of its own (callers capture it). */
+sfw_status sfw_step_topk(sfw_plan* plan, const float* y, const sfw_atoms* atoms, double lambda,
+                         double* loss_out, double* grad_out, float* residual_out, int topk,
+                         float* cand_theta, float* cand_grid, double* cand_eta, float* best_theta,
+                         double* best_eta, void* stream, void* aux_stream);
+
 /* Per-launch timing.  sfw_profile_start records a CUDA event pair on the
  * launching stream around each of the next max_launches kernels this library
  * launches (any thread) whose tag equals only_tag (host string; NULL = every

@@ -18,7 +18,7 @@ from . import _abi
 from ._abi import (SfwError, sfw_argmax, sfw_certificate_grid, sfw_certificate_topk,  # noqa: F401
                    sfw_eta_points, sfw_forward, sfw_gram,
                    sfw_launch_count, sfw_plan_create, sfw_plan_destroy, sfw_plan_query,
-                   sfw_plan_check, sfw_autotune, sfw_slide_loss_grad, sfw_step, sfw_version)
+                   sfw_plan_check, sfw_autotune, sfw_slide_loss_grad, sfw_step, sfw_step_topk, sfw_version)
 
 __all__ = ["Plan", "AtomSet", "Batch", "argmax", "launch_count", "SfwError", "build_library"]
 
@@ -260,6 +260,28 @@ class Plan:
                  _ptr(out["grad"]) if want_grad else 0, _ptr(out["residual"]), _ptr(out["best_val"]),
                  _ptr(out["best_idx"]), _stream_ptr(stream),
                  int(aux_stream.cuda_stream) if aux_stream is not None else 0)
+        return out
+
+    def step_topk(self, y, atoms: AtomSet, lam: float, topk: int = 64, aux_stream=None, stream=None,
+                  out=None):
+        """The same iteration with the precision configuration's seed (libsfw ``sfw_step_topk``):
+        the sliding loss, gradient and residual, and the grid certificate's topk voxels
+        re-scored in FP32, one back-projection serving both.  With ``aux_stream`` the
+        certificate overlaps the back-projection and the adjoint sums.  Returns dict(loss,
+        grad, residual, theta, grid, eta, best_theta, best_eta)."""
+        torch = _torch()
+        out = {} if out is None else out
+        shapes = {"loss": ((1,), torch.float64), "grad": ((6 * atoms.N,), torch.float64),
+                  "residual": (tuple(self.n), torch.float32), "theta": ((topk, 5), torch.float32),
+                  "grid": ((topk,), torch.float32), "eta": ((topk,), torch.float64),
+                  "best_theta": ((5,), torch.float32), "best_eta": ((1,), torch.float64)}
+        for k, (shape, dt) in shapes.items():
+            if out.get(k) is None or tuple(out[k].shape) != shape:
+                out[k] = torch.empty(shape, dtype=dt, device="cuda")
+        sfw_step_topk(self.handle, _ptr(y), atoms.abi(), lam, _ptr(out["loss"]), _ptr(out["grad"]),
+                      _ptr(out["residual"]), topk, _ptr(out["theta"]), _ptr(out["grid"]), _ptr(out["eta"]),
+                      _ptr(out["best_theta"]), _ptr(out["best_eta"]), _stream_ptr(stream),
+                      int(aux_stream.cuda_stream) if aux_stream is not None else 0)
         return out
 
 

@@ -26,7 +26,7 @@ SFW_ROUTE_DIRECT = 2
 EXPORTS = ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_autotune",
            "sfw_forward",
            "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
-           "sfw_slide_loss_grad", "sfw_step", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
+           "sfw_slide_loss_grad", "sfw_step", "sfw_step_topk", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
            "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect", "sfw_profile_stop", "sfw_last_error",
            "sfw_launch_count",
            "sfw_version")
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
     L.sfw_argmax_noalloc.argtypes = [vp, i64, i32, vp, vp, vp]
     L.sfw_slide_loss_grad.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp]
     L.sfw_step.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, vp, vp, vp, vp]
+    L.sfw_step_topk.argtypes = [vp, vp, ctypes.POINTER(Atoms), dbl, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.sfw_plan_check.argtypes = [vp]
     L.sfw_profile_start.argtypes = [i32, ctypes.c_char_p]
     L.sfw_gram.argtypes = [vp, ctypes.POINTER(Atoms), vp, vp, vp, vp]
@@ -103,7 +104,7 @@ def lib() -> ctypes.CDLL:
     for name in ("sfw_plan_create", "sfw_plan_destroy", "sfw_plan_query", "sfw_plan_check", "sfw_autotune",
                  "sfw_forward",
                  "sfw_certificate_grid", "sfw_certificate_topk", "sfw_eta_points", "sfw_argmax", "sfw_argmax_noalloc",
-                 "sfw_slide_loss_grad", "sfw_step", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
+                 "sfw_slide_loss_grad", "sfw_step", "sfw_step_topk", "sfw_gram", "sfw_batch_create", "sfw_batch_destroy",
            "sfw_batch_query", "sfw_batch_step", "sfw_batch_autotune", "sfw_profile_start", "sfw_profile_collect",
                  "sfw_profile_stop"):
         getattr(L, name).restype = ctypes.c_int
@@ -194,6 +195,14 @@ def sfw_step(plan: int, y: int, atoms: Atoms, lam: float, loss_out: int, grad_ou
              residual_out: int, best_val: int, best_idx: int, stream: int, aux_stream: int) -> None:
     check(lib().sfw_step(plan, y, ctypes.byref(atoms), float(lam), loss_out, grad_out, residual_out,
                          best_val, best_idx, stream, aux_stream), "sfw_step")
+
+
+def sfw_step_topk(plan: int, y: int, atoms: Atoms, lam: float, loss_out: int, grad_out: int,
+                  residual_out: int, topk: int, cand_theta: int, cand_grid: int, cand_eta: int,
+                  best_theta: int, best_eta: int, stream: int, aux_stream: int) -> None:
+    check(lib().sfw_step_topk(plan, y, ctypes.byref(atoms), float(lam), loss_out, grad_out, residual_out,
+                              int(topk), cand_theta, cand_grid, cand_eta, best_theta, best_eta, stream,
+                              aux_stream), "sfw_step_topk")
 
 
 def sfw_gram(plan: int, atoms: Atoms, y: int, G_out: int, c_out: int, stream: int) -> None:

@@ -635,6 +635,7 @@ struct sfw_plan {
     float* unit_slot;             // one atom (m0, m1, m2, sigma, d, w = 1)
     int num_sms;
     cudaEvent_t ev_fork, ev_join;  // sfw_step: residual ready / certificate done
+    cudaEvent_t ev_grad;           // sfw_step_topk: back-projection and adjoint sums done
     cudaEvent_t ev_graph;          // sfw_step: recorded after each launch of the cached graph
     cudaStream_t cap_own, aux_own; // sfw_step captures its graph on these (origin, branch)
     // certificate tail by TMA: tensor map of the line-group-major axis-0 output (opaque)
@@ -716,6 +717,8 @@ static void plan_free(sfw_plan* p) {
     p->aux_own = p->cap_own = nullptr;
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->ev_grad) cudaEventDestroy(p->ev_grad);
+    p->ev_grad = nullptr;
     if (p->ev_graph) cudaEventDestroy(p->ev_graph);
     p->ev_fork = p->ev_join = p->ev_graph = nullptr;
     if (p->gram_cols) cudaFree(p->gram_cols);
@@ -1258,6 +1261,7 @@ sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out) {
         if ((s = plan_alloc_t(p, &p->red_scratch, (size_t)p->red_scratch_len))) break;
         if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&p->ev_graph, cudaEventDisableTiming) != cudaSuccess ||
             cudaStreamCreateWithFlags(&p->aux_own, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&p->cap_own, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1846,23 +1850,77 @@ sfw_status sfw_gram(sfw_plan* p, const sfw_atoms* atoms, const float* y, double*
     return launch_gram(p->gram_cols, y, N, p->V, G_out, c_out, st);
 }
 
-sfw_status sfw_certificate_topk(sfw_plan* p, const float* residual, double lambda, int topk,
-                                float* cand_theta, float* cand_grid, double* cand_eta,
-                                float* best_theta, double* best_eta, void* stream) {
-    clear_error();
+static sfw_status topk_rescore(sfw_plan* p, double lambda, int topk, float* cand_theta, float* cand_grid,
+                               double* cand_eta, float* best_theta, double* best_eta, cudaStream_t st);
+
+static sfw_status topk_args(const sfw_plan* p, const float* residual, double lambda, int topk) {
     if (!p || !residual) return fail(SFW_ERR_ARG, "plan and residual must be non-NULL");
     if (p->K == 0) return fail(SFW_ERR_ARG, "plan has no certificate grid");
     if (topk < 1 || topk > 64 || topk > p->V) return fail(SFW_ERR_ARG, "topk must be in [1, min(64, V)]");
     if (!(lambda > 0.0) || !isfinite(lambda)) return fail(SFW_ERR_ARG, "lambda must be finite and > 0");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // 1. grid certificate -> per-voxel max over k and its k
-    SFW_TRY(sfw_certificate_grid(p, residual, lambda, nullptr, p->vmax, p->vargk, nullptr, nullptr, stream));
-    // 2. the topk voxels by their grid maximum
+    return SFW_OK;
+}
+
+// Steps 1-3 of the top-k seed without the re-score: the grid certificate's per-voxel maximum
+// over k and its k, the topk voxels by that maximum, their parameter rows.
+static sfw_status topk_select(sfw_plan* p, const float* residual, double lambda, int topk, cudaStream_t st) {
+    SFW_TRY(certificate_impl(p, residual, lambda, nullptr, p->vmax, p->vargk, nullptr, nullptr, st));
     SFW_TRY(launch_topk(p->vmax, p->V, topk, p->red_scratch, p->red_scratch_len, p->cand_val,
                         p->cand_idx, st));
-    // 3. parameter rows (voxel position, sigma_k, d_k) and their FP32 re-score
-    SFW_TRY(launch_candidate_theta(p->cand_idx, p->vargk, p->grid_sd, topk, p->n, p->cand_theta, st));
+    return launch_candidate_theta(p->cand_idx, p->vargk, p->grid_sd, topk, p->n, p->cand_theta, st);
+}
+
+sfw_status sfw_certificate_topk(sfw_plan* p, const float* residual, double lambda, int topk,
+                                float* cand_theta, float* cand_grid, double* cand_eta,
+                                float* best_theta, double* best_eta, void* stream) {
+    clear_error();
+    SFW_TRY(topk_args(p, residual, lambda, topk));
+    if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the argmax-only certificate");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // 1.-3. grid certificate -> per-voxel max over k, the topk voxels, their parameter rows
+    SFW_TRY(topk_select(p, residual, lambda, topk, st));
+    // 4. their FP32 re-score against b = Phi^T r, and the best
     SFW_TRY(plan_transpose(p, residual, p->bE, st));
+    return topk_rescore(p, lambda, topk, cand_theta, cand_grid, cand_eta, best_theta, best_eta, st);
+}
+
+sfw_status sfw_step_topk(sfw_plan* p, const float* y, const sfw_atoms* atoms, double lambda,
+                         double* loss_out, double* grad_out, float* residual_out, int topk,
+                         float* cand_theta, float* cand_grid, double* cand_eta, float* best_theta,
+                         double* best_eta, void* stream, void* aux_stream) {
+    clear_error();
+    SFW_TRY(slide_args(p, y, atoms, lambda, loss_out));
+    if (!grad_out) return fail(SFW_ERR_ARG, "grad_out must be non-NULL");
+    if (g_recorder) return fail(SFW_ERR_UNSUPPORTED, "batches record the single calls");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t aux = aux_stream ? static_cast<cudaStream_t>(aux_stream) : st;
+    float* r = residual_out ? residual_out : p->r;
+    SFW_TRY(topk_args(p, r, lambda, topk));
+    SFW_TRY(residual_and_loss(p, y, atoms, lambda, loss_out, r, st));
+    if (aux != st) {
+        SFW_CUDA(cudaEventRecord(p->ev_fork, st));
+        SFW_CUDA(cudaStreamWaitEvent(aux, p->ev_fork, 0));
+    }
+    // the certificate and the selection on aux; b = Phi^T r and the adjoint sums on st
+    SFW_TRY(topk_select(p, r, lambda, topk, aux));
+    SFW_TRY(loss_gradient(p, atoms, lambda, r, grad_out, st));
+    if (aux != st) {
+        SFW_CUDA(cudaEventRecord(p->ev_grad, st));
+        SFW_CUDA(cudaStreamWaitEvent(aux, p->ev_grad, 0));
+    }
+    // the re-score reads b and the adjoint sums' scratch: after both branches
+    SFW_TRY(topk_rescore(p, lambda, topk, cand_theta, cand_grid, cand_eta, best_theta, best_eta, aux));
+    if (aux != st) {
+        SFW_CUDA(cudaEventRecord(p->ev_join, aux));
+        SFW_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
+    }
+    return SFW_OK;
+}
+
+// The FP32 re-score of the topk candidate rows against b = Phi^T r (already in p->bE) and the
+// best of them.
+static sfw_status topk_rescore(sfw_plan* p, double lambda, int topk, float* cand_theta, float* cand_grid,
+                               double* cand_eta, float* best_theta, double* best_eta, cudaStream_t st) {
     AtomsDev pts;
     pts.N = topk;
     pts.m = p->cand_theta;

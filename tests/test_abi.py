@@ -60,6 +60,9 @@ def test_host_argument_checks_need_no_gpu(built):
     assert e.value.status == 1
     with pytest.raises(_abi.SfwError):
         _abi.sfw_slide_loss_grad(0, 0, _abi.Atoms(), 1.0, 0, 0, 0, 0)
+    with pytest.raises(_abi.SfwError) as e:
+        _abi.sfw_step_topk(0, 0, _abi.Atoms(), 1.0, 0, 0, 0, 64, 0, 0, 0, 0, 0, 0, 0)   # NULL plan
+    assert e.value.status == 1
     # an unknown route is refused before any device work
     import numpy as np
     psf = np.full((3, 3, 3), 1.0 / 27, np.float32)

@@ -272,6 +272,55 @@ def test_step_equals_separate_calls(sfw, oracle_mod, vol64, which):
     plan.check()   # no bounded device wait (TMA slab copies) ran out
 
 
+@pytest.mark.parametrize("which", ["vol64_bf16", "tc_tail"])
+def test_step_topk_equals_separate_calls(sfw, oracle_mod, vol64, which):
+    """sfw_step_topk (sliding loss, gradient and residual, and the grid certificate's top-64
+    voxels re-scored in FP32, the certificate on an auxiliary stream, one back-projection for
+    both) gives bit-identical outputs to sfw_slide_loss_grad followed by
+    sfw_certificate_topk: with and without the auxiliary stream, and replayed from a captured
+    graph.  The second case takes the per-axis certificate tail on the tensor cores."""
+    import torch
+    if which == "vol64_bf16":
+        vol, y, lam, _, (m, s, d, w), yd = vol64
+    else:
+        vol = sfw_inputs.make_volume("tc", (70, 18, 22), (3, 2, 3), (1.2, 1.3, 1.7), 3, seed=21,
+                                     grid_sigmas=tuple(np.linspace(1, 3, 8)), grid_ds=(1.5, 2.0, 2.5, 3.0),
+                                     min_sep=2.0)
+        y = _f32(oracle_mod.observe(vol, fft=True))
+        lam = oracle_mod.lambda_rule(vol.n, vol.R, vol.psf, y, vol.grid_kernels(), fft=True)
+        m, s, d, w = (_f32(a) for a in _estimate(vol))
+        yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    plan = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, precision="bf16")
+    atoms = sfw.AtomSet.from_numpy(m, s, d, w)
+    loss, grad, res = plan.slide_loss_grad(yd, atoms, lam, want_residual=True)
+    top = plan.certificate_topk(res, lam, 64)
+    ref = {"loss": loss.clone(), "grad": grad.clone(), "residual": res.clone()}
+    ref.update({k: v.clone() for k, v in top.items()})
+
+    def same(out):
+        for k, v in ref.items():
+            assert torch.equal(out[k], v), k
+
+    aux = torch.cuda.Stream()
+    same(plan.step_topk(yd, atoms, lam, 64, aux_stream=aux))
+    same(plan.step_topk(yd, atoms, lam, 64))
+    out = plan.step_topk(yd, atoms, lam, 64, aux_stream=aux)
+    torch.cuda.synchronize()
+    for v in out.values():
+        v.zero_()
+    cap = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            plan.step_topk(yd, atoms, lam, 64, aux_stream=aux, out=out)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    same(out)
+    plan.check()
+    plan.close()
+
+
 @pytest.mark.parametrize("n", [(16, 61, 32), (10, 32, 62)])
 def test_certificate_slabs_ragged(sfw, oracle_mod, n):
     """The slab head/tail kernels on shapes whose certificate grid is 128 x 64 and 64 x 128 on
