@@ -94,22 +94,23 @@ __host__ __device__ inline int tc_tile_lines(int Np) { return 128 / Np; }
 // Dynamic shared memory (byte offsets from a 1024-aligned base; every region a multiple of
 // 1024 bytes, as the 128-byte swizzle wants):
 //   a      A, 128 rows x 2 Kp                       (resident)
-//   b[3]   B' of a block: Re and Im slices, 128 rows x 64 each (32 KB)
+//   t[3]   the table pieces of a block: LT lines x Np kernels x 64 points (16 KB, bulk copies)
+//   b[2]   B' of a block: Re and Im slices, 128 rows x 64 each (32 KB)
 //   xs[2]  X of a tile: LT lines x Kp points, FP32 complex (one tile ahead)
-// The table pieces go from global memory (L2) straight to registers: keeping them out of
-// shared memory leaves its bandwidth to the tensor core's operand reads.
 struct TcSmem {
-    uint32_t a, b[3], xs[2], total;
+    uint32_t a, t[3], b[2], xs[2], total;
 };
 
 __host__ __device__ inline TcSmem tc_smem_layout(int Kp, int Np) {
     TcSmem s;
     const uint32_t abytes = 128u * 2u * (uint32_t)Kp * 2u;
+    const uint32_t tbytes = 128u * 64u * 2u;
     const uint32_t bbytes = 2u * 128u * 64u * 2u;
     const uint32_t xbytes = ((uint32_t)tc_tile_lines(Np) * (uint32_t)Kp * 8u + 1023u) & ~1023u;
     s.a = 0;
-    for (int i = 0; i < 3; ++i) s.b[i] = abytes + (uint32_t)i * bbytes;
-    s.xs[0] = abytes + 3u * bbytes;
+    for (int i = 0; i < 3; ++i) s.t[i] = abytes + (uint32_t)i * tbytes;
+    for (int i = 0; i < 2; ++i) s.b[i] = abytes + 3u * tbytes + (uint32_t)i * bbytes;
+    s.xs[0] = abytes + 3u * tbytes + 2u * bbytes;
     s.xs[1] = s.xs[0] + xbytes;
     s.total = s.xs[1] + xbytes + 1024u;   // + alignment slack of the base
     return s;
@@ -117,7 +118,9 @@ __host__ __device__ inline TcSmem tc_smem_layout(int Kp, int Np) {
 
 constexpr int kTcFormWarps = 8;                   // warps 0-7: B' of every block
 constexpr int kTcEpiWarps = 4;                    // warps 8-11: results (TMEM lane quadrant = warp % 4)
-constexpr int kTcThreadsWs = 32 * (kTcFormWarps + kTcEpiWarps + 1);   // + warp 12: the MMAs
+constexpr int kTcMmaWarp = kTcFormWarps + kTcEpiWarps;                 // warp 12: the MMAs
+constexpr int kTcProdWarp = kTcMmaWarp + 1;                            // warp 13: the table copies
+constexpr int kTcThreadsWs = 32 * (kTcFormWarps + kTcEpiWarps + 2);
 constexpr int kTcFormThreads = 32 * kTcFormWarps;
 
 // One CTA per (half of the output rows, share of the tiles).  A = the real form of W's 64
@@ -127,12 +130,14 @@ constexpr int kTcFormThreads = 32 * kTcFormWarps;
 // For every tile and block of 64 points, B'_re = T (.) Re X and B'_im = T (.) Im X (128
 // columns = LT lines x Np kernels); D (+)= A_re-block B'_re^T + A_im-block B'_im^T, so that
 // after the last block D = [Re U_k; Im U_k] for the tile's lines, in tensor memory.
-// Warp roles: warps 0-7 build B' (three stages; the table chunks read from global memory into
-// registers ahead of the stage wait, X staged a tile ahead); warps 8-11 write the results of a
+// Warp roles: one lane of warp 13 bulk-copies the table pieces of every block into a ring of
+// three stages (a line's piece of a 64-point block is 4 KB contiguous at Np = 32); warps 0-7
+// build B' from them (two stages; X staged a tile ahead); warps 8-11 write the results of a
 // tile while the next one accumulates (two tensor-memory buffers); one lane of warp 12 issues
-// the MMAs.  Hand-offs go through mbarriers: b_full (B' built, 8 arrivals), done (MMAs of a
-// block finished, tcgen05.commit), acc_full / acc_empty (a tile's results ready / read, 4
-// arrivals).  Every wait is bounded; a wait that runs out sets p.err.
+// the MMAs.  Hand-offs go through mbarriers: t_full / t_empty (table stage landed / read, 8
+// arrivals), b_full (B' built, 8 arrivals), done (MMAs of a block finished, tcgen05.commit),
+// acc_full / acc_empty (a tile's results ready / read, 4 arrivals).  Every wait is bounded; a
+// wait that runs out sets p.err.
 template <int LT>
 __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     extern __shared__ unsigned char tc_smem_raw[];
@@ -141,7 +146,8 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     const int Kp = p.Kp, Np = p.Np, P0 = p.P0;
     const int nb = Kp / 64;
     const TcSmem L = tc_smem_layout(Kp, Np);
-    __shared__ __align__(8) unsigned long long s_bfull[3], s_done[3], s_accf[2], s_acce[2], s_abar;
+    __shared__ __align__(8) unsigned long long s_tfull[3], s_tempty[3], s_bfull[2], s_done[2], s_accf[2],
+        s_acce[2], s_abar;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -156,10 +162,12 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
 
     if (tid == 0) {
         for (int i = 0; i < 3; ++i) {
-            tc::mbar_init(tc::smem_addr(&s_bfull[i]), kTcFormWarps);
-            tc::mbar_init(tc::smem_addr(&s_done[i]), 1);
+            tc::mbar_init(tc::smem_addr(&s_tfull[i]), 1);
+            tc::mbar_init(tc::smem_addr(&s_tempty[i]), kTcFormWarps);
         }
         for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(tc::smem_addr(&s_bfull[i]), kTcFormWarps);
+            tc::mbar_init(tc::smem_addr(&s_done[i]), 1);
             tc::mbar_init(tc::smem_addr(&s_accf[i]), 1);
             tc::mbar_init(tc::smem_addr(&s_acce[i]), kTcEpiWarps);
         }
@@ -173,7 +181,38 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
 
-    if (warp == kTcFormWarps + kTcEpiWarps) {
+    if (warp == kTcProdWarp) {
+        // ---------------- table pieces of every block: LT bulk copies (one per line)
+        if (lane == 0) {
+            const uint32_t piece = (uint32_t)Np * 64u * 2u;
+            int ts = 0;
+            uint32_t tph = 0;
+            bool wrapped = false;
+            for (long long u = 0; u < my_tiles && !s_abort; ++u) {
+                const long long l0 = tile_l0(u);
+                for (int b = 0; b < nb; ++b) {
+                    // the stage is free once the formation warps have read its previous block
+                    if (wrapped && !tc::mbar_wait(tc::smem_addr(&s_tempty[ts]), tph ^ 1u)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    const uint32_t bar = tc::smem_addr(&s_tfull[ts]);
+                    tc::mbar_expect_tx(bar, piece * (uint32_t)LT);
+                    for (int j = 0; j < LT; ++j) {
+                        const long long l = min(l0 + j, p.nl - 1);   // padding lines copy a real block
+                        const __nv_bfloat16* src = p.Tb + (size_t)l * (size_t)Np * (size_t)Kp + (size_t)b * 64u * Np;
+                        tc::bulk_g2s(tc::smem_addr(base + L.t[ts] + (uint32_t)j * piece), src, piece, bar);
+                    }
+                    if (++ts == 3) {
+                        ts = 0;
+                        tph ^= 1u;
+                        wrapped = true;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == kTcMmaWarp) {
         // ---------------- MMA lane
         if (lane == 0) {
             const uint32_t abytes = 128u * 2u * (uint32_t)Kp * 2u;
@@ -183,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
             if (!tc::mbar_wait(tc::smem_addr(&s_abar), 0)) s_abort = 1;
             // This one thread's instruction latency paces the MMAs: descriptors are built once
             // and advanced by adding to their address field (16-byte units), the B' stage ring
-            // (3 stages) is tracked without divisions, a block's 8 MMAs are unrolled.
+            // (2 stages) is tracked without divisions, a block's 8 MMAs are unrolled.
             const uint64_t dA0 = tc::desc_kmajor_sw128(tc::smem_addr(base + L.a));
             // the B' stages lie 2 x 16 KB apart (Re and Im slices)
             const uint64_t dB0 = tc::desc_kmajor_sw128(tc::smem_addr(base + L.b[0]));
@@ -217,7 +256,7 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                     tc::mma_bf16(d, aim + 2 * kKStep, bim + 2 * kKStep, idesc, 1u);
                     tc::mma_bf16(d, aim + 3 * kKStep, bim + 3 * kKStep, idesc, 1u);
                     tc::mma_commit(tc::smem_addr(&s_done[s]));
-                    if (++s == 3) {
+                    if (++s == 2) {
                         s = 0;
                         ph ^= 1u;
                     }
@@ -242,25 +281,10 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
         };
         if (my_tiles > 0) stage_x(0);
         constexpr int PER = 128 * 8 / kTcFormThreads;     // items (16-byte chunks) per thread and block
-        int s = 0;          // B' stage of the next block (ring of 3) and its use count
-        uint32_t uses = 0;
+        const uint32_t piece = (uint32_t)Np * 64u * 2u;
         const int lnp = __ffs(Np) - 1;                    // Np is a power of two
-        // this thread's table chunks of block b of tile u, from global memory into registers;
-        // the next block's are loaded while the current one is formed
-        auto load_t = [&](long long u, int b, uint4 (&tv)[PER]) {
-            const long long l0 = tile_l0(u);
-#pragma unroll
-            for (int r = 0; r < PER; ++r) {
-                const int e = tid + r * kTcFormThreads;
-                const int col = e & 127, c = e >> 7;
-                const int j = col >> lnp, n = col - (j << lnp);
-                const long long l = min(l0 + j, p.nl - 1);   // padding lines read a real block
-                const unsigned char* blk = reinterpret_cast<const unsigned char*>(p.Tb + (size_t)l * (size_t)Np * (size_t)Kp);
-                tv[r] = __ldg(reinterpret_cast<const uint4*>(blk + tc::kmajor_offset(n, 64 * b + 8 * c, Np)));
-            }
-        };
-        uint4 tv[PER], tvn[PER];
-        if (my_tiles > 0) load_t(0, 0, tv);
+        int s = 0, ts = 0;  // B' stage (ring of 2) and table stage (ring of 3) of the next block
+        uint32_t uses = 0, tph = 0;
         for (long long u = 0; u < my_tiles; ++u) {
             tc::cp_async_wait_all();
             // all formation threads stop together (a barrier with a missing thread never ends)
@@ -268,19 +292,22 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
             if (u + 1 < my_tiles) stage_x(u + 1);
             const float2* xs = reinterpret_cast<const float2*>(base + L.xs[u & 1]);
             for (int b = 0; b < nb; ++b) {
-                if (b + 1 < nb) load_t(u, b + 1, tvn);
-                else if (u + 1 < my_tiles) load_t(u + 1, 0, tvn);
-                // B'[s] is free once the MMAs of its previous use (block q - 3) are done
+                // the block's table pieces have landed; B'[s] is free once the MMAs of its
+                // previous use (block q - 2) are done
+                if (!tc::mbar_wait(tc::smem_addr(&s_tfull[ts]), tph)) s_abort = 1;
                 if (uses > 0 && !tc::mbar_wait(tc::smem_addr(&s_done[s]), (uses - 1u) & 1u)) s_abort = 1;
                 if (s_abort) break;
+                const unsigned char* Ts = base + L.t[ts];
                 unsigned char* Bre = base + L.b[s];
                 unsigned char* Bim = Bre + 128u * 64u * 2u;
 #pragma unroll
                 for (int r = 0; r < PER; ++r) {
                     const int e = tid + r * kTcFormThreads;
                     const int col = e & 127, c = e >> 7;          // column of B', 8-point chunk of the block
-                    const int j = col >> lnp;
-                    const uint32_t tw[4] = {tv[r].x, tv[r].y, tv[r].z, tv[r].w};
+                    const int j = col >> lnp, n = col - (j << lnp);
+                    const uint4 tvr = *reinterpret_cast<const uint4*>(Ts + (uint32_t)j * piece +
+                                                                      tc::kmajor_offset(n, 8 * c, Np));
+                    const uint32_t tw[4] = {tvr.x, tvr.y, tvr.z, tvr.w};
                     const float4* x4 = reinterpret_cast<const float4*>(xs + j * Kp + 64 * b + 8 * c);
                     uint32_t re[4], imv[4];
 #pragma unroll
@@ -296,12 +323,17 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
                 }
                 tc::fence_async_smem();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(tc::smem_addr(&s_bfull[s]));
-#pragma unroll
-                for (int r = 0; r < PER; ++r) tv[r] = tvn[r];
-                if (++s == 3) {
+                if (lane == 0) {
+                    tc::mbar_arrive(tc::smem_addr(&s_bfull[s]));
+                    tc::mbar_arrive(tc::smem_addr(&s_tempty[ts]));
+                }
+                if (++s == 2) {
                     s = 0;
                     ++uses;
+                }
+                if (++ts == 3) {
+                    ts = 0;
+                    tph ^= 1u;
                 }
             }
         }
@@ -369,7 +401,8 @@ __global__ void __launch_bounds__(kTcThreadsWs, 1) k_axis0_tc(Axis0TcPass p) {
         // finish (bounded) before the tensor memory is released
         if (tid == 0) {
             atomicExch(p.err, 1);
-            for (int i = 0; i < 3; ++i) tc::mbar_wait(tc::smem_addr(&s_done[i]), 0, 1 << 16);
+            for (int i = 0; i < 2; ++i) tc::mbar_wait(tc::smem_addr(&s_done[i]), 0, 1 << 16);
+            for (int i = 0; i < 3; ++i) tc::mbar_wait(tc::smem_addr(&s_tfull[i]), 0, 1 << 16);
             tc::mbar_wait(tc::smem_addr(&s_abar), 0, 1 << 16);
         }
         __syncthreads();
