@@ -111,13 +111,18 @@ def test_slide_loss_grad_matches_oracle(sfw, oracle_mod, torch_mod, case):
     loss, grad, res = plan.slide_loss_grad(torch_mod.tensor(y32, dtype=torch_mod.float32, device="cuda"),
                                            atoms, lam, want_residual=True)
     assert abs(loss.item() - C) <= RTOL * abs(C)
-    assert _rel_inf(res.cpu().numpy(), r) <= RTOL * 10
+    assert _rel_inf(res.cpu().numpy(), r) <= 1e-5
     gg = grad.cpu().numpy()
-    assert _rel_inf(gg, g) <= 1e-4
-    # each block of 6 (m, sigma, d, w) on its own scale
     Nn = w.size
-    for blk in (slice(0, 3 * Nn), slice(3 * Nn, 4 * Nn), slice(4 * Nn, 5 * Nn), slice(5 * Nn, 6 * Nn)):
-        assert _rel_inf(gg[blk], g[blk]) <= 1e-3
+    blocks = (slice(0, 3 * Nn), slice(3 * Nn, 4 * Nn), slice(4 * Nn, 5 * Nn), slice(5 * Nn, 6 * Nn))
+    print(f"\n[slide {n}] loss {abs(loss.item() - C) / abs(C):.1e}, residual {_rel_inf(res.cpu().numpy(), r):.1e}, "
+          f"gradient {_rel_inf(gg, g):.1e} (m, sigma, d, w: "
+          + ", ".join(f"{_rel_inf(gg[b], g[b]):.1e}" for b in blocks) + ")")
+    # the FP32 path's 1e-5 relative bar, overall and for each block of (m, sigma, d, w) on its
+    # own scale (measured: at most 2.7e-6 on these cases)
+    assert _rel_inf(gg, g) <= 1e-5
+    for blk in blocks:
+        assert _rel_inf(gg[blk], g[blk]) <= 1e-5
 
 
 def test_eta_points_match_oracle(sfw, oracle_mod, torch_mod):
