@@ -67,6 +67,8 @@ TC_CASES = [
     # odd line count x odd half-spectrum length: every other kernel's spectra start off the
     # 16-byte grid, and the last 128-line tile has empty quarters
     ((21, 15, 18), (2, 2, 3), (1.0, 2.0, 3.0), (1.5, 2.5)),                     # K = 6 -> 16
+    # one line per 128-column tile (kernels padded to 128)
+    ((18, 20, 24), (2, 2, 3), tuple(np.linspace(1, 3, 10)), tuple(np.linspace(1.3, 2.9, 10))),  # K = 100 -> 128
 ]
 
 
@@ -136,3 +138,21 @@ def test_tensor_core_engine_choice_by_timing(sfw, oracle_mod, tmp_path):
     assert np.max(np.abs(eta - ref)) <= 1e-2 * np.max(np.abs(ref))
     pb.close()
     again.close()
+
+
+def test_more_kernels_than_tensor_core_tiles_fall_back_to_fft(sfw, oracle_mod):
+    """K = 130 exceeds the 128 kernels of a tensor-core tile: the bf16 plan keeps the FFT
+    arithmetic for the certificate, within the bf16 bar of the oracle."""
+    import torch
+    vol = sfw_inputs.make_volume("tc", (16, 18, 20), (2, 2, 3), (1.2, 1.3, 1.7), 2, seed=22,
+                                 grid_sigmas=tuple(np.linspace(1, 3, 13)), grid_ds=tuple(np.linspace(1.3, 2.9, 10)),
+                                 min_sep=2.0)
+    y = np.asarray(oracle_mod.observe(vol, fft=True), np.float32)
+    kernels = vol.grid_kernels()
+    assert len(kernels) == 130
+    pb = sfw.Plan(vol.n, vol.R, vol.psf, vol.grid_sigmas, vol.grid_ds, precision="bf16")
+    assert not pb.info["tensor_cores"]
+    eta = pb.certificate(torch.tensor(y, device="cuda"), 1.0, want_eta=True)["eta"].cpu().numpy()
+    ref = oracle_mod.eta_grid_fft(vol.n, vol.R, vol.psf, y.astype(np.float64), 1.0, kernels)
+    assert np.max(np.abs(eta - ref)) <= 1e-2 * np.max(np.abs(ref))
+    pb.close()
