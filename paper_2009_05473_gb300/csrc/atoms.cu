@@ -185,6 +185,7 @@ __device__ __forceinline__ void warp_chunk_sums(int n, int chunks, const double*
 // partial sums; the last chunk-block of the atom to finish turns the atom's
 // partials into its gradient entries (mode 0) or its certificate and
 // certificate gradient (mode 1), then re-arms the atom's counter.
+template <bool ETA_ONLY>
 __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1, int E2, int R0,
                                                int R1, int R2, float log_inv_eps2,
                                                const float* __restrict__ b, double* partials, int n,
@@ -220,6 +221,7 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
         const float g = exp2f(-kLog2e * u);
         const float gb = g * bt;
         sg_b += gb;
+        if constexpr (ETA_ONLY) return;   // eta alone: no derivative sums
         if (r2 > 0.f) {
             // dg/dm_a = -g d u (m_a - x_a) / rho^2
             const float cm = -gb * dd * u / r2;
@@ -311,11 +313,12 @@ __device__ __forceinline__ void atom_grad_body(const AtomsDev& a, int E0, int E1
     }
 }
 
+template <bool ETA_ONLY>
 __global__ void __launch_bounds__(kGradThreads, 3)
 k_atom_grad(AtomsDev a, int E0, int E1, int E2, int R0, int R1, int R2, float log_inv_eps2,
             const float* __restrict__ b, double* partials, AdjFin fin) {
-    atom_grad_body(a, E0, E1, E2, R0, R1, R2, log_inv_eps2, b, partials, blockIdx.x, blockIdx.y,
-                   gridDim.y, fin);
+    atom_grad_body<ETA_ONLY>(a, E0, E1, E2, R0, R1, R2, log_inv_eps2, b, partials, blockIdx.x, blockIdx.y,
+                             gridDim.y, fin);
 }
 
 int grad_tiles(const GradOp& op, int* nbx) {
@@ -333,8 +336,8 @@ k_atom_grad_g(const GradOp* __restrict__ ops, const int* __restrict__ start, con
         const GradOp& o = ops[q];
         const int local = t - start[q];
         const float lie2 = log2f(2.0f * logf(1.0f / o.eps));
-        atom_grad_body(o.a, o.E[0], o.E[1], o.E[2], o.R[0], o.R[1], o.R[2], lie2, o.b, o.partials,
-                       local / kGradChunks, local % kGradChunks, kGradChunks, o.fin);
+        atom_grad_body<false>(o.a, o.E[0], o.E[1], o.E[2], o.R[0], o.R[1], o.R[2], lie2, o.b, o.partials,
+                              local / kGradChunks, local % kGradChunks, kGradChunks, o.fin);
         __syncthreads();
     }
 }
@@ -364,7 +367,11 @@ static sfw_status adjoint(const AtomsDev& a, const int E[3], const int R[3], flo
     }
     const float log_inv_eps2 = log2f(2.0f * logf(1.0f / eps));
     dim3 grid(a.N, kGradChunks);
-    SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, b, partials, fin));
+    // eta without its gradient (the FP32 re-score of grid candidates): the value sums alone
+    if (fin.mode == 1 && !fin.grad)
+        SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<true><<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, b, partials, fin));
+    else
+        SFW_LAUNCH(st, "k_atom_grad", k_atom_grad<false><<<grid, kGradThreads, 0, st>>>(a, E[0], E[1], E[2], R[0], R[1], R[2], log_inv_eps2, b, partials, fin));
     return launch_check("k_atom_grad");
 }
 
