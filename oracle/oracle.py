@@ -25,7 +25,7 @@ with ctypes.  This file adds, in numpy, float64:
 
 Readings of points the paper leaves open (each listed in the design notes):
 domain box D = {m_a in [0, n_a-1], sigma in [0.75, 4], d in [1.25, 3], w >= 0};
-the stopping test is max eta <= 1 + tau with tau = 1e-4; the prune threshold
+the stopping test is max eta <= 1 + tau with tau = 1e-3; the prune threshold
 is w <= 1e-10 max w; lambda = 0.05 max over the grid of Phi^T y.
 """
 
