@@ -54,7 +54,7 @@ PRUNE_REL = 1e-10
 __all__ = [
     "build_oracle", "lib", "num_threads", "render", "forward_conv", "backproject", "eta_points",
     "atom_grad", "argmax", "forward", "forward_fft", "backproject_fft", "observe", "criterion",
-    "loss_and_grad", "eta_grid", "eta_grid_fft", "grid_argmax", "lambda_rule", "nnls_gram",
+    "loss_and_grad", "grid_thetas", "eta_grid", "eta_grid_fft", "grid_argmax", "lambda_rule", "nnls_gram",
     "lasso_weights", "atom_columns", "projected_bfgs", "sfw", "bsfw", "domain_bounds", "pack_params",
     "unpack_params", "SIGMA_BOUNDS", "D_BOUNDS", "TAU",
 ]

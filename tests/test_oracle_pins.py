@@ -245,6 +245,39 @@ def test_eta_of_unit_atom_is_its_own_energy(oracle_mod):
     assert e == pytest.approx(float(np.sum(a * a)) / 2.0, rel=1e-12)
 
 
+def test_grid_thetas_flat_order(oracle_mod):
+    """Grid candidates (Algorithm 1 step 1) in flat order k*V + lin(m): row i is the voxel
+    numpy's unravel_index gives for i mod V and kernel i div V."""
+    n = (3, 4, 5)
+    kernels = [(1.0, 2.0), (2.5, 1.5), (1.7, 2.9)]
+    G = oracle_mod.grid_thetas(n, kernels)
+    V = int(np.prod(n))
+    assert G.shape == (len(kernels) * V, 5)
+    for i in (0, 1, 4, 5, 19, 20, V - 1, V, V + 37, 2 * V + 58, 3 * V - 1):
+        k, v = divmod(i, V)
+        m = np.unravel_index(v, n)
+        np.testing.assert_array_equal(G[i], [m[0], m[1], m[2], kernels[k][0], kernels[k][1]])
+
+
+@pytest.mark.parametrize("fft", [False, True])
+def test_lambda_rule_unit_atom_on_the_grid(oracle_mod, fft):
+    """lambda = frac * max over the grid of Phi^T y (the reading of Section 3's lambda).  For
+    y = Phi G(theta*, 1), theta* on the grid, one kernel: by Cauchy-Schwarz the maximum is at
+    theta* and equals |y|^2, so the rule gives frac |y|^2, and the grid argmax is theta*."""
+    n, R = (10, 11, 12), (2, 2, 3)
+    H = sfw_inputs.gaussian_psf((1.1, 1.2, 1.6), R)
+    kernels = [(1.2, 2.0)]
+    m = np.array([[5.0, 5.0, 6.0]])
+    y = oracle_mod.forward(n, R, H, m, np.array([1.2]), np.array([2.0]), np.ones(1))
+    e = float(np.sum(y * y))
+    assert oracle_mod.lambda_rule(n, R, H, y, kernels, frac=0.05, fft=fft) == pytest.approx(0.05 * e, rel=1e-9)
+    assert oracle_mod.lambda_rule(n, R, H, y, kernels, frac=1.0, fft=fft) == pytest.approx(e, rel=1e-9)
+    eta = (oracle_mod.eta_grid_fft if fft else oracle_mod.eta_grid)(n, R, H, y, 1.0, kernels)
+    i, val = oracle_mod.grid_argmax(eta)
+    assert i == int(np.ravel_multi_index((5, 5, 6), n))
+    assert val == pytest.approx(e, rel=1e-9)
+
+
 # ---------------------------------------------------------------- argmax (step 1 seed)
 
 @pytest.mark.parametrize("shape", [(3, 8, 8, 8), (15, 12, 12, 12)])
