@@ -68,13 +68,15 @@ enum { SFW_ROUTE_AUTO = 0, SFW_ROUTE_FFT = 1, SFW_ROUTE_DIRECT = 2 };
  *   psf       (2R0+1)(2R1+1)(2R2+1) values, C order, centred at index R
  *   n_sigma, n_d, sigmas, ds
  *             certificate grid (step 1 of Algorithms 1 and 2): kernels
- *             k = i_sigma * n_d + i_d, sigma in [0.25, 16], d in [0.5, 4]
+ *             k = i_sigma * n_d + i_d, sigma in [0.25, 16], d in [0.5, 4];
+ *             K = n_sigma * n_d in [0, 256] (0: no certificate grid) and
+ *             K * n0 * n1 * n2 < 2^32 (flat candidate indices fit 32 bits)
  *   precision SFW_PREC_FP32 (complex64 kernel-family table) or SFW_PREC_BF16
  *             (bfloat16 table; tensor-core axis-0 stage for real tables, see
  *             sfw_certificate_grid)
  *   eps       atom truncation level for rendering and the adjoint: an atom is
- *             evaluated only where exp(-(rho/sigma)^d/2) >= eps; 0 selects
- *             1e-9
+ *             evaluated only where exp(-(rho/sigma)^d/2) >= eps; in [0, 0.1),
+ *             0 selects 1e-9
  *   route     SFW_ROUTE_AUTO, SFW_ROUTE_FFT or SFW_ROUTE_DIRECT (above).  A
  *             DIRECT plan builds no kernel-family table; an AUTO plan builds
  *             what both routes need. */
@@ -127,8 +129,10 @@ typedef struct {
  * convolution in D computed once" of Section 2: for every grid kernel k,
  * K_k = H * g_{sigma_k, d_k} sampled at every grid displacement, transformed
  * on P_cert.  Synchronous (returns after the table is built).  *out receives
- * the plan.  Errors: SFW_ERR_ARG / SFW_ERR_SHAPE on bad sizes,
- * SFW_ERR_ALLOC, SFW_ERR_CUDA. */
+ * the plan.  Errors (checked before any CUDA call): SFW_ERR_SHAPE for n, R,
+ * K or K * V outside the ranges above; SFW_ERR_ARG for NULL desc, out, psf or
+ * grid arrays, negative grid sizes, grid values, precision, eps or route
+ * outside theirs.  Then SFW_ERR_ALLOC or SFW_ERR_CUDA from the build. */
 sfw_status sfw_plan_create(const sfw_plan_desc* desc, sfw_plan** out);
 
 /* Engine choice by timing (no counterpart in the paper).  For an SFW_ROUTE_AUTO

@@ -80,6 +80,57 @@ def test_host_argument_checks_need_no_gpu(built):
     assert _abi.sfw_launch_count() == 0
 
 
+def _desc(np, ctypes, _abi, keep, **over):
+    """A valid 8^3 plan description (3 x 2 certificate kernels), with fields replaced."""
+    psf = np.full((3, 3, 3), 1.0 / 27, np.float32)
+    sig = np.array(over.pop("sigmas", [1.0, 2.0, 3.0]), np.float32)
+    ds = np.array(over.pop("ds", [1.5, 2.0]), np.float32)
+    keep += [psf, sig, ds]
+    d = _abi.PlanDesc()
+    d.n[:] = over.pop("n", [8, 8, 8])
+    d.R[:] = over.pop("R", [1, 1, 1])
+    fp = ctypes.POINTER(ctypes.c_float)
+    d.psf = psf.ctypes.data_as(fp)
+    d.n_sigma, d.n_d = over.pop("n_sigma", sig.size), over.pop("n_d", ds.size)
+    d.sigmas, d.ds = sig.ctypes.data_as(fp), ds.ctypes.data_as(fp)
+    if over.pop("null_sigmas", False):
+        d.sigmas = fp()
+    for k, v in over.items():
+        setattr(d, k, fp() if v is None else v)
+    return d
+
+
+@pytest.mark.parametrize("over,status,what", [
+    (dict(n=[3, 8, 8]), 2, "n[0]"),
+    (dict(n=[8, 8, 1025]), 2, "n[2]"),
+    (dict(R=[1, -1, 1]), 2, "R[1]"),
+    (dict(R=[65, 1, 1]), 2, "R[0]"),
+    (dict(psf=None), 1, "psf"),
+    (dict(n_sigma=-1), 1, "negative grid"),
+    (dict(null_sigmas=True), 1, "grid arrays"),
+    (dict(sigmas=[1.0] * 16, ds=[1.5] * 17), 2, "K=272"),
+    (dict(sigmas=[0.2, 1.0, 2.0]), 1, "grid sigma"),
+    (dict(ds=[1.5, 4.5]), 1, "grid d"),
+    (dict(precision=2), 1, "precision"),
+    (dict(eps=0.1), 1, "eps"),
+    (dict(eps=-1e-3), 1, "eps"),
+    (dict(n=[1024, 1024, 1024], sigmas=[1.0, 2.0, 3.0, 4.0], ds=[1.5]), 2, "2^32"),
+])
+def test_plan_description_errors(built, over, status, what):
+    """Every range of the plan description that include/sfw.h documents is refused with the
+    documented status before any CUDA call (no GPU needed)."""
+    import ctypes
+    import numpy as np
+    from paper_2009_05473_gb300 import _abi
+    keep = []
+    d = _desc(np, ctypes, _abi, keep, **over)
+    with pytest.raises(_abi.SfwError) as e:
+        _abi.sfw_plan_create(d)
+    assert e.value.status == status, str(e.value)
+    assert what in str(e.value), str(e.value)
+    assert _abi.sfw_launch_count() == 0
+
+
 def test_no_cpu_fallback():
     """Without a GPU the product path refuses to run (there is no CPU path), and without the
     built library the binding raises instead of computing anything."""
