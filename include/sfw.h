@@ -369,12 +369,16 @@ sfw_status sfw_gram(sfw_plan* plan, const sfw_atoms* atoms, const float* y, doub
  * synchronisation, no allocation): capture it into a CUDA graph to run the
  * whole batch as one graph launch.  The first step computes the launch grids
  * (occupancy queries): run it once before any capture.
+ *   count     number of volumes, 1..1024
  *   plans     host array of count distinct plans with a certificate grid; they
  *             must outlive the batch and not be used concurrently with a step
  *   vols      host array of count volume descriptions: device buffers owned by
  *             the caller, fixed for the batch's lifetime (the step reads y and
  *             the atoms and writes the outputs in place)
- *   lambdas   host array of count regularisation weights (> 0) */
+ *   lambdas   host array of count regularisation weights (> 0)
+ * Errors: SFW_ERR_ARG for a NULL array, count outside its range, a NULL,
+ * repeated or grid-less plan, N outside 1..4096, a NULL buffer or a lambda
+ * not > 0 (all checked before any CUDA call); SFW_ERR_ALLOC, SFW_ERR_CUDA. */
 typedef struct sfw_batch sfw_batch;
 
 typedef struct {

@@ -131,6 +131,17 @@ def test_plan_description_errors(built, over, status, what):
     assert _abi.sfw_launch_count() == 0
 
 
+def test_batch_argument_errors(built):
+    """sfw_batch_create refuses a count outside 1..1024 and a NULL plan before any CUDA call."""
+    from paper_2009_05473_gb300 import _abi
+    for plans, what in (([], "count"), ([None] * 1025, "count"), ([None], "plan 0 is NULL")):
+        vols = [_abi.BatchVolume() for _ in plans]
+        with pytest.raises(_abi.SfwError) as e:
+            _abi.sfw_batch_create(plans, vols, [1.0] * len(plans))
+        assert e.value.status == 1 and what in str(e.value), str(e.value)
+    assert _abi.sfw_launch_count() == 0
+
+
 def test_no_cpu_fallback():
     """Without a GPU the product path refuses to run (there is no CPU path), and without the
     built library the binding raises instead of computing anything."""
