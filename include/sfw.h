@@ -155,7 +155,8 @@ sfw_status sfw_plan_query(const sfw_plan* plan, sfw_plan_info* info);
 
 /* Device-side health of a plan (no counterpart in the paper).  Kernels that
  * wait on the copy engine or the tensor cores (the certificate tail's TMA slab
- * copies; the tensor-core axis-0 stage's bulk copies and MMA completions) give
+ * copies; the tensor-core axis-0 stage's bulk copies and MMA completions; the
+ * tensor-core axis-2 tail's tensor-map loads and MMA completions) give
  * up after a bounded number of polls, leave their results unspecified and set
  * a flag of the plan instead of hanging.  This call synchronises the device,
  * returns SFW_ERR_TIMEOUT if the flag is set (and clears it), else SFW_OK. */
@@ -185,8 +186,10 @@ sfw_status sfw_forward(sfw_plan* plan, const sfw_atoms* atoms, float* y_out, voi
  * With precision SFW_PREC_BF16 the table is read as bfloat16 (values carry
  * ~3 significant digits); with a real table (even PSF) the axis-0 stage of the
  * correlation then runs on the tensor cores: bf16 operands (the table and the
- * twiddled residual spectrum), FP32 accumulation.  sfw_eta_points re-evaluates
- * candidates in FP32. */
+ * twiddled residual spectrum), FP32 accumulation; where the certificate takes
+ * its per-axis tail and n2 <= 128, the axis-2 real inverse with the max over k
+ * runs on them too (tf32 operands read straight from the FP32 spectra).
+ * sfw_eta_points re-evaluates candidates in FP32. */
 sfw_status sfw_certificate_grid(sfw_plan* plan, const float* residual, double lambda,
                                 float* eta_out, float* max_out, int32_t* argk_out,
                                 float* best_val, int64_t* best_idx, void* stream);
